@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the RoofGS forward render on one GB300 (or N replicas).
+
+Workload (default): 3M Gaussians in 20 Gaussian clusters plus a far shell of
+radius 50, degree-3 SH stored INT8 with one FP16 factor per Gaussian,
+3840x2160 with 16x16 tiles, 30 camera poses on an orbit (radius 4, elevation
+15 deg, 12 deg apart). One step = one full frame of the hot path: fused front
+end -> 32-bit quantized-key radix sort -> tile ranges -> dual-pixel fast-exp
+rasterizer. The plain 3DGS path (exact mode) is timed on the same frames for
+the speedup, and the CPU oracle on a bounded sample for the CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0). With N > 1 (torchrun) every rank renders its
+own K frames of the same orbit (replicas, no collective on the data path);
+the timed region is bracketed by barriers and the max over ranks is taken.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "4K FPS RoofGS vs plain 3DGS path on GB300 at ≤0.05 dB; serve p50/p99 ms"
+UNIT = "FPS"
+CLOCK_QUERY = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+# Source-level FP32/ALU-pipe instruction counts of the rasterizers' inner loops
+# (per evaluated (Gaussian, pixel) exponent, and per pair inside the
+# alpha >= 1/255 range that is blended or ends the pixel):
+#   RoofGS dual-pixel: exponent 4 (5 FFMA for P(x,y), 3 for P(x,y+1), per pixel)
+#     + range test 1; blend = FFMA + shift-add (bit exp) + min + 1-alpha +
+#     T(1-alpha) + stop test + alpha*T + 3 FFMA colour + T update = 11.
+#   exact: exponent (2 FADD + 6 FMUL/FFMA/FADD) + test 2 = 10; blend = expf
+#     (~9) + o*e + min + alpha test + 1-alpha + T(1-alpha) + stop test + alpha*T
+#     + 3 FFMA + T update = 20.
+OPS = {"roofgs": (5, 11), "exact": (10, 20)}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--gaussians", type=int, default=3_000_000)
+    p.add_argument("--width", type=int, default=3840)
+    p.add_argument("--height", type=int, default=2160)
+    p.add_argument("--poses", type=int, default=30)
+    p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-exact", action="store_true")
+    return p.parse_args()
+
+
+def workload_desc(a):
+    return ("clustered %dM Gaussians (20 clusters + shell r=50), %dx%d, 16x16 tiles, %d orbit poses, "
+            "INT8 SH with per-Gaussian FP16 scale" % (a.gaussians // 1_000_000, a.width, a.height, a.poses))
+
+
+def make_inputs(a):
+    from paper_2608_15785_gb300 import synth
+    sc = synth.clustered_scene(a.gaussians, a.seed)
+    cams = [synth.orbit_camera(k, a.width, a.height) for k in range(a.poses)]
+    return sc, cams
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, bus_id: str | None):
+        self.bus = (bus_id or "").lower()
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + CLOCK_QUERY, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        self.t0 = time.time()
+        self.marks = {}
+
+    def mark(self, name):
+        self.marks[name] = time.time()
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = []
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.bus and self.bus[-12:] not in parts[1].lower():
+                continue
+            rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        loaded = [x for x in sm if smax and x >= 0.3 * max(smax)] or sm
+        reasons = sorted({REASONS[i] for r in rows for i in range(4) if "active" == r[6 + i].lower()})
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per stage (bytes for the HBM-bound stages, ops for raster)
+# ---------------------------------------------------------------------------
+def stage_work(mode, st, W, H):
+    N, nf, nv, nd = st["n_gaussians"], st["n_front"], st["n_visible"], st["n_entries"]
+    tiles = st["tiles_x"] * st["tiles_y"]
+    passes = st["sort_passes"]
+    if mode == "roofgs":
+        # 16 B mean+log o per Gaussian; 16 B FP16 geometry if inside the depth/opacity range;
+        # 48 B INT8 SH + 32 B record if visible; 8 B key+value per entry
+        front = 16 * N + 16 * nf + 80 * nv + 8 * nd
+        sort = 4 * nd + passes * 16 * nd
+        ranges = 4 * nd + 8 * tiles
+    else:
+        # preprocess: 44 B geometry per Gaussian, 192 B FP32 SH + 56 B outputs if visible, 4 B count;
+        # scan: 8 B per Gaussian; duplicate: 4 B per Gaussian + 24 B per visible + 12 B per entry
+        front = 44 * N + 248 * nv + 4 * N + 8 * N + 4 * N + 24 * nv + 12 * nd
+        sort = 8 * nd + passes * 24 * nd
+        ranges = 8 * nd + 8 * tiles
+    a, b = OPS[mode]
+    raster_ops = a * st["n_pairs"] + b * st["n_blends"]
+    return {"front": front, "sort": sort, "ranges": ranges, "raster_ops": raster_ops,
+            "raster_bytes": 36 * nd + 12 * W * H}
+
+
+def mean_stats(stats, poses_used):
+    keys = ["n_gaussians", "n_front", "n_visible", "n_entries", "n_pairs", "n_blends", "tiles_x", "tiles_y",
+            "sort_passes"]
+    return {k: sum(stats[p][k] for p in poses_used) / len(poses_used) for k in keys}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(a, rank, world, local_rank):
+    import torch
+
+    from paper_2608_15785_gb300 import binding
+    from paper_2608_15785_gb300.build import build
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    build()
+    sc, cams = make_inputs(a)
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    bus_id = None
+    if bus is not None:
+        bus_id = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), bus, getattr(props, "pci_device_id", 0))
+    gs = binding.Scene(sc, sh_scale_mode=binding.RG_SH_SCALE_BAND_GAUSS)
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty((3, a.height, a.width), dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(mode, steps, flags):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            gs.render(cams[(rank + k * world) % len(cams)], mode=mode, flags=flags, out=out)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    results = {}
+    sampler = ClockSampler(bus_id) if rank == 0 else None
+    modes = ["roofgs"] if a.no_exact else ["roofgs", "exact"]
+    for mode in modes:
+        # checked frames: size the workspace for every pose, collect the work counters
+        stats = []
+        for cam in cams:
+            _, st = gs.render(cam, mode=mode, out=out, stats=True)
+            stats.append(st)
+        for k in range(a.warmup):
+            gs.render(cams[k % len(cams)], mode=mode, out=out)
+        torch.cuda.synchronize(dev)
+        gs.stage_times()  # discard
+        steps = a.steps if mode == "roofgs" else max(10, a.steps // 2)
+        if sampler and mode == "roofgs":
+            sampler.mark("timed_start")
+        ms = timed(mode, steps, binding.RG_FLAG_STAGE_EVENTS)
+        if sampler and mode == "roofgs":
+            sampler.mark("timed_end")
+        stage_ms, frames = gs.stage_times()
+        gs.check()  # no overflow, no timed-out wait in the timed frames
+        poses_used = sorted({(rank + k * world) % len(cams) for k in range(steps)})
+        results[mode] = {"ms": ms, "steps": steps, "stats": mean_stats(stats, poses_used),
+                         "stage_ms": [x / max(frames, 1) for x in stage_ms], "frames_timed_by_events": frames}
+    # end-to-end through the public API: render + device->host read of every frame into pinned memory
+    host = torch.empty((3, a.height, a.width), dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(5, min(a.steps, 60))
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        gs.render(cams[(rank + k * world) % len(cams)], mode="roofgs", out=out)
+        host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    gs.check()
+    clocks = sampler.stop() if sampler else None
+    if dist is not None:
+        dist.barrier()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    r = results["roofgs"]
+    fps = world * r["steps"] / (r["ms"] / 1000.0)
+    line = {"metric": METRIC, "value": round(fps, 2), "unit": UNIT, "n_gpus": world, "steps": r["steps"],
+            "warmup": a.warmup, "ms_per_step": round(r["ms"] / r["steps"], 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    cfg = {"workload": workload_desc(a), "mode": "roofgs", "n_gaussians": a.gaussians,
+           "resolution": [a.width, a.height], "tile": [16, 16], "poses": a.poses, "parallelism": "replicas",
+           "l2": "inputs larger than L2: 240 MB compact scene read per frame, 99.5 MB image written per frame",
+           "entries_per_frame": round(r["stats"]["n_entries"]),
+           "stage_ms": dict(zip(["front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"],
+                                [round(x, 4) for x in r["stage_ms"]]))}
+    if "exact" in results:
+        ex = results["exact"]
+        ex_fps = world * ex["steps"] / (ex["ms"] / 1000.0)
+        cfg["exact_fps"] = round(ex_fps, 2)
+        cfg["speedup_vs_exact"] = round(fps / ex_fps, 3)
+        cfg["exact_stage_ms"] = dict(zip(["front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"],
+                                         [round(x, 4) for x in ex["stage_ms"]]))
+        cfg["exact_entries_per_frame"] = round(ex["stats"]["n_entries"])
+    line["config"] = cfg
+    line["roofline"], line["stages"] = rooflines(r, a, props, clocks)
+    line["gpu_launches"] = r["steps"] * 8  # front end, histogram, 4 sort passes, ranges, raster
+    line["e2e"] = {"value": round(world * e2e_steps / e2e_s, 2), "unit": UNIT,
+                   "h2d_bytes_per_step": 100,  # the rg_camera struct, passed by value per call
+                   "d2h_bytes_per_step": 3 * a.width * a.height * 4}
+    line["clocks"] = {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if clocks else None
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, sc, cams, budget_tiles=64)
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+def rooflines(r, a, props, clocks):
+    hbm, src = measured_peaks()
+    W, H = a.width, a.height
+    work = stage_work("roofgs", r["stats"], W, H)
+    sms = props.multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    alu_peak = sms * 128 * mhz * 1e6 / 1e9  # FP32-pipe instructions per second (G/s): 128 lanes per SM
+    st_ms = dict(zip(["front", "hist", "passes", "ranges", "raster"], r["stage_ms"][:5]))
+    sort_ms = st_ms["hist"] + st_ms["passes"]
+    stages = {
+        "front_end": {"bound": "hbm", "achieved": work["front"] / (st_ms["front"] * 1e-3) / 1e9, "peak": hbm,
+                      "unit": "GB/s", "ms": st_ms["front"], "bytes": work["front"]},
+        "sort": {"bound": "hbm", "achieved": work["sort"] / (sort_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                 "ms": sort_ms, "bytes": work["sort"]},
+        "ranges": {"bound": "hbm", "achieved": work["ranges"] / (st_ms["ranges"] * 1e-3) / 1e9, "peak": hbm,
+                   "unit": "GB/s", "ms": st_ms["ranges"], "bytes": work["ranges"]},
+        "raster": {"bound": "alu", "achieved": work["raster_ops"] / (st_ms["raster"] * 1e-3) / 1e9, "peak": alu_peak,
+                   "unit": "Gop/s", "ms": st_ms["raster"], "ops": work["raster_ops"]},
+    }
+    for v in stages.values():
+        v["frac"] = round(v["achieved"] / v["peak"], 4)
+        v["achieved"] = round(v["achieved"], 1)
+        v["peak"] = round(v["peak"], 1)
+        v["ms"] = round(v["ms"], 4)
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    d = stages[dom]
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+            "frac": d["frac"], "traffic": None,
+            "peak_source": (src + " HBM copy bandwidth") if d["bound"] == "hbm"
+            else "%d SMs x 128 FP32 lanes x %.0f MHz median SM clock under load" % (sms, mhz)}
+    return roof, stages
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_setup(sc):
+    import oracle
+    oracle.build()
+    comp = oracle.compact(sc, per_gaussian_sh_scale=True)
+    return oracle, comp
+
+
+def oracle_frame_seconds(oracle, sc, comp, cam, stride, t_bin=None):
+    """Binning of every Gaussian + FP64 blend of every `stride`-th tile, extrapolated to the frame."""
+    lay = oracle.layout(cam)
+    nt = lay["tiles_x"] * lay["tiles_y"]
+    import numpy as np
+    if t_bin is None:
+        t0 = time.perf_counter()
+        oracle.render(sc, cam, oracle.ROOFGS, comp=comp, tiles=np.zeros(0, np.int32), with_diag=False)
+        t_bin = time.perf_counter() - t0
+    tiles = np.arange(0, nt, stride, dtype=np.int32)
+    t0 = time.perf_counter()
+    oracle.render(sc, cam, oracle.ROOFGS, comp=comp, tiles=tiles, with_diag=False)
+    t = time.perf_counter() - t0
+    return t_bin + max(t - t_bin, 0.0) * nt / len(tiles), t_bin, len(tiles), nt
+
+
+def cpu_baseline(a, sc, cams, budget_tiles=64):
+    oracle, comp = oracle_setup(sc)
+    sec, t_bin, ns, nt = oracle_frame_seconds(oracle, sc, comp, cams[0], budget_tiles)
+    return {"value": round(1.0 / sec, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "pose 0: FP32 binning of all %d Gaussians (%.1f s) + FP64 blend of every %dth tile "
+                      "(%d of %d), extrapolated to the full frame" % (a.gaussians, t_bin, budget_tiles, ns, nt)}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return None
+    sc, cams = make_inputs(a)
+    oracle, comp = oracle_setup(sc)
+    stride = 256
+    _, t_bin, ns, nt = oracle_frame_seconds(oracle, sc, comp, cams[0], stride)
+    for k in range(a.warmup):
+        oracle_frame_seconds(oracle, sc, comp, cams[k % len(cams)], stride, t_bin)
+    secs = [oracle_frame_seconds(oracle, sc, comp, cams[k % len(cams)], stride, t_bin)[0] for k in range(a.steps)]
+    total = sum(secs)
+    fps = a.steps / total
+    sample = ("per step: FP32 binning of all %d Gaussians (measured once, %.1f s) + FP64 blend of every %dth tile "
+              "(%d of %d) of one orbit pose, extrapolated to the full frame" % (a.gaussians, t_bin, stride, ns, nt))
+    return {"metric": METRIC, "value": round(fps, 5), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(1000 * total / a.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_desc(a), "mode": "roofgs (oracle, exact exp)",
+                       "n_gaussians": a.gaussians, "resolution": [a.width, a.height], "poses": a.poses},
+            "cpu_baseline": {"value": round(fps, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(fps, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(a.gpus)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != a.gpus and "WORLD_SIZE" not in os.environ:
+        world = 1
+    if a.impl == "reference":
+        line = run_reference(a, rank, world)
+    else:
+        line = run_ours(a, rank, world, local_rank)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

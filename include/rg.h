@@ -1,0 +1,233 @@
+/*
+ * rg.h -- C ABI of the GB300 RoofGS renderer (librg.so).
+ *
+ * Forward render of 3D Gaussian Splatting in two modes:
+ *   RG_MODE_EXACT   the plain 3DGS path: FP32 attributes (236 bytes per
+ *                   Gaussian, paper Sec. III-A, Eq. (3)), separate
+ *                   preprocess / scan / duplicate kernels, 64-bit
+ *                   tile|float-depth keys (Sec. IV-A.2), IEEE expf in the
+ *                   rasterizer (Eqs. (7), (10)-(12));
+ *   RG_MODE_ROOFGS  the paper's method: compact attributes (FP32 mean, FP16
+ *                   rotation and scale, INT8 spherical harmonics with one
+ *                   scale per degree and channel, Sec. IV-A.1, Eq. (8)), one
+ *                   fused preprocess+duplicate+key kernel (Sec. IV-A.3), the
+ *                   resolution-adaptive 32-bit key (Sec. IV-A.2, Eq. (9)),
+ *                   coefficient folding and dual-pixel evaluation
+ *                   (Sec. IV-B.1, Eqs. (13)-(20)) and the range-aware bit-level
+ *                   exponential (Sec. IV-B.2, Eqs. (23)-(25)).
+ *
+ * Conventions for every entry point:
+ *   - Functions never abort or trap; they return an rg_status. On failure,
+ *     rg_last_error() returns a thread-local message.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Work is stream-ordered; only rg_scene_create, rg_scene_destroy,
+ *     rg_scene_reserve, rg_inspect and an rg_render call given a non-NULL
+ *     `stats` synchronise the stream.
+ *   - Device pointers must be CUDA device memory of the current device.
+ *     Output buffers are owned by the caller. Input arrays may be freed after
+ *     rg_scene_create returns.
+ *   - One scene owns one frame workspace: rg_render calls on the same scene
+ *     must be ordered on one stream (calls on different streams race).
+ */
+#ifndef RG_H
+#define RG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RG_OK = 0,
+    RG_ERR_INVALID_ARG = 1,  /* a NULL pointer, a bad size, a non-finite input, ... */
+    RG_ERR_OOM = 2,          /* a device allocation failed */
+    RG_ERR_CUDA = 3,         /* a CUDA call failed (message in rg_last_error) */
+    RG_ERR_CAPACITY = 4,     /* entries exceeded the workspace and it could not grow */
+    RG_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up (result invalid) */
+    RG_ERR_BUSY = 6,
+    RG_ERR_NOT_READY = 7,
+    RG_ERR_UNSUPPORTED = 8   /* entry point or option not built yet */
+} rg_status;
+
+typedef struct rg_scene rg_scene;   /* opaque; owns every device buffer it allocates */
+typedef struct rg_server rg_server; /* opaque; request loop (not built yet) */
+
+/* storage flags of rg_scene_desc */
+#define RG_STORE_FP32 1u     /* keep the FP32 attributes (needed by RG_MODE_EXACT) */
+#define RG_STORE_COMPACT 2u  /* build the compact attributes (needed by RG_MODE_ROOFGS) */
+
+/* sh_scale_mode of rg_scene_desc */
+#define RG_SH_SCALE_BAND 0       /* Eq. (8): one INT8 scale per SH degree d and channel c */
+#define RG_SH_SCALE_BAND_GAUSS 1 /* additionally one FP16 factor per Gaussian */
+
+/*
+ * Scene description (paper Table I notation: mean mu, rotation r, scale s,
+ * opacity, plus degree-3 spherical harmonics).
+ *   means     [n][3] FP32 world positions
+ *   scales    [n][3] FP32 activated scales (standard deviations along the axes)
+ *   quats     [n][4] FP32 rotations (w, x, y, z); normalised by the renderer
+ *   opacities [n]    FP32 activated opacities in [0, 1]
+ *   sh        [n][16][3] FP32 coefficients, index k = l^2 + l + m (real
+ *             orthonormal harmonics without Condon-Shortley phase), then RGB
+ *   on_device 1 if the five pointers are device memory, 0 if host memory
+ * Every value must be finite; opacities outside [0, 1] are rejected.
+ */
+typedef struct {
+    int64_t n;
+    int32_t sh_degree; /* 0..3: coefficients beyond (deg+1)^2 are ignored */
+    int32_t on_device;
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opacities;
+    const float* sh;
+    uint32_t storage;      /* RG_STORE_* bits; 0 means both */
+    int32_t sh_scale_mode; /* RG_SH_SCALE_* */
+} rg_scene_desc;
+
+/*
+ * Pinhole camera. world -> camera: p = R mu + t (R row-major); the camera looks
+ * along +z with x right and y down. Pixel (i, j) is sampled at the continuous
+ * point (i, j): u = fx p_x / p_z + cx, v = fy p_y / p_z + cy. Gaussians with
+ * p_z outside (znear, zfar] are culled (Sec. IV-A.2: the quantization interval
+ * [z_near, z_far] is fixed per camera). bg is added with the final
+ * transmittance: out = C + T bg.
+ */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear, zfar;
+    float bg[3];
+} rg_camera;
+
+#define RG_MODE_EXACT 0
+#define RG_MODE_ROOFGS 1
+
+/* RoofGS-mode ingredient flags (ignored in exact mode) */
+#define RG_FLAG_EXACT_EXP (1u << 0)    /* use expf instead of the bit-level exponential of Eq. (24) */
+#define RG_FLAG_SINGLE_PIXEL (1u << 1) /* one pixel per thread instead of the dual-pixel scheme, Eq. (20) */
+/* flags for both modes */
+#define RG_FLAG_STAGE_EVENTS (1u << 8) /* record per-stage CUDA events (rg_stage_times) */
+
+typedef struct {
+    int32_t mode;   /* RG_MODE_EXACT or RG_MODE_ROOFGS */
+    uint32_t flags; /* RG_FLAG_* */
+    int32_t tile_w; /* tile shape; 16 x 16 (0 = default 16) */
+    int32_t tile_h;
+} rg_render_opts;
+
+/* Frame statistics (filled only when rg_render is given a non-NULL stats pointer). */
+typedef struct {
+    int64_t n_gaussians;
+    int64_t n_front;    /* Gaussians inside (znear, zfar] (RoofGS: also with o >= 1/255) */
+    int64_t n_visible;  /* Gaussians that emitted at least one (tile, Gaussian) entry */
+    int64_t n_entries;  /* N_dup: (tile, Gaussian) entries sorted this frame */
+    int64_t capacity;   /* entry capacity of the workspace after the call */
+    int64_t n_pairs;    /* (Gaussian, pixel) exponents the rasterizer evaluated for unfinished pixels */
+    int64_t n_blends;   /* of those, pairs inside the alpha >= 1/255 range (blended, or ending the pixel) */
+    int32_t regrown;    /* 1 if the call grew the workspace and rendered again */
+    int32_t sort_passes;
+    int32_t b_t, b_d;   /* key bit split (RoofGS) or tile bits used (exact) */
+    int32_t tiles_x, tiles_y;
+} rg_stats;
+
+/*
+ * Create a resident scene (Sec. IV-A.1 for the compact layout): copies the FP32
+ * attributes (RG_STORE_FP32) and/or builds the compact attributes
+ * (RG_STORE_COMPACT): FP16 rotation and scale, FP32 mean, log o in FP32, and the
+ * INT8 SH codes of Eq. (8) with their 12 band scales. Synchronises `stream`.
+ * Errors: RG_ERR_INVALID_ARG (NULL/negative sizes, non-finite values,
+ * opacity outside [0, 1], sh_degree outside 0..3), RG_ERR_OOM, RG_ERR_CUDA.
+ */
+rg_status rg_scene_create(const rg_scene_desc* desc, void* stream, rg_scene** out);
+
+/* Free every device buffer of the scene (synchronises the device). NULL is a no-op. */
+rg_status rg_scene_destroy(rg_scene* scene);
+
+/* Grow the frame workspace to hold at least n_entries (tile, Gaussian) entries. Synchronous. */
+rg_status rg_scene_reserve(rg_scene* scene, int64_t n_entries);
+
+/*
+ * Render one view into out_chw, a caller-owned device buffer of 3*H*W FP32
+ * values laid out [channel][row][column].
+ * Pipeline (exact): preprocess -> scan -> duplicate -> 64-bit radix sort ->
+ * tile ranges -> rasterizer (Sec. II-A pipeline, Sec. III).
+ * Pipeline (RoofGS): fused front end -> 32-bit radix sort (4 passes) ->
+ * tile ranges -> dual-pixel fast-exp rasterizer (Sec. IV).
+ * The number of entries stays on the device: with stats == NULL the call does
+ * not synchronise; if the entries exceed the workspace the image is
+ * incomplete and the overflow is recorded (see rg_scene_check). With stats
+ * != NULL the call synchronises, grows the workspace and renders again if
+ * needed, and fills *stats.
+ * Errors: RG_ERR_INVALID_ARG (NULL, width/height <= 0, zfar <= znear, tile
+ * shape other than 16x16, a mode whose storage the scene lacks),
+ * RG_ERR_CAPACITY, RG_ERR_TIMEOUT, RG_ERR_CUDA, RG_ERR_OOM.
+ */
+rg_status rg_render(rg_scene* scene, const rg_camera* cam, const rg_render_opts* opts, float* out_chw,
+                    rg_stats* stats, void* stream);
+
+/*
+ * Report and clear the sticky device flags of every render since the last
+ * check: RG_ERR_CAPACITY if a frame overflowed its workspace,
+ * RG_ERR_TIMEOUT if a bounded device wait gave up, else RG_OK. Synchronous.
+ */
+rg_status rg_scene_check(rg_scene* scene, void* stream);
+
+/*
+ * Per-stage device times (ms) of the frames rendered with RG_FLAG_STAGE_EVENTS
+ * since the last call, summed: ms[0..5] = front end (exact: preprocess + scan +
+ * duplicate), sort histogram, sort passes, tile ranges, rasterizer, whole frame.
+ * *frames receives the number of frames summed. Synchronises the recorded events.
+ */
+rg_status rg_stage_times(rg_scene* scene, float* ms6, int32_t* frames);
+
+/* rg_inspect selectors: copy internal buffers of the last frame to host memory */
+#define RG_INSPECT_KEYS 1        /* sorted keys: uint32 (RoofGS) or uint64 (exact), n_entries of them */
+#define RG_INSPECT_VALUES 2      /* sorted values: uint32 Gaussian indices */
+#define RG_INSPECT_RANGES 3      /* uint32 [tiles][2] = [start, end) per tile */
+#define RG_INSPECT_SH_CODES 4    /* int8 [n][16][3] compact SH codes */
+#define RG_INSPECT_SH_SCALES 5   /* float [4][3] band scales s_{d,c} */
+#define RG_INSPECT_GAUSS_SCALE 6 /* uint16 [n] FP16 per-Gaussian SH factors */
+#define RG_INSPECT_GEOM16 7      /* uint16 [n][8] = q (4), s (3), g as FP16 bits */
+#define RG_INSPECT_LOG_OPACITY 8 /* float [n] stored log o */
+
+/*
+ * Copy one internal buffer to host memory (synchronises the device).
+ * *out_bytes receives the buffer size; if cap_bytes is smaller nothing is
+ * copied and RG_ERR_INVALID_ARG is returned.
+ */
+rg_status rg_inspect(rg_scene* scene, int32_t what, void* host_dst, int64_t cap_bytes, int64_t* out_bytes);
+
+/*
+ * Diagnostic: out_dev[i] = exp^(P_dev[i]), the bit-level exponential of Eq. (24)
+ * exactly as the RoofGS rasterizer evaluates it (FP32, valid on [-ln 255, 0]).
+ * Device arrays of n floats; stream-ordered.
+ */
+rg_status rg_eval_fast_exp(const float* P_dev, float* out_dev, int64_t n, void* stream);
+
+/*
+ * Not built yet (return RG_ERR_UNSUPPORTED): batched multi-view rendering,
+ * the rasterizer/preprocess backward, and the request loop.
+ */
+rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
+                          const rg_render_opts* opts, float* const* outs, void* stream);
+rg_status rg_backward(rg_scene* scene, const rg_camera* cam, const rg_render_opts* opts, const float* dL_dimg,
+                      float* grads, void* stream);
+rg_status rg_submit(rg_server* server, const rg_camera* cam, int32_t scene_slot, uint64_t* ticket);
+rg_status rg_poll(rg_server* server, uint64_t ticket, float* out_chw);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* rg_last_error(void);
+
+/* ABI version: 100 * major + minor. */
+int32_t rg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RG_H */

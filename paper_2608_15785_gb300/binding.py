@@ -1,0 +1,229 @@
+"""ctypes binding of librg.so (include/rg.h): argument marshalling only.
+
+Every step of the render runs in the library's CUDA kernels. PyTorch provides
+device memory for outputs and the current CUDA stream. There is no CPU
+fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librg.so")
+
+RG_OK = 0
+STATUS = {0: "RG_OK", 1: "RG_ERR_INVALID_ARG", 2: "RG_ERR_OOM", 3: "RG_ERR_CUDA", 4: "RG_ERR_CAPACITY",
+          5: "RG_ERR_TIMEOUT", 6: "RG_ERR_BUSY", 7: "RG_ERR_NOT_READY", 8: "RG_ERR_UNSUPPORTED"}
+RG_STORE_FP32 = 1
+RG_STORE_COMPACT = 2
+RG_SH_SCALE_BAND = 0
+RG_SH_SCALE_BAND_GAUSS = 1
+RG_MODE_EXACT = 0
+RG_MODE_ROOFGS = 1
+RG_FLAG_EXACT_EXP = 1 << 0
+RG_FLAG_SINGLE_PIXEL = 1 << 1
+RG_FLAG_STAGE_EVENTS = 1 << 8
+RG_INSPECT_KEYS = 1
+RG_INSPECT_VALUES = 2
+RG_INSPECT_RANGES = 3
+RG_INSPECT_SH_CODES = 4
+RG_INSPECT_SH_SCALES = 5
+RG_INSPECT_GAUSS_SCALE = 6
+RG_INSPECT_GEOM16 = 7
+RG_INSPECT_LOG_OPACITY = 8
+
+# every entry point include/rg.h declares
+EXPORTS = ["rg_scene_create", "rg_scene_destroy", "rg_scene_reserve", "rg_render", "rg_scene_check",
+           "rg_stage_times", "rg_inspect", "rg_eval_fast_exp", "rg_render_batch", "rg_backward", "rg_submit",
+           "rg_poll", "rg_last_error", "rg_version"]
+
+
+class RgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class RgCamera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("znear", C.c_float), ("zfar", C.c_float), ("bg", C.c_float * 3)]
+
+
+class RgSceneDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("on_device", C.c_int32), ("means", C.c_void_p),
+                ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacities", C.c_void_p), ("sh", C.c_void_p),
+                ("storage", C.c_uint32), ("sh_scale_mode", C.c_int32)]
+
+
+class RgOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("flags", C.c_uint32), ("tile_w", C.c_int32), ("tile_h", C.c_int32)]
+
+
+class RgStats(C.Structure):
+    _fields_ = [("n_gaussians", C.c_int64), ("n_front", C.c_int64), ("n_visible", C.c_int64),
+                ("n_entries", C.c_int64), ("capacity", C.c_int64), ("n_pairs", C.c_int64), ("n_blends", C.c_int64),
+                ("regrown", C.c_int32), ("sort_passes", C.c_int32), ("b_t", C.c_int32),
+                ("b_d", C.c_int32), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load librg.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("librg.so is not built (run __graft_entry__.build() or "
+                               "python paper_2608_15785_gb300/build.py); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.rg_scene_create.argtypes = [C.POINTER(RgSceneDesc), P, C.POINTER(P)]
+        L.rg_scene_destroy.argtypes = [P]
+        L.rg_scene_reserve.argtypes = [P, C.c_int64]
+        L.rg_render.argtypes = [P, C.POINTER(RgCamera), C.POINTER(RgOpts), P, C.POINTER(RgStats), P]
+        L.rg_scene_check.argtypes = [P, P]
+        L.rg_stage_times.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_int32)]
+        L.rg_inspect.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
+        L.rg_eval_fast_exp.argtypes = [P, P, C.c_int64, P]
+        L.rg_render_batch.argtypes = [P, P, P, C.c_int32, P, P, P]
+        L.rg_backward.argtypes = [P, P, P, P, P, P]
+        L.rg_submit.argtypes = [P, P, C.c_int32, P]
+        L.rg_poll.argtypes = [P, C.c_uint64, P]
+        L.rg_last_error.restype = C.c_char_p
+        L.rg_last_error.argtypes = []
+        L.rg_version.restype = C.c_int32
+        for name in EXPORTS:
+            if name not in ("rg_last_error", "rg_version"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != RG_OK:
+        raise RgError(status, lib().rg_last_error().decode())
+
+
+def camera_struct(cam) -> RgCamera:
+    c = RgCamera()
+    for i, x in enumerate(np.asarray(cam.R, dtype=np.float32).reshape(9)):
+        c.R[i] = float(x)
+    for i, x in enumerate(np.asarray(cam.t, dtype=np.float32).reshape(3)):
+        c.t[i] = float(x)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.znear, c.zfar = float(cam.znear), float(cam.zfar)
+    for i, x in enumerate(np.asarray(cam.bg, dtype=np.float32).reshape(3)):
+        c.bg[i] = float(x)
+    return c
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _mode(mode) -> int:
+    if isinstance(mode, str):
+        return {"exact": RG_MODE_EXACT, "roofgs": RG_MODE_ROOFGS}[mode]
+    return int(mode)
+
+
+class Scene:
+    """A resident scene on the current CUDA device (rg_scene_create)."""
+
+    def __init__(self, scene, storage: int = RG_STORE_FP32 | RG_STORE_COMPACT,
+                 sh_scale_mode: int = RG_SH_SCALE_BAND, stream=None):
+        import torch
+        L = lib()
+        arrs = [scene.means, scene.scales, scene.quats, scene.opacities, scene.sh]
+        on_dev = all(isinstance(a, torch.Tensor) and a.is_cuda for a in arrs)
+        if on_dev:
+            keep = [a.contiguous().float() for a in arrs]
+            ptrs = [a.data_ptr() for a in keep]
+        else:
+            keep = [np.ascontiguousarray(a if not isinstance(a, torch.Tensor) else a.cpu().numpy(), dtype=np.float32)
+                    for a in arrs]
+            ptrs = [a.ctypes.data for a in keep]
+        d = RgSceneDesc()
+        d.n = int(keep[0].shape[0])
+        d.sh_degree = int(getattr(scene, "sh_degree", 3))
+        d.on_device = 1 if on_dev else 0
+        d.means, d.scales, d.quats, d.opacities, d.sh = ptrs
+        d.storage = int(storage)
+        d.sh_scale_mode = int(sh_scale_mode)
+        h = C.c_void_p()
+        check(L.rg_scene_create(C.byref(d), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+        self.n = d.n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rg_scene_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, cam, mode="roofgs", flags: int = 0, out=None, stats: bool = False, stream=None):
+        """Render one view; returns a [3, H, W] float32 CUDA tensor (and stats if asked)."""
+        import torch
+        c = camera_struct(cam)
+        if out is None:
+            out = torch.empty((3, c.height, c.width), dtype=torch.float32, device="cuda")
+        o = RgOpts(_mode(mode), int(flags), 16, 16)
+        st = RgStats() if stats else None
+        check(lib().rg_render(self._h, C.byref(c), C.byref(o), C.c_void_p(out.data_ptr()),
+                              C.byref(st) if st is not None else None, _stream_ptr(stream)))
+        return (out, st.as_dict()) if stats else out
+
+    def reserve(self, n_entries: int):
+        check(lib().rg_scene_reserve(self._h, int(n_entries)))
+
+    def check(self, stream=None):
+        check(lib().rg_scene_check(self._h, _stream_ptr(stream)))
+
+    def stage_times(self):
+        ms = (C.c_float * 6)()
+        fr = C.c_int32()
+        check(lib().rg_stage_times(self._h, ms, C.byref(fr)))
+        return list(ms), fr.value
+
+    def inspect(self, what: int) -> np.ndarray:
+        nb = C.c_int64()
+        check(lib().rg_inspect(self._h, int(what), None, 0, C.byref(nb)))
+        dtype = {RG_INSPECT_KEYS: np.uint8, RG_INSPECT_VALUES: np.uint32, RG_INSPECT_RANGES: np.uint32,
+                 RG_INSPECT_SH_CODES: np.int8, RG_INSPECT_SH_SCALES: np.float32, RG_INSPECT_GAUSS_SCALE: np.uint16,
+                 RG_INSPECT_GEOM16: np.uint16, RG_INSPECT_LOG_OPACITY: np.float32}[what]
+        buf = np.zeros(nb.value, dtype=np.uint8)
+        check(lib().rg_inspect(self._h, int(what), buf.ctypes.data_as(C.c_void_p), nb.value, C.byref(nb)))
+        return buf.view(dtype)
+
+
+def eval_fast_exp(P, stream=None):
+    """Device evaluation of the rasterizer's bit-level exponential (Eq. (24))."""
+    import torch
+    P = P.contiguous().float()
+    out = torch.empty_like(P)
+    check(lib().rg_eval_fast_exp(C.c_void_p(P.data_ptr()), C.c_void_p(out.data_ptr()), P.numel(), _stream_ptr(stream)))
+    return out
+
+
+def version() -> int:
+    return lib().rg_version()

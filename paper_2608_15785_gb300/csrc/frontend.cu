@@ -1,0 +1,453 @@
+// frontend.cu -- front ends of the renderer and the scene conversion kernels.
+//
+//  * k_frontend_fused: the RoofGS fused preprocess + duplicate + key kernel
+//    (Sec. IV-A.3): one thread per Gaussian projects, culls, decodes INT8 SH
+//    (Eq. (8)) and FP16 geometry (Sec. IV-A.1), computes the tile rectangle
+//    and the 32-bit tile|quantized-depth key (Sec. IV-A.2, Eq. (9)); the block
+//    allocates its entries with one shared-memory prefix sum and one
+//    device-wide slot (decoupled look-back, ordered by block, so equal keys stay
+//    in Gaussian order) and then writes the (key, value) array cooperatively:
+//    consecutive threads write consecutive entries (coalesced), whichever
+//    Gaussian they belong to. Only the raster record and the key-value array go
+//    to global memory.
+//  * k_exact_*: the plain 3DGS front end (preprocess -> scan -> duplicate,
+//    Sec. II-A), 64-bit keys of 32-bit tile id | 32-bit float depth.
+//  * scene conversion: finite-value check, per-(degree, channel) max |SH|,
+//    and the compact attribute encoder.
+#include "rg_internal.cuh"
+
+namespace rg {
+
+__device__ __forceinline__ float h_lo(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+__device__ __forceinline__ float h_hi(unsigned w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+
+// signed INT8 code j (0..47) of a 48-byte code block held in 12 words
+__device__ __forceinline__ float sh_code(const unsigned (&w)[12], int j)
+{
+    return (float)(((int)(w[j >> 2] << (24 - 8 * (j & 3)))) >> 24);
+}
+
+__device__ __forceinline__ int sh_band(int k) { return k == 0 ? 0 : (k < 4 ? 1 : (k < 9 ? 2 : 3)); }
+
+// two FP32 values rounded to FP16 (round to nearest even), packed low | high << 16
+__device__ __forceinline__ unsigned pack_h2(float lo, float hi)
+{
+    return (unsigned)__half_as_ushort(__float2half_rn(lo)) | ((unsigned)__half_as_ushort(__float2half_rn(hi)) << 16);
+}
+
+// ---------------------------------------------------------------------------
+// Fused front end (RoofGS)
+// ---------------------------------------------------------------------------
+constexpr int FE_THREADS = 256;
+
+__global__ void __launch_bounds__(FE_THREADS) k_frontend_fused(FrontendArgs a)
+{
+    __shared__ unsigned s_vb;
+    __shared__ unsigned s_wsum[FE_THREADS / 32];
+    __shared__ unsigned s_incl[FE_THREADS];
+    __shared__ int4 s_meta[FE_THREADS]; // tx0, ty0, width in tiles, q_d
+    __shared__ unsigned long long s_base;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
+    __syncthreads();
+    const unsigned vb = s_vb;
+    const long long i = (long long)vb * FE_THREADS + tid;
+
+    unsigned cnt = 0;
+    bool front = false;
+    int4 meta = make_int4(0, 0, 1, 0);
+    if (i < a.n) {
+        const float4 ga = __ldg(&a.geoA[i]); // mean, log o
+        const float pz = view_z(a.cam, ga.x, ga.y, ga.z);
+        // depth interval (Sec. IV-A.2) and opacity culling o >= 1/255
+        front = pz > a.cam.zn && pz <= a.cam.zf && ga.w >= -LN255F;
+        if (front) {
+            const uint4 gb = __ldg(&a.geoB[i]);
+            Binned b;
+            if (project_bin(a.cam, ga.x, ga.y, ga.z, pz, h_lo(gb.x), h_hi(gb.x), h_lo(gb.y), h_hi(gb.y), h_lo(gb.z),
+                            h_hi(gb.z), h_lo(gb.w), true, ga.w, b)) {
+                const int wt = b.tx1 - b.tx0 + 1;
+                cnt = (unsigned)(wt * (b.ty1 - b.ty0 + 1));
+                meta = make_int4(b.tx0, b.ty0, wt, (int)quantize_depth(pz, a.cam.zn, a.lay));
+                // conic in the paper's (a, b, c) of Eq. (10): b multiplies dx*dy
+                const float inv = 1.0f / b.det;
+                const float ca = b.sc * inv, cb = -2.0f * b.sb * inv, cc = b.sa * inv;
+                // INT8 SH (Eq. (8)) decoded in registers, evaluated per band
+                unsigned w[12];
+                {
+                    const uint4 p0 = __ldg(&a.shq[i]);
+                    const uint4 p1 = __ldg(&a.shq[a.n + i]);
+                    const uint4 p2 = __ldg(&a.shq[2 * a.n + i]);
+                    w[0] = p0.x; w[1] = p0.y; w[2] = p0.z; w[3] = p0.w;
+                    w[4] = p1.x; w[5] = p1.y; w[6] = p1.z; w[7] = p1.w;
+                    w[8] = p2.x; w[9] = p2.y; w[10] = p2.z; w[11] = p2.w;
+                }
+                float dx, dy, dz;
+                view_dir(a.cam, ga.x, ga.y, ga.z, dx, dy, dz);
+                float Y[16];
+                sh_basis(dx, dy, dz, Y);
+                float acc[4][3];
+#pragma unroll
+                for (int d = 0; d < 4; d++) acc[d][0] = acc[d][1] = acc[d][2] = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 16; k++)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ch++)
+                        acc[sh_band(k)][ch] = fmaf(Y[k], sh_code(w, 3 * k + ch), acc[sh_band(k)][ch]);
+                const float g = a.per_gauss_scale ? h_hi(gb.w) : 1.0f;
+                float rgb[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++) {
+                    float sum = a.band_scale[ch] * acc[0][ch];
+                    sum = fmaf(a.band_scale[3 + ch], acc[1][ch], sum);
+                    sum = fmaf(a.band_scale[6 + ch], acc[2][ch], sum);
+                    sum = fmaf(a.band_scale[9 + ch], acc[3][ch], sum);
+                    rgb[ch] = clamp01(fmaf(g, sum, 0.5f));
+                }
+                a.rec[2 * i] = make_float4(b.u, b.v, ca, cb);
+                a.rec[2 * i + 1] = make_float4(cc, ga.w, __uint_as_float(pack_h2(rgb[0], rgb[1])),
+                                               __uint_as_float(pack_h2(rgb[2], 0.0f)));
+            }
+        }
+    }
+    s_meta[tid] = meta;
+
+    // block-level inclusive prefix sum of the entry counts
+    const int lane = tid & 31, warp = tid >> 5;
+    unsigned x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    const int nfront = __syncthreads_count(front);
+    const int nvis = __syncthreads_count(cnt > 0);
+    if (warp == 0) {
+        unsigned ws = lane < FE_THREADS / 32 ? s_wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += y;
+        }
+        if (lane < FE_THREADS / 32) s_wsum[lane] = ws; // inclusive warp totals
+    }
+    __syncthreads();
+    const unsigned incl = x + (warp ? s_wsum[warp - 1] : 0u);
+    s_incl[tid] = incl;
+    const unsigned block_total = s_wsum[FE_THREADS / 32 - 1];
+
+    // one device-wide allocation per block, ordered by block
+    if (warp == 0) {
+        const unsigned long long base =
+            lookback_exclusive(a.status, vb, (unsigned long long)block_total, a.ctr, a.sticky, ERR_FE_LOOKBACK);
+        if (lane == 0) {
+            s_base = base;
+            if (nvis) atomicAdd(&a.ctr->n_visible, (unsigned)nvis);
+            if (nfront) atomicAdd(&a.ctr->n_front, (unsigned)nfront);
+            const unsigned nblocks = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
+            if (vb == nblocks - 1) {
+                const unsigned long long total = base + block_total;
+                a.ctr->n_entries_total = total;
+                a.ctr->n_entries = (unsigned)(total < (unsigned long long)a.cap ? total : (unsigned long long)a.cap);
+            }
+            if (base + block_total > (unsigned long long)a.cap) {
+                atomicOr(&a.ctr->overflow, 1u);
+                atomicOr(&a.sticky->overflow, 1u);
+            }
+        }
+    }
+    __syncthreads();
+    const unsigned long long base = s_base;
+
+    // cooperative emission: entry j of the block -> owner thread by binary search
+    const int b_d = a.lay.b_d;
+    const int tiles_x = a.lay.tiles_x;
+    for (unsigned j = tid; j < block_total; j += FE_THREADS) {
+        int pos = 0;
+#pragma unroll
+        for (int step = FE_THREADS / 2; step > 0; step >>= 1)
+            if (s_incl[pos + step - 1] <= j) pos += step;
+        const unsigned excl = pos ? s_incl[pos - 1] : 0u;
+        const unsigned local = j - excl;
+        const int4 m = s_meta[pos];
+        const unsigned r = local / (unsigned)m.z;
+        const unsigned tile = (unsigned)(m.y + (int)r) * (unsigned)tiles_x + (unsigned)(m.x + (int)(local - r * (unsigned)m.z));
+        const unsigned key = (b_d >= 32) ? (unsigned)m.w : ((tile << b_d) | (unsigned)m.w);
+        const unsigned long long dst = base + j;
+        if (dst < (unsigned long long)a.cap) {
+            a.keys[dst] = key;
+            a.vals[dst] = vb * FE_THREADS + (unsigned)pos;
+        }
+    }
+}
+
+void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s)
+{
+    if (a.n <= 0) return;
+    const unsigned blocks = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
+    k_frontend_fused<<<blocks, FE_THREADS, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Plain 3DGS front end (exact mode)
+// ---------------------------------------------------------------------------
+constexpr int EX_THREADS = 256;
+
+__global__ void __launch_bounds__(EX_THREADS) k_exact_preprocess(ExactArgs a)
+{
+    const long long i = (long long)blockIdx.x * EX_THREADS + threadIdx.x;
+    if (i >= a.n) return;
+    a.touched[i] = 0;
+    const float mx = a.means[3 * i], my = a.means[3 * i + 1], mz = a.means[3 * i + 2];
+    const float pz = view_z(a.cam, mx, my, mz);
+    const bool front = pz > a.cam.zn && pz <= a.cam.zf;
+    const unsigned fm = __ballot_sync(__activemask(), front);
+    if (front && __popc(fm & ((1u << (threadIdx.x & 31)) - 1u)) == 0) atomicAdd(&a.ctr->n_front, (unsigned)__popc(fm));
+    if (!front) return;
+    const float4 q = *reinterpret_cast<const float4*>(&a.quats[4 * i]);
+    Binned b;
+    if (!project_bin(a.cam, mx, my, mz, pz, q.x, q.y, q.z, q.w, a.scales[3 * i], a.scales[3 * i + 1],
+                     a.scales[3 * i + 2], false, 0.0f, b))
+        return;
+    const float inv = 1.0f / b.det;
+    // conic as plain 3DGS stores it: (inv00, inv01, inv11, opacity)
+    a.conic_op[i] = make_float4(b.sc * inv, -b.sb * inv, b.sa * inv, a.opac[i]);
+    a.xy[i] = make_float2(b.u, b.v);
+    a.depth[i] = pz;
+    a.rect[i] = make_int4(b.tx0, b.ty0, b.tx1, b.ty1);
+    a.touched[i] = (unsigned)((b.tx1 - b.tx0 + 1) * (b.ty1 - b.ty0 + 1));
+    // degree-3 SH colour from FP32 coefficients
+    float dx, dy, dz;
+    view_dir(a.cam, mx, my, mz, dx, dy, dz);
+    float Y[16];
+    sh_basis(dx, dy, dz, Y);
+    const int nk = (a.sh_degree + 1) * (a.sh_degree + 1);
+    const float4* shp = reinterpret_cast<const float4*>(a.sh + 48 * i);
+    float c[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int v4 = 0; v4 < 12; v4++) {
+        const float4 f = shp[v4];
+        const float e[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int j = 4 * v4 + u;
+            const int k = j / 3, ch = j % 3;
+            if (k < nk) c[ch] = fmaf(Y[k], e[u], c[ch]);
+        }
+    }
+    a.rgb[3 * i] = clamp01(c[0]);
+    a.rgb[3 * i + 1] = clamp01(c[1]);
+    a.rgb[3 * i + 2] = clamp01(c[2]);
+}
+
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = EX_THREADS * SCAN_ITEMS;
+
+// Exclusive scan of the tile counts (single pass, decoupled look-back).
+__global__ void __launch_bounds__(EX_THREADS) k_exact_scan(ExactArgs a)
+{
+    __shared__ unsigned s_vb;
+    __shared__ unsigned long long s_wsum[EX_THREADS / 32];
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
+    __syncthreads();
+    const unsigned vb = s_vb;
+    const long long start = (long long)vb * SCAN_TILE + (long long)tid * SCAN_ITEMS;
+    unsigned v[SCAN_ITEMS];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        v[k] = (start + k < a.n) ? a.touched[start + k] : 0u;
+        sum += v[k];
+    }
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long ws = lane < EX_THREADS / 32 ? s_wsum[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += y;
+        }
+        if (lane < EX_THREADS / 32) s_wsum[lane] = ws;
+    }
+    __syncthreads();
+    const unsigned long long block_total = s_wsum[EX_THREADS / 32 - 1];
+    if (warp == 0) {
+        const unsigned long long base = lookback_exclusive(a.status, vb, block_total, a.ctr, a.sticky, ERR_SCAN_LOOKBACK);
+        if (lane == 0) {
+            s_base = base;
+            const unsigned nblocks = (unsigned)((a.n + SCAN_TILE - 1) / SCAN_TILE);
+            if (vb == nblocks - 1) {
+                const unsigned long long total = base + block_total;
+                a.ctr->n_entries_total = total;
+                a.ctr->n_entries = (unsigned)(total < (unsigned long long)a.cap ? total : (unsigned long long)a.cap);
+                if (total > (unsigned long long)a.cap) {
+                    atomicOr(&a.ctr->overflow, 1u);
+                    atomicOr(&a.sticky->overflow, 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    unsigned long long run = s_base + (x - sum) + (warp ? s_wsum[warp - 1] : 0ull);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        if (start + k < a.n) a.offsets[start + k] = (unsigned)(run > 0xffffffffull ? 0xffffffffull : run);
+        run += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(EX_THREADS) k_exact_duplicate(ExactArgs a)
+{
+    const long long i = (long long)blockIdx.x * EX_THREADS + threadIdx.x;
+    if (i >= a.n) return;
+    const unsigned cnt = a.touched[i];
+    if (cnt == 0) return;
+    const unsigned long long off = a.offsets[i];
+    const int4 r = a.rect[i];
+    const unsigned long long zbits = (unsigned long long)__float_as_uint(a.depth[i]);
+    unsigned long long dst = off;
+    for (int ty = r.y; ty <= r.w; ty++)
+        for (int tx = r.x; tx <= r.z; tx++, dst++) {
+            if (dst >= (unsigned long long)a.cap) return;
+            const unsigned long long tile = (unsigned long long)(ty * a.lay.tiles_x + tx);
+            a.keys[dst] = (tile << 32) | zbits;
+            a.vals[dst] = (unsigned)i;
+        }
+}
+
+void launch_exact_preprocess(const ExactArgs& a, cudaStream_t s)
+{
+    if (a.n <= 0) return;
+    k_exact_preprocess<<<(unsigned)((a.n + EX_THREADS - 1) / EX_THREADS), EX_THREADS, 0, s>>>(a);
+}
+void launch_exact_scan(const ExactArgs& a, cudaStream_t s)
+{
+    if (a.n <= 0) return;
+    k_exact_scan<<<(unsigned)((a.n + SCAN_TILE - 1) / SCAN_TILE), EX_THREADS, 0, s>>>(a);
+}
+void launch_exact_duplicate(const ExactArgs& a, cudaStream_t s)
+{
+    if (a.n <= 0) return;
+    k_exact_duplicate<<<(unsigned)((a.n + EX_THREADS - 1) / EX_THREADS), EX_THREADS, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Scene conversion (one-off at scene creation)
+// ---------------------------------------------------------------------------
+__global__ void k_check_finite(const float* p, long long count, unsigned* flag)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < count; i += stride) bad |= !isfinite(p[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+void launch_check_finite(const float* p, long long count, unsigned* flag, cudaStream_t s)
+{
+    if (count <= 0) return;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_check_finite<<<(unsigned)blocks, 256, 0, s>>>(p, count, flag);
+}
+
+// max |SH| per (degree, channel): float bits of non-negative values order like integers
+__global__ void k_sh_absmax(const float* sh, long long n, unsigned* maxbits)
+{
+    __shared__ unsigned s_max[12];
+    if (threadIdx.x < 12) s_max[threadIdx.x] = 0u;
+    __syncthreads();
+    unsigned local[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) local[k] = 0u;
+    const long long total = n * 48;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(j % 48), k = e / 3, ch = e % 3;
+        const unsigned bits = __float_as_uint(fabsf(sh[j]));
+        const int slot = sh_band(k) * 3 + ch;
+#pragma unroll
+        for (int t = 0; t < 12; t++)
+            if (t == slot) local[t] = max(local[t], bits);
+    }
+#pragma unroll
+    for (int t = 0; t < 12; t++) atomicMax(&s_max[t], local[t]);
+    __syncthreads();
+    if (threadIdx.x < 12) atomicMax(&maxbits[threadIdx.x], s_max[threadIdx.x]);
+}
+
+void launch_sh_absmax(const float* sh, long long n, unsigned* maxbits, cudaStream_t s)
+{
+    if (n <= 0) return;
+    long long blocks = (n * 48 + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_sh_absmax<<<(unsigned)blocks, 256, 0, s>>>(sh, n, maxbits);
+}
+
+struct CompactParams {
+    float band_scale[12];
+    int per_gauss;
+};
+
+__global__ void k_compact(const float* means, const float* scales, const float* quats, const float* logo,
+                          const float* sh, long long n, CompactParams p, float4* geoA, uint4* geoB, uint4* shq)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* c = sh + 48 * i;
+    float g = 1.0f;
+    if (p.per_gauss) {
+        float gm = 0.0f;
+        for (int e = 0; e < 48; e++) {
+            const float s = p.band_scale[sh_band(e / 3) * 3 + e % 3];
+            const float den127 = __fmul_rn(127.0f, s);
+            const float r = den127 > 0.0f ? __fdiv_rn(fabsf(c[e]), den127) : 0.0f;
+            gm = fmaxf(gm, r);
+        }
+        g = __half2float(__float2half_rn(gm));
+    }
+    unsigned char codes[48];
+    for (int e = 0; e < 48; e++) {
+        const float s = p.band_scale[sh_band(e / 3) * 3 + e % 3];
+        const float den = p.per_gauss ? __fmul_rn(g, s) : s;
+        int q = 0;
+        if (den > 0.0f) {
+            q = __float2int_rn(__fdiv_rn(c[e], den));
+            q = max(-127, min(127, q));
+        }
+        codes[e] = (unsigned char)(signed char)q;
+    }
+    for (int pl = 0; pl < 3; pl++) {
+        unsigned w[4];
+        for (int k = 0; k < 4; k++)
+            w[k] = (unsigned)codes[16 * pl + 4 * k] | ((unsigned)codes[16 * pl + 4 * k + 1] << 8) |
+                   ((unsigned)codes[16 * pl + 4 * k + 2] << 16) | ((unsigned)codes[16 * pl + 4 * k + 3] << 24);
+        shq[pl * n + i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    geoA[i] = make_float4(means[3 * i], means[3 * i + 1], means[3 * i + 2], logo[i]);
+    geoB[i] = make_uint4(pack_h2(quats[4 * i], quats[4 * i + 1]), pack_h2(quats[4 * i + 2], quats[4 * i + 3]),
+                         pack_h2(scales[3 * i], scales[3 * i + 1]), pack_h2(scales[3 * i + 2], g));
+}
+
+void launch_compact(const float* means, const float* scales, const float* quats, const float* logo, const float* sh,
+                    long long n, const float* band_scale, int per_gauss, float4* geoA, uint4* geoB, uint4* shq,
+                    cudaStream_t s)
+{
+    if (n <= 0) return;
+    CompactParams p;
+    for (int k = 0; k < 12; k++) p.band_scale[k] = band_scale[k];
+    p.per_gauss = per_gauss;
+    k_compact<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(means, scales, quats, logo, sh, n, p, geoA, geoB, shq);
+}
+
+} // namespace rg

@@ -1,0 +1,258 @@
+// raster.cu -- tile rasterizers (one thread block per 16x16 tile).
+//
+// Front-to-back alpha blending of Sec. III-D, Eq. (7): for each pixel, over
+// the tile's depth-sorted Gaussians, alpha = min(0.99, o exp(p)) (Eqs. (10)-(12)),
+// pairs with alpha < 1/255 are skipped, the loop stops (without adding) once
+// the transmittance would fall below 1e-4, C += c alpha T, out = C + T bg.
+//
+// RoofGS mode (Sec. IV-B): while a batch of records is staged in shared
+// memory, each Gaussian's coefficients are folded (Eqs. (13)-(15)) --
+// -1/2 and log o absorbed, C1..C6 -- in TILE-LOCAL coordinates (pixel and mean
+// shifted by the tile origin, so the FP32 terms stay small at 4K); every
+// thread owns two vertically adjacent pixels (x, y) and (x, y+1): the first
+// exponent is the FMA chain of Eq. (16) on hoisted x^2, xy, y^2, x, y, the
+// second follows from Eq. (20). Pairs with P < -ln 255 are skipped before any
+// exponential (Eq. (23)); alpha = min(0.99, exp^(P)) with the bit-level
+// exponential of Eq. (24) (Eq. (25)). A warp whose pixels are all finished
+// skips the batch (vote); the block leaves once every pixel is finished.
+#include "rg_internal.cuh"
+
+namespace rg {
+
+// Eq. (24) evaluated in FP32: I = floor(P 2^23 log2 e + 2^23 (127 - sigma)).
+// With w = fma(P, log2 e, 127 - sigma) in [64, 128) (P in [-ln 255, 0]),
+// 2^23 * w is exactly the FP32 result of fma(P, 2^23 log2 e, 2^23 (127 - sigma))
+// (scaling by 2^23 commutes with rounding) and is an integer multiple of 64, so
+// I = 2^23 w = 2^29 + 64 * mantissa(w) = (bits(w) << 6) + 2^31 (mod 2^32):
+// one FFMA and one integer shift-add instead of a float->int conversion.
+__device__ __forceinline__ float fast_exp(float P)
+{
+    const float w = fmaf(P, 1.44269502f, 126.954323f);
+    return __uint_as_float((__float_as_uint(w) << 6) + 0x80000000u);
+}
+
+__global__ void k_fast_exp_eval(const float* P, float* out, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = fast_exp(P[i]);
+}
+
+constexpr int R_THREADS = 128;  // 128 threads x 2 pixels = one 16x16 tile
+
+template <bool FAST, bool COUNT>
+__device__ __forceinline__ void blend(float P, float r, float g, float b, float& T, float& c0, float& c1, float& c2,
+                                      bool& done, unsigned& n_eval, unsigned& n_blend)
+{
+    if (COUNT && !done) {
+        n_eval++;
+        if (P >= -LN255F) n_blend++;
+    }
+    if (!done && P >= -LN255F) {
+        const float e = FAST ? fast_exp(P) : expf(P);
+        const float alpha = fminf(0.99f, e);
+        const float Tn = T * (1.0f - alpha);
+        if (Tn < 1e-4f) {
+            done = true;
+        } else {
+            const float wgt = alpha * T;
+            c0 = fmaf(r, wgt, c0);
+            c1 = fmaf(g, wgt, c1);
+            c2 = fmaf(b, wgt, c2);
+            T = Tn;
+        }
+    }
+}
+
+// sums the per-thread work counters of a counting launch into the frame counters
+__device__ __forceinline__ void flush_counts(Counters* c, unsigned n_eval, unsigned n_blend)
+{
+    unsigned long long e = n_eval, b = n_blend;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&c->n_pairs, e);
+        atomicAdd(&c->n_blends, b);
+    }
+}
+
+template <bool FAST, bool DUAL, bool COUNT>
+__global__ void __launch_bounds__(DUAL ? R_THREADS : 256) k_raster_roofgs(RasterArgs a)
+{
+    constexpr int NT = DUAL ? R_THREADS : 256;
+    __shared__ float4 s_c0[NT];
+    __shared__ float4 s_c1[NT];
+    __shared__ float4 s_c2[NT];
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int x0 = tx * TILE, y0 = ty * TILE;
+    const int t = threadIdx.x;
+    const int lx = t & 15;
+    const int ly = DUAL ? (t >> 4) * 2 : (t >> 4);
+    const int px = x0 + lx, py = y0 + ly;
+    const int W = a.cam.W, H = a.cam.H;
+    bool done1 = !(px < W && py < H);
+    bool done2 = DUAL ? !(px < W && py + 1 < H) : true;
+    // hoisted pixel terms (tile-local)
+    const float x = (float)lx, y = (float)ly;
+    const float xx = x * x, xy = x * y, yy = y * y, y2p1 = 2.0f * y + 1.0f;
+    float T1 = 1.0f, T2 = 1.0f;
+    float r1 = 0.f, g1 = 0.f, b1 = 0.f, r2 = 0.f, g2 = 0.f, b2 = 0.f;
+    unsigned n_eval = 0, n_blend = 0;
+    const uint2 range = a.ranges[tile];
+    for (unsigned start = range.x; start < range.y; start += NT) {
+        if (__syncthreads_count(!(done1 && done2)) == 0) break;
+        const unsigned j = start + t;
+        if (j < range.y) {
+            unsigned id = a.vals[j];
+            if (id >= (unsigned long long)a.n) id = 0; // only after a failed (timed-out) sort
+            const float4 q0 = __ldg(&a.rec[2 * id]);
+            const float4 q1 = __ldg(&a.rec[2 * id + 1]);
+            const float u = q0.x - (float)x0, v = q0.y - (float)y0;
+            const float ca = q0.z, cb = q0.w, cc = q1.x, logo = q1.y;
+            // Eq. (15): folded coefficients
+            const float C1 = -0.5f * ca, C2 = -0.5f * cb, C3 = -0.5f * cc;
+            const float C4 = fmaf(ca, u, 0.5f * cb * v);
+            const float C5 = fmaf(cc, v, 0.5f * cb * u);
+            const float C0 = fmaf(ca * u, u, fmaf(cb * u, v, cc * v * v)); // Eq. (14)
+            const float C6 = fmaf(-0.5f, C0, logo);
+            const unsigned rg = __float_as_uint(q1.z), bb = __float_as_uint(q1.w);
+            const float cr = __half2float(__ushort_as_half((unsigned short)(rg & 0xffffu)));
+            const float cg = __half2float(__ushort_as_half((unsigned short)(rg >> 16)));
+            const float cbl = __half2float(__ushort_as_half((unsigned short)(bb & 0xffffu)));
+            s_c0[t] = make_float4(C1, C2, C3, C4);
+            s_c1[t] = make_float4(C5, C6, cr, cg);
+            s_c2[t] = make_float4(cbl, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        const int cnt = min((unsigned)NT, range.y - start);
+        if (!__all_sync(0xffffffffu, done1 && done2)) {
+            for (int k = 0; k < cnt; k++) {
+                const float4 c0 = s_c0[k];
+                const float4 c1 = s_c1[k];
+                const float cbl = s_c2[k].x;
+                // Eq. (16): P(x, y) = C1 x^2 + C2 xy + C3 y^2 + C4 x + C5 y + C6
+                const float P1 = fmaf(c0.x, xx, fmaf(c0.y, xy, fmaf(c0.z, yy, fmaf(c0.w, x, fmaf(c1.x, y, c1.y)))));
+                blend<FAST, COUNT>(P1, c1.z, c1.w, cbl, T1, r1, g1, b1, done1, n_eval, n_blend);
+                if (DUAL) {
+                    // Eq. (20): P(x, y+1) = P(x, y) + C2 x + C3 (2y + 1) + C5
+                    const float P2 = P1 + fmaf(c0.y, x, fmaf(c0.z, y2p1, c1.x));
+                    blend<FAST, COUNT>(P2, c1.z, c1.w, cbl, T2, r2, g2, b2, done2, n_eval, n_blend);
+                }
+            }
+        }
+    }
+    if (COUNT) flush_counts(a.count, n_eval, n_blend);
+    const size_t plane = (size_t)W * H;
+    if (px < W && py < H) {
+        const size_t o = (size_t)py * W + px;
+        a.out[o] = r1 + T1 * a.cam.bg[0];
+        a.out[plane + o] = g1 + T1 * a.cam.bg[1];
+        a.out[2 * plane + o] = b1 + T1 * a.cam.bg[2];
+    }
+    if (DUAL && px < W && py + 1 < H) {
+        const size_t o = (size_t)(py + 1) * W + px;
+        a.out[o] = r2 + T2 * a.cam.bg[0];
+        a.out[plane + o] = g2 + T2 * a.cam.bg[1];
+        a.out[2 * plane + o] = b2 + T2 * a.cam.bg[2];
+    }
+}
+
+template <bool COUNT>
+static void raster_roofgs_variant(const RasterArgs& a, cudaStream_t s)
+{
+    const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
+    if (a.dual_pixel) {
+        if (a.fast_exp) k_raster_roofgs<true, true, COUNT><<<tiles, R_THREADS, 0, s>>>(a);
+        else k_raster_roofgs<false, true, COUNT><<<tiles, R_THREADS, 0, s>>>(a);
+    } else {
+        if (a.fast_exp) k_raster_roofgs<true, false, COUNT><<<tiles, 256, 0, s>>>(a);
+        else k_raster_roofgs<false, false, COUNT><<<tiles, 256, 0, s>>>(a);
+    }
+}
+
+void launch_raster_roofgs(const RasterArgs& a, cudaStream_t s)
+{
+    if (a.count) raster_roofgs_variant<true>(a, s);
+    else raster_roofgs_variant<false>(a, s);
+}
+
+// Plain 3DGS rasterizer: one pixel per thread, expf, un-folded quadratic form.
+constexpr int E_THREADS = 256;
+
+template <bool COUNT>
+__global__ void __launch_bounds__(E_THREADS) k_raster_exact(RasterArgs a)
+{
+    __shared__ float2 s_xy[E_THREADS];
+    __shared__ float4 s_co[E_THREADS];
+    __shared__ float4 s_rgb[E_THREADS];
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int px = tx * TILE + (threadIdx.x & 15), py = ty * TILE + (threadIdx.x >> 4);
+    const int W = a.cam.W, H = a.cam.H;
+    const bool inside = px < W && py < H;
+    bool done = !inside;
+    const float fx = (float)px, fy = (float)py;
+    float T = 1.0f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    unsigned n_eval = 0, n_blend = 0;
+    const uint2 range = a.ranges[tile];
+    for (unsigned start = range.x; start < range.y; start += E_THREADS) {
+        if (__syncthreads_count(!done) == 0) break;
+        const unsigned j = start + threadIdx.x;
+        if (j < range.y) {
+            unsigned id = a.vals[j];
+            if (id >= (unsigned long long)a.n) id = 0; // only after a failed (timed-out) sort
+            s_xy[threadIdx.x] = a.xy[id];
+            s_co[threadIdx.x] = a.conic_op[id];
+            s_rgb[threadIdx.x] = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], 0.f);
+        }
+        __syncthreads();
+        const int cnt = min((unsigned)E_THREADS, range.y - start);
+        for (int k = 0; !done && k < cnt; k++) {
+            const float2 m = s_xy[k];
+            const float4 co = s_co[k];
+            const float dx = m.x - fx, dy = m.y - fy;
+            const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy; // Eq. (10)
+            if (COUNT) n_eval++;
+            if (power > 0.0f) continue;
+            const float alpha = fminf(0.99f, co.w * expf(power)); // Eqs. (11)-(12)
+            if (alpha < 1.0f / 255.0f) continue;
+            if (COUNT) n_blend++;
+            const float Tn = T * (1.0f - alpha);
+            if (Tn < 1e-4f) {
+                done = true;
+                continue;
+            }
+            const float4 c = s_rgb[k];
+            const float wgt = alpha * T;
+            c0 += c.x * wgt;
+            c1 += c.y * wgt;
+            c2 += c.z * wgt;
+            T = Tn;
+        }
+    }
+    if (COUNT) flush_counts(a.count, n_eval, n_blend);
+    if (inside) {
+        const size_t plane = (size_t)W * H, o = (size_t)py * W + px;
+        a.out[o] = c0 + T * a.cam.bg[0];
+        a.out[plane + o] = c1 + T * a.cam.bg[1];
+        a.out[2 * plane + o] = c2 + T * a.cam.bg[2];
+    }
+}
+
+void launch_raster_exact(const RasterArgs& a, cudaStream_t s)
+{
+    const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
+    if (a.count) k_raster_exact<true><<<tiles, E_THREADS, 0, s>>>(a);
+    else k_raster_exact<false><<<tiles, E_THREADS, 0, s>>>(a);
+}
+
+void launch_fast_exp_eval(const float* P, float* out, long long n, cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_fast_exp_eval<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, out, n);
+}
+
+} // namespace rg

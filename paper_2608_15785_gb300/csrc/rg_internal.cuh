@@ -1,0 +1,393 @@
+// rg_internal.cuh -- device-side types and helpers shared by the renderer's kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rg {
+
+constexpr int TILE = 16;                       // tile edge in pixels (16 x 16 tiles)
+constexpr float LN255F = 5.541263545158426f;   // ln 255: alpha = 1/255 in log space, Eq. (23)
+constexpr unsigned SPIN_LIMIT = 1u << 22;      // bounded device waits (x ~64 ns sleep)
+
+// Error bits of Counters::error / Sticky::error
+constexpr unsigned ERR_FE_LOOKBACK = 1u;
+constexpr unsigned ERR_SORT_LOOKBACK = 2u;
+constexpr unsigned ERR_SCAN_LOOKBACK = 4u;
+
+// Camera as the kernels see it (kernel parameter, uniform across threads).
+struct CamDev {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int W, H;
+    float zn, zf;
+    float bg[3];
+    float campos[3];  // camera centre -R^T t (for the SH view direction)
+    float limx, limy; // 1.3 * tan(half field of view), FP32 pinned: 1.3f * ((0.5f * W) / fx)
+};
+
+// Tile grid and resolution-adaptive key split (Sec. IV-A.2).
+struct Layout {
+    int tiles_x, tiles_y;
+    int b_t, b_d;
+    unsigned qmax;       // 2^b_d - 1
+    float depth_scale;   // fl32((2^b_d - 1) / (zf - zn)) computed in FP64
+};
+
+// Per-frame device counters (zeroed at the start of every frame).
+struct Counters {
+    unsigned long long n_entries_total; // entries the front end wanted to emit
+    unsigned n_entries;                 // entries present in the key arrays (<= capacity)
+    unsigned n_visible;
+    unsigned overflow;
+    unsigned error;
+    unsigned fe_block_ctr;   // virtual block ids of the fused front end / exact scan
+    unsigned sort_tile_ctr[8];
+    unsigned n_front;
+    unsigned pad;
+    unsigned long long n_pairs;  // rasterizer work counters (counting launches only)
+    unsigned long long n_blends;
+};
+
+// Sticky flags across frames (cleared by rg_scene_check).
+struct Sticky {
+    unsigned overflow;
+    unsigned error;
+};
+
+// Status word of the decoupled look-back (64-bit: 2 flag bits + 62-bit value).
+constexpr unsigned long long LB_AGG = 1ull << 62;
+constexpr unsigned long long LB_PRE = 2ull << 62;
+constexpr unsigned long long LB_VAL = (1ull << 62) - 1ull;
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p)
+{
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v)
+{
+    *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+
+// Single-pass decoupled look-back (warp-parallel). Called by all 32 lanes of ONE
+// warp of the block; returns the exclusive prefix of `aggregate` over all lower
+// virtual block ids in every lane. Waits are bounded: on time-out the error bit
+// is raised (sticky too) and the missing predecessors count as zero.
+__device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long long* status, unsigned vb,
+                                                                 unsigned long long aggregate, Counters* ctr,
+                                                                 Sticky* sticky, unsigned errbit)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    if (vb == 0) {
+        if (lane == 0) st_volatile_u64(&status[0], LB_PRE | aggregate);
+        return 0ull;
+    }
+    if (lane == 0) st_volatile_u64(&status[vb], LB_AGG | aggregate);
+    unsigned long long excl = 0ull;
+    long long top = (long long)vb - 1;
+    bool timed_out = false;
+    while (true) {
+        long long idx = top - (long long)lane;
+        unsigned long long s = LB_PRE; // before block 0: prefix 0
+        if (idx >= 0) {
+            unsigned spins = 0;
+            s = ld_volatile_u64(&status[idx]);
+            while ((s >> 62) == 0ull) {
+                if (++spins > SPIN_LIMIT) {
+                    timed_out = true;
+                    s = LB_PRE;
+                    break;
+                }
+                __nanosleep(64);
+                s = ld_volatile_u64(&status[idx]);
+            }
+        }
+        const unsigned pmask = __ballot_sync(0xffffffffu, (s >> 62) == 2ull);
+        const int stop = pmask ? (__ffs(pmask) - 1) : 32;
+        unsigned long long v = ((int)lane <= stop) ? (s & LB_VAL) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (pmask) break;
+        top -= 32;
+    }
+    if (__any_sync(0xffffffffu, timed_out) && lane == 0) {
+        atomicOr(&ctr->error, errbit);
+        atomicOr(&sticky->error, errbit);
+    }
+    if (lane == 0) st_volatile_u64(&status[vb], LB_PRE | (excl + aggregate));
+    return excl;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 pinned-order projection and binning (every step one IEEE operation;
+// the CPU oracle evaluates the same sequence, so culling, tile rectangles and
+// keys are bit-exact).
+// ---------------------------------------------------------------------------
+struct Binned {
+    float z, u, v;
+    float sa, sb, sc;   // Sigma' = [[sa, sb], [sb, sc]] including the 0.3 dilation
+    float det;          // det Sigma' (Lagrange form, not pinned)
+    int tx0, ty0, tx1, ty1;
+};
+
+#define FM(a, b) __fmul_rn((a), (b))
+#define FA(a, b) __fadd_rn((a), (b))
+#define FS(a, b) __fsub_rn((a), (b))
+#define FD(a, b) __fdiv_rn((a), (b))
+
+__device__ __forceinline__ float view_z(const CamDev& c, float mx, float my, float mz)
+{
+    return FA(FA(FA(FM(c.R[6], mx), FM(c.R[7], my)), FM(c.R[8], mz)), c.t[2]);
+}
+
+// Projection, EWA covariance, box and tile rectangle. snug = RoofGS box (exact
+// alpha = 1/255 ellipse, needs log o) else the 3-sigma box of plain 3DGS.
+// Returns false if culled or if the rectangle is empty. pz has been computed
+// by view_z and passed the depth-interval test.
+__device__ __forceinline__ bool project_bin(const CamDev& c, float mx, float my, float mz, float pz, float qw,
+                                            float qx, float qy, float qz, float s0, float s1, float s2, bool snug,
+                                            float logo, Binned& b)
+{
+    const float px = FA(FA(FA(FM(c.R[0], mx), FM(c.R[1], my)), FM(c.R[2], mz)), c.t[0]);
+    const float py = FA(FA(FA(FM(c.R[3], mx), FM(c.R[4], my)), FM(c.R[5], mz)), c.t[1]);
+    b.z = pz;
+    const float n2 = FA(FA(FA(FM(qw, qw), FM(qx, qx)), FM(qy, qy)), FM(qz, qz));
+    if (!(n2 > 0.0f)) return false;
+    const float rn = __fsqrt_rn(n2);
+    const float w = FD(qw, rn), x = FD(qx, rn), y = FD(qy, rn), z = FD(qz, rn);
+    const float xx = FM(x, x), yy = FM(y, y), zz = FM(z, z);
+    const float xy = FM(x, y), xz = FM(x, z), yz = FM(y, z);
+    const float wx = FM(w, x), wy = FM(w, y), wz = FM(w, z);
+    float Q[9];
+    Q[0] = FS(1.0f, FM(2.0f, FA(yy, zz)));
+    Q[1] = FM(2.0f, FS(xy, wz));
+    Q[2] = FM(2.0f, FA(xz, wy));
+    Q[3] = FM(2.0f, FA(xy, wz));
+    Q[4] = FS(1.0f, FM(2.0f, FA(xx, zz)));
+    Q[5] = FM(2.0f, FS(yz, wx));
+    Q[6] = FM(2.0f, FS(xz, wy));
+    Q[7] = FM(2.0f, FA(yz, wx));
+    Q[8] = FS(1.0f, FM(2.0f, FA(xx, yy)));
+    const float s[3] = {s0, s1, s2};
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) M[3 * i + k] = FM(Q[3 * i + k], s[k]);
+
+    const float xzr = FD(px, pz), yzr = FD(py, pz);
+    const float cxz = fminf(c.limx, fmaxf(-c.limx, xzr));
+    const float cyz = fminf(c.limy, fmaxf(-c.limy, yzr));
+    const float j00 = FD(c.fx, pz), j11 = FD(c.fy, pz);
+    const float j02 = -FM(j00, cxz), j12 = -FM(j11, cyz);
+    float A[6];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        A[k] = FA(FM(j00, c.R[k]), FM(j02, c.R[6 + k]));
+        A[3 + k] = FA(FM(j11, c.R[3 + k]), FM(j12, c.R[6 + k]));
+    }
+    float U[6];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            U[3 * i + k] = FA(FA(FM(A[3 * i], M[k]), FM(A[3 * i + 1], M[3 + k])), FM(A[3 * i + 2], M[6 + k]));
+    const float n0 = FA(FA(FM(U[0], U[0]), FM(U[1], U[1])), FM(U[2], U[2]));
+    const float n1 = FA(FA(FM(U[3], U[3]), FM(U[4], U[4])), FM(U[5], U[5]));
+    const float sa = FA(n0, 0.3f);
+    const float sc = FA(n1, 0.3f);
+    const float sb = FA(FA(FM(U[0], U[3]), FM(U[1], U[4])), FM(U[2], U[5]));
+    const float u = FA(FM(c.fx, xzr), c.cx);
+    const float v = FA(FM(c.fy, yzr), c.cy);
+    float rx, ry;
+    if (!snug) {
+        const float h = FM(0.5f, FS(sa, sc));
+        const float disc = __fsqrt_rn(FA(FM(h, h), FM(sb, sb)));
+        const float lmax = FA(FM(0.5f, FA(sa, sc)), disc);
+        rx = ry = ceilf(FM(3.0f, __fsqrt_rn(lmax)));
+    } else {
+        const float tt = FM(2.0f, FA(logo, LN255F));
+        rx = __fsqrt_rn(FM(tt, sa));
+        ry = __fsqrt_rn(FM(tt, sc));
+    }
+    b.u = u;
+    b.v = v;
+    b.sa = sa;
+    b.sb = sb;
+    b.sc = sc;
+    if (!isfinite(u) || !isfinite(v) || !isfinite(rx) || !isfinite(ry)) return false;
+    const float xl = fmaxf(ceilf(FS(u, rx)), 0.0f);
+    const float xh = fminf(floorf(FA(u, rx)), (float)(c.W - 1));
+    const float yl = fmaxf(ceilf(FS(v, ry)), 0.0f);
+    const float yh = fminf(floorf(FA(v, ry)), (float)(c.H - 1));
+    if (xl > xh || yl > yh) return false;
+    b.tx0 = (int)xl / TILE;
+    b.tx1 = (int)xh / TILE;
+    b.ty0 = (int)yl / TILE;
+    b.ty1 = (int)yh / TILE;
+    // det Sigma' = |U0 x U1|^2 + 0.3 (|U0|^2 + |U1|^2) + 0.09 (Lagrange identity:
+    // no cancellation for thin Gaussians). Not part of the pinned path.
+    const float cx0 = U[1] * U[5] - U[2] * U[4];
+    const float cx1 = U[2] * U[3] - U[0] * U[5];
+    const float cx2 = U[0] * U[4] - U[1] * U[3];
+    b.det = (cx0 * cx0 + cx1 * cx1 + cx2 * cx2) + 0.3f * (n0 + n1) + 0.09f;
+    return true;
+}
+
+// Quantized depth of Eq. (9): clamp(floor((d - zn) * (2^b_d - 1) / (zf - zn)), 0, 2^b_d - 1)
+__device__ __forceinline__ unsigned quantize_depth(float pz, float zn, const Layout& L)
+{
+    float dq = FM(FS(pz, zn), L.depth_scale);
+    dq = fmaxf(dq, 0.0f);
+    const float fq = floorf(dq);
+    return (fq >= (float)L.qmax) ? L.qmax : (unsigned)fq;
+}
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics, degree <= 3, index k = l^2 + l + m, no
+// Condon-Shortley phase (Y_{1,-1}, Y_{1,0}, Y_{1,1} are positive multiples of
+// y, z, x).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16])
+{
+    Y[0] = 0.28209479177387814f;
+    Y[1] = 0.4886025119029199f * y;
+    Y[2] = 0.4886025119029199f * z;
+    Y[3] = 0.4886025119029199f * x;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = 1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);
+    Y[7] = 1.0925484305920792f * x * z;
+    Y[8] = 0.5462742152960396f * (xx - yy);
+    Y[9] = 0.5900435899266435f * y * (3.0f * xx - yy);
+    Y[10] = 2.890611442640554f * x * y * z;
+    Y[11] = 0.4570457994644658f * y * (5.0f * zz - 1.0f);
+    Y[12] = 0.3731763325901154f * z * (5.0f * zz - 3.0f);
+    Y[13] = 0.4570457994644658f * x * (5.0f * zz - 1.0f);
+    Y[14] = 1.445305721320277f * z * (xx - yy);
+    Y[15] = 0.5900435899266435f * x * (xx - 3.0f * yy);
+}
+
+__device__ __forceinline__ void view_dir(const CamDev& c, float mx, float my, float mz, float& dx, float& dy,
+                                         float& dz)
+{
+    dx = mx - c.campos[0];
+    dy = my - c.campos[1];
+    dz = mz - c.campos[2];
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv;
+    dy *= inv;
+    dz *= inv;
+}
+
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files).
+// ---------------------------------------------------------------------------
+struct FrontendArgs {
+    const float4* geoA;    // [N] (mean.xyz, log o)
+    const uint4* geoB;     // [N] FP16 (qw,qx | qy,qz | s0,s1 | s2,g)
+    const uint4* shq;      // [3][N] INT8 SH codes, 48 bytes per Gaussian in 3 planes
+    float band_scale[12];  // s_{d,c}, [d][c]
+    int per_gauss_scale;
+    int sh_degree;
+    long long n;
+    CamDev cam;
+    Layout lay;
+    float4* rec;           // [N][2] raster record
+    unsigned* keys;        // [cap]
+    unsigned* vals;        // [cap]
+    long long cap;
+    unsigned long long* status; // [ceil(N/256)]
+    Counters* ctr;
+    Sticky* sticky;
+};
+void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s);
+
+struct ExactArgs {
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opac;
+    const float* sh;
+    int sh_degree;
+    long long n;
+    CamDev cam;
+    Layout lay;
+    float2* xy;
+    float* depth;
+    float4* conic_op;
+    float* rgb;            // [N][3]
+    int4* rect;            // [N] tx0, ty0, tx1, ty1
+    unsigned* touched;     // [N]
+    unsigned* offsets;     // [N] exclusive scan of touched
+    unsigned long long* keys; // [cap]
+    unsigned* vals;
+    long long cap;
+    unsigned long long* status; // scan look-back
+    Counters* ctr;
+    Sticky* sticky;
+};
+void launch_exact_preprocess(const ExactArgs& a, cudaStream_t s);
+void launch_exact_scan(const ExactArgs& a, cudaStream_t s);
+void launch_exact_duplicate(const ExactArgs& a, cudaStream_t s);
+
+struct SortArgs {
+    void* keys[2];        // ping-pong key buffers (uint32 or uint64)
+    unsigned* vals[2];
+    long long cap;
+    int key_bytes;        // 4 or 8
+    int passes;           // 8-bit digits from bit 0
+    unsigned* hist;       // [8][256]
+    unsigned* status[2];  // [max_tiles][256] look-back status per pass (alternating)
+    long long max_tiles;
+    Counters* ctr;
+    Sticky* sticky;
+};
+int sort_tile_items();
+void launch_sort(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hist);
+
+struct RangeArgs {
+    const void* keys;
+    int key_bytes;
+    int tile_shift;  // key >> tile_shift = tile id
+    long long ntiles;
+    uint2* ranges;
+    Counters* ctr;
+};
+void launch_ranges(const RangeArgs& a, cudaStream_t s);
+
+struct RasterArgs {
+    const uint2* ranges;
+    const unsigned* vals;
+    long long n;          // Gaussians (values are indices below n)
+    int tiles_x, tiles_y;
+    CamDev cam;
+    float* out;           // [3][H][W]
+    // RoofGS
+    const float4* rec;
+    int fast_exp;
+    int dual_pixel;
+    // exact
+    const float2* xy;
+    const float4* conic_op;
+    const float* rgb;
+    Counters* count;      // non-null: count evaluated / blended pairs (separate kernel variant)
+};
+void launch_raster_roofgs(const RasterArgs& a, cudaStream_t s);
+void launch_raster_exact(const RasterArgs& a, cudaStream_t s);
+void launch_fast_exp_eval(const float* P, float* out, long long n, cudaStream_t s);
+
+// Scene creation kernels
+void launch_check_finite(const float* p, long long count, unsigned* flag, cudaStream_t s);
+void launch_sh_absmax(const float* sh, long long n, unsigned* maxbits /*[12]*/, cudaStream_t s);
+void launch_compact(const float* means, const float* scales, const float* quats, const float* logo,
+                    const float* sh, long long n, const float* band_scale /*host [12]*/, int per_gauss,
+                    float4* geoA, uint4* geoB, uint4* shq, cudaStream_t s);
+
+} // namespace rg

@@ -1,0 +1,278 @@
+// sort.cu -- stable LSD radix sort of (key, value) entries and per-tile ranges.
+//
+// Depth sort of Sec. III-C / Sec. IV-A.2: traffic ~ S_kv * N_dup * N_pass
+// (Eq. (6)). 8-bit digits; 4 passes for the 32-bit RoofGS key and
+// ceil((32 + b_t) / 8) passes for the 64-bit exact-mode key (only the bits
+// that can be non-zero are sorted).
+//
+// One histogram kernel reads every key once and counts the digits of all
+// passes. Each pass is then ONE kernel over tiles of 4096 entries (one-sweep
+// scheme): a persistent grid takes tiles in order from an atomic counter,
+// ranks the tile's digits in shared memory (per-warp counters with match_any,
+// stable), publishes its per-digit counts, obtains the counts of all earlier
+// tiles by decoupled look-back (bounded waits), reorders the tile in shared
+// memory by digit and writes each digit run to its global position (runs of
+// consecutive addresses). Per pass every entry is read once and written once.
+// The number of entries is read on the device: no host round trip.
+#include "rg_internal.cuh"
+
+namespace rg {
+
+constexpr int S_THREADS = 256;
+constexpr int S_KPT = 16;
+constexpr int S_TILE = S_THREADS * S_KPT; // 4096 entries
+constexpr int S_WARPS = S_THREADS / 32;
+constexpr int RADIX = 256;
+constexpr unsigned SF_AGG = 1u << 30, SF_PRE = 2u << 30, SF_VAL = (1u << 30) - 1u;
+
+int sort_tile_items() { return S_TILE; }
+
+template <typename K>
+__global__ void __launch_bounds__(S_THREADS) k_sort_hist(const K* __restrict__ keys, int passes, unsigned* hist,
+                                                         unsigned* status0, const Counters* __restrict__ ctr)
+{
+    __shared__ unsigned s_h[8][RADIX];
+    for (int j = threadIdx.x; j < 8 * RADIX; j += S_THREADS) (&s_h[0][0])[j] = 0u;
+    __syncthreads();
+    const long long n = ctr->n_entries;
+    const long long ntiles = (n + S_TILE - 1) / S_TILE;
+    const long long gsz = (long long)gridDim.x * S_THREADS;
+    const long long gid = (long long)blockIdx.x * S_THREADS + threadIdx.x;
+    // clear the look-back status words of the first pass
+    for (long long j = gid; j < ntiles * RADIX; j += gsz) status0[j] = 0u;
+    for (long long j = gid; j < n; j += gsz) {
+        const K k = keys[j];
+        for (int p = 0; p < passes; p++) atomicAdd(&s_h[p][(unsigned)(k >> (8 * p)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < passes * RADIX; j += S_THREADS) {
+        const unsigned c = (&s_h[0][0])[j];
+        if (c) atomicAdd(&hist[j], c);
+    }
+}
+
+// exclusive scan of one value per thread over the 256 threads of the block
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* s_w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned w = lane < S_WARPS ? s_w[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < S_WARPS) s_w[lane] = w;
+    }
+    __syncthreads();
+    return x - v + (warp ? s_w[warp - 1] : 0u);
+}
+
+template <typename K>
+struct SortSmem {
+    K keys[S_TILE];
+    unsigned vals[S_TILE];
+    unsigned whist[S_WARPS][RADIX]; // per-warp digit counters, then per-warp exclusive offsets
+    unsigned goff[RADIX];           // global exclusive digit offsets of this pass
+    unsigned loff[RADIX];           // tile-local exclusive digit offsets
+    unsigned gbase[RADIX];          // global start of this tile's run of each digit
+    unsigned scan[S_WARPS];
+    unsigned tile;
+};
+
+template <typename K>
+__global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ kin, const unsigned* __restrict__ vin,
+                                                        K* __restrict__ kout, unsigned* __restrict__ vout, int pass,
+                                                        const unsigned* __restrict__ hist, unsigned* status,
+                                                        unsigned* status_next, Counters* ctr, Sticky* sticky)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int shift = 8 * pass;
+    const long long n = ctr->n_entries;
+    const long long ntiles = (n + S_TILE - 1) / S_TILE;
+    {
+        const unsigned h = hist[pass * RADIX + tid];
+        S.goff[tid] = block_exclusive_scan(h, S.scan);
+    }
+    const unsigned lt_mask = (1u << lane) - 1u;
+    while (true) {
+        if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
+#pragma unroll
+        for (int w = 0; w < S_WARPS; w++) S.whist[w][tid] = 0u;
+        __syncthreads();
+        const long long tile = S.tile;
+        if (tile >= ntiles) break;
+
+        // load the tile warp-striped: element = tile*TILE + warp*32*KPT + i*32 + lane
+        const long long e0 = tile * S_TILE + (long long)warp * 32 * S_KPT + lane;
+        K k[S_KPT];
+        unsigned v[S_KPT];
+#pragma unroll
+        for (int i = 0; i < S_KPT; i++) {
+            const long long e = e0 + 32 * i;
+            const bool ok = e < n;
+            k[i] = ok ? kin[e] : (K)~(K)0; // padding sorts last (digit 255, after the valid ones)
+            v[i] = ok ? vin[e] : 0u;
+        }
+        // stable rank of each element among the warp's elements of the same digit
+        unsigned rank[S_KPT];
+#pragma unroll
+        for (int i = 0; i < S_KPT; i++) {
+            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            unsigned b = 0;
+            if (lane == leader) {
+                b = S.whist[warp][d];
+                S.whist[warp][d] = b + __popc(peers);
+            }
+            b = __shfl_sync(0xffffffffu, b, leader);
+            rank[i] = b + __popc(peers & lt_mask);
+            __syncwarp();
+        }
+        __syncthreads();
+        // digit tid: tile count and per-warp exclusive offsets
+        unsigned count = 0;
+#pragma unroll
+        for (int w = 0; w < S_WARPS; w++) {
+            const unsigned c = S.whist[w][tid];
+            S.whist[w][tid] = count;
+            count += c;
+        }
+        // publish, look back over earlier tiles, publish the inclusive prefix
+        unsigned* st = status + tile * RADIX + tid;
+        unsigned excl = 0;
+        if (tile == 0) {
+            *reinterpret_cast<volatile unsigned*>(st) = SF_PRE | count;
+        } else {
+            *reinterpret_cast<volatile unsigned*>(st) = SF_AGG | count;
+            long long t = tile - 1;
+            bool timed_out = false;
+            while (t >= 0) {
+                unsigned s = *reinterpret_cast<volatile unsigned*>(status + t * RADIX + tid);
+                unsigned spins = 0;
+                while ((s >> 30) == 0u) {
+                    if (++spins > SPIN_LIMIT) {
+                        timed_out = true;
+                        s = SF_PRE;
+                        break;
+                    }
+                    __nanosleep(32);
+                    s = *reinterpret_cast<volatile unsigned*>(status + t * RADIX + tid);
+                }
+                excl += s & SF_VAL;
+                if ((s >> 30) == 2u) break;
+                t--;
+            }
+            if (timed_out) {
+                atomicOr(&ctr->error, ERR_SORT_LOOKBACK);
+                atomicOr(&sticky->error, ERR_SORT_LOOKBACK);
+            }
+            *reinterpret_cast<volatile unsigned*>(st) = SF_PRE | ((excl + count) & SF_VAL);
+        }
+        S.gbase[tid] = S.goff[tid] + excl;
+        if (status_next) status_next[tile * RADIX + tid] = 0u;
+        S.loff[tid] = block_exclusive_scan(count, S.scan);
+        __syncthreads();
+        // reorder the tile by digit in shared memory
+#pragma unroll
+        for (int i = 0; i < S_KPT; i++) {
+            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+            const unsigned pos = S.loff[d] + S.whist[warp][d] + rank[i];
+            S.keys[pos] = k[i];
+            S.vals[pos] = v[i];
+        }
+        __syncthreads();
+        const long long rem = n - tile * S_TILE;
+        const int valid = rem < S_TILE ? (int)rem : S_TILE;
+        for (int j = tid; j < valid; j += S_THREADS) {
+            const K kk = S.keys[j];
+            const unsigned d = (unsigned)(kk >> shift) & 0xffu;
+            const unsigned dst = S.gbase[d] + (unsigned)j - S.loff[d];
+            if (dst < (unsigned long long)n) { // always true unless a bounded wait gave up
+                kout[dst] = kk;
+                vout[dst] = S.vals[j];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename K>
+static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hist)
+{
+    static int grid = 0;
+    const size_t smem = sizeof(SortSmem<K>);
+    if (grid == 0) {
+        cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0, sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K>, S_THREADS, smem);
+        grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    int hist_grid = 0;
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        hist_grid = 4 * (sms > 0 ? sms : 1);
+    }
+    const K* kin = (const K*)a.keys[0];
+    k_sort_hist<K><<<hist_grid, S_THREADS, 0, s>>>(kin, a.passes, a.hist, a.status[0], a.ctr);
+    if (ev_after_hist) cudaEventRecord(ev_after_hist, s);
+    for (int p = 0; p < a.passes; p++) {
+        const int src = p & 1, dst = src ^ 1;
+        unsigned* nxt = (p + 1 < a.passes) ? a.status[(p + 1) & 1] : nullptr;
+        k_onesweep<K><<<grid, S_THREADS, smem, s>>>((const K*)a.keys[src], a.vals[src], (K*)a.keys[dst], a.vals[dst], p,
+                                                    a.hist, a.status[p & 1], nxt, a.ctr, a.sticky);
+    }
+}
+
+void launch_sort(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hist)
+{
+    if (a.key_bytes == 4) sort_impl<unsigned>(a, s, ev_after_hist);
+    else sort_impl<unsigned long long>(a, s, ev_after_hist);
+}
+
+// ---------------------------------------------------------------------------
+// Per-tile [start, end) ranges of the sorted entries (ranges zeroed beforehand).
+// ---------------------------------------------------------------------------
+template <typename K>
+__global__ void k_ranges(const K* __restrict__ keys, int tile_shift, long long ntiles, uint2* ranges,
+                         const Counters* __restrict__ ctr)
+{
+    const long long n = ctr->n_entries;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long t = (unsigned long long)keys[i] >> tile_shift;
+        if (t >= (unsigned long long)ntiles) continue; // only after a failed (timed-out) sort
+        if (i == 0 || ((unsigned long long)keys[i - 1] >> tile_shift) != t) ranges[t].x = (unsigned)i;
+        if (i == n - 1 || ((unsigned long long)keys[i + 1] >> tile_shift) != t) ranges[t].y = (unsigned)(i + 1);
+    }
+}
+
+void launch_ranges(const RangeArgs& a, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = 8 * (sms > 0 ? sms : 1);
+    if (a.key_bytes == 4)
+        k_ranges<unsigned><<<grid, 256, 0, s>>>((const unsigned*)a.keys, a.tile_shift, a.ntiles, a.ranges, a.ctr);
+    else
+        k_ranges<unsigned long long><<<grid, 256, 0, s>>>((const unsigned long long*)a.keys, a.tile_shift, a.ntiles,
+                                                          a.ranges, a.ctr);
+}
+
+} // namespace rg

@@ -1,0 +1,89 @@
+"""Host-side checks of the C ABI (CPU only, no GPU compute).
+
+The library must build for sm_103a, load, export every entry point that
+include/rg.h declares, and reject bad arguments before touching the GPU.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2608_15785_gb300 import binding
+from paper_2608_15785_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return binding.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["rg_scene_create", "rg_scene_destroy", "rg_render", "rg_render_batch", "rg_backward",
+                 "rg_submit", "rg_poll", "rg_last_error"]:
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert sorted(binding.EXPORTS) == names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version_and_error_string(L):
+    assert L.rg_version() == 100
+    assert isinstance(L.rg_last_error(), bytes)
+
+
+def test_bad_arguments_are_rejected_without_a_gpu(L):
+    out = C.c_void_p()
+    assert L.rg_scene_create(None, None, C.byref(out)) == 1  # RG_ERR_INVALID_ARG
+    assert b"NULL" in L.rg_last_error()
+    d = binding.RgSceneDesc()
+    d.n = -5
+    assert L.rg_scene_create(C.byref(d), None, C.byref(out)) == 1
+    d.n, d.sh_degree = 10, 4
+    assert L.rg_scene_create(C.byref(d), None, C.byref(out)) == 1
+    d.sh_degree = 3
+    assert L.rg_scene_create(C.byref(d), None, C.byref(out)) == 1  # NULL attribute pointers
+    assert L.rg_render(None, None, None, None, None, None) == 1
+    assert L.rg_render_batch(None, None, None, 0, None, None, None) == 8  # RG_ERR_UNSUPPORTED
+    assert L.rg_backward(None, None, None, None, None, None) == 8
+    assert L.rg_submit(None, None, 0, None) == 8
+    assert L.rg_poll(None, 0, None) == 8
+    assert L.rg_eval_fast_exp(None, None, -1, None) == 1
+    assert L.rg_stage_times(None, None, None) == 1
+    assert L.rg_scene_destroy(None) == 0
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors of the public structs have the C compiler's sizes and offsets."""
+    import subprocess
+    structs = {"rg_camera": binding.RgCamera, "rg_scene_desc": binding.RgSceneDesc,
+               "rg_render_opts": binding.RgOpts, "rg_stats": binding.RgStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rg.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%%s %%zu\\n", "%s", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%%s.%%s %%zu\\n", "%s", "%s", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)

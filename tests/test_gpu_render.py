@@ -1,0 +1,334 @@
+"""GPU parity of the renderer (through the C ABI) against the CPU oracle.
+
+Bars (see the tolerance helper below):
+  * bit-exact: compact attributes (FP16 geometry, log o, INT8 SH codes and
+    scales), the bit-level exponential, sorted keys/values and tile ranges;
+  * exact mode: |GPU - FP64 oracle| <= 2e-4 per channel, plus, on the pixels
+    where a single-precision renderer cannot reach 2e-4, the oracle's
+    first-order FP32 error bound (diag[0]) and the colour jump of a skip/stop
+    decision that lies within rounding of its threshold (diag[1], diag[2]);
+    the share of pixels that need any allowance is asserted to be small;
+  * RoofGS mode: within eps_max = 0.0312 (the measured bound of Eq. (24)) of
+    the oracle with exact exp, within 2e-4 + FP16 colour rounding of the
+    oracle that evaluates Eq. (24) in FP32, and >= 46.4 dB PSNR against exact
+    mode (0.05 dB against a 27 dB reference error).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_15785_gb300 import binding, synth
+from tests._helpers import single_scene, small_random_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-4
+HALF_COLOUR = 2.0 ** -12  # FP16 rounding of a colour in [0, 1] (RoofGS raster record)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_15785_gb300.build import build
+    build()
+
+
+def gpu_scene(sc, per_gauss=False):
+    return binding.Scene(sc, sh_scale_mode=binding.RG_SH_SCALE_BAND_GAUSS if per_gauss else binding.RG_SH_SCALE_BAND)
+
+
+def render(gs, cam, mode, flags=0, stats=False):
+    out = gs.render(cam, mode=mode, flags=flags, stats=stats)
+    torch.cuda.synchronize()
+    if stats:
+        return out[0].cpu().numpy().astype(np.float64), out[1]
+    return out.cpu().numpy().astype(np.float64)
+
+
+def allowance(diag):
+    return 4.0 * diag[..., 0] + diag[..., 1] + diag[..., 2]
+
+
+def assert_close(img, ref, diag, base, max_flagged=0.01, label=""):
+    tol = base + allowance(diag)
+    err = np.abs(img - ref)
+    bad = err > tol[None]
+    flagged = np.mean(allowance(diag) > 0.1 * TOL)
+    assert not bad.any(), "%s: %d values over tolerance, worst %.3g (tol %.3g)" % (
+        label, int(bad.sum()), float((err - tol[None]).max()), float(tol[None].repeat(3, 0)[bad].min()))
+    assert flagged <= max_flagged, "%s: %.3f of pixels needed an FP32 allowance" % (label, flagged)
+    return float(err.max()), float(flagged)
+
+
+def psnr(a, b):
+    mse = float(np.mean((a - b) ** 2))
+    return float("inf") if mse == 0 else -10 * math.log10(mse)
+
+
+# ---------------------------------------------------------------------------
+# bit-exact pieces
+# ---------------------------------------------------------------------------
+
+def test_fast_exp_bit_exact_against_fp32_formula():
+    lo = np.float32(-oracle.LN255)
+    a = np.uint32(np.float32(-0.0).view(np.uint32))
+    b = np.uint32(lo.view(np.uint32))
+    # every 7th FP32 value of [-ln 255, 0] plus the end points
+    P = np.concatenate([np.arange(a, b + 1, 7, dtype=np.uint32).view(np.float32), [lo, np.float32(0)]])
+    got = binding.eval_fast_exp(torch.from_numpy(P).cuda()).cpu().numpy()
+    ref = oracle.fast_exp_many(P.astype(np.float64), oracle.EXP_FAST32).astype(np.float32)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("per_gauss", [False, True])
+def test_compact_attributes_bit_exact(per_gauss):
+    sc = synth.tiny_scene(20_000, seed=5)
+    gs = gpu_scene(sc, per_gauss)
+    comp = oracle.compact(sc, per_gauss)
+    codes = gs.inspect(binding.RG_INSPECT_SH_CODES).reshape(sc.n, 16, 3)
+    assert np.array_equal(codes, comp.codes)
+    assert np.array_equal(gs.inspect(binding.RG_INSPECT_SH_SCALES).reshape(4, 3).view(np.uint32),
+                          comp.band_scale.view(np.uint32))
+    g16 = gs.inspect(binding.RG_INSPECT_GEOM16).reshape(sc.n, 8)
+    assert np.array_equal(g16[:, 0:4], sc.quats.astype(np.float16).view(np.uint16))
+    assert np.array_equal(g16[:, 4:7], sc.scales.astype(np.float16).view(np.uint16))
+    assert np.array_equal(g16[:, 7], comp.gauss_scale.astype(np.float16).view(np.uint16))
+    assert np.array_equal(gs.inspect(binding.RG_INSPECT_LOG_OPACITY).view(np.uint32), comp.log_opac.view(np.uint32))
+
+
+def _keys_equal(gs, sc, cam, mode, comp=None):
+    k, v, ranges, _ = oracle.keys(sc, cam, mode, comp=comp)
+    gk = gs.inspect(binding.RG_INSPECT_KEYS)
+    gk = gk.view(np.uint64) if mode == oracle.EXACT else gk.view(np.uint32).astype(np.uint64)
+    gv = gs.inspect(binding.RG_INSPECT_VALUES)
+    gr = gs.inspect(binding.RG_INSPECT_RANGES).reshape(-1, 2)
+    assert gk.size == k.size, (gk.size, k.size)
+    assert np.array_equal(gk, k)
+    assert np.array_equal(gv, v)
+    assert np.array_equal(gr, ranges)
+    return k.size
+
+
+@pytest.mark.parametrize("mode", [oracle.EXACT, oracle.ROOFGS])
+def test_keys_values_ranges_bit_exact_tiny(mode):
+    sc, cams = synth.workload("tiny_256")
+    gs = gpu_scene(sc)
+    comp = oracle.compact(sc) if mode == oracle.ROOFGS else None
+    _, st = render(gs, cams[0], mode, stats=True)
+    n = _keys_equal(gs, sc, cams[0], mode, comp)
+    assert st["n_entries"] == n
+    assert st["sort_passes"] == (4 if mode == oracle.ROOFGS else 5)  # 32 + 8 tile bits -> 5 digits
+
+
+# ---------------------------------------------------------------------------
+# images
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def tiny():
+    sc, cams = synth.workload("tiny_256")
+    return sc, cams[0], gpu_scene(sc), oracle.compact(sc)
+
+
+def test_exact_mode_matches_oracle_tiny(tiny):
+    sc, cam, gs, _ = tiny
+    img = render(gs, cam, "exact")
+    ref, diag, _ = oracle.render(sc, cam, oracle.EXACT)
+    err, flagged = assert_close(img, ref, diag, TOL, label="exact tiny")
+    print("exact tiny: max err %.3g, flagged %.4f" % (err, flagged))
+
+
+def test_roofgs_mode_within_fast_exp_bound_tiny(tiny):
+    sc, cam, gs, comp = tiny
+    img = render(gs, cam, "roofgs")
+    ref, diag, _ = oracle.render(sc, cam, oracle.ROOFGS, comp=comp)
+    assert_close(img, ref, diag, oracle.EPS_MAX + TOL + HALF_COLOUR, label="roofgs vs exact exp")
+    ref32, diag32, _ = oracle.render(sc, cam, oracle.ROOFGS, comp=comp, exp_kind=oracle.EXP_FAST32)
+    err, flagged = assert_close(img, ref32, diag32, TOL + HALF_COLOUR, label="roofgs vs fp32 fast exp")
+    print("roofgs tiny vs fast-exp oracle: max err %.3g, flagged %.4f" % (err, flagged))
+
+
+@pytest.mark.parametrize("flags", [binding.RG_FLAG_EXACT_EXP, binding.RG_FLAG_SINGLE_PIXEL,
+                                   binding.RG_FLAG_EXACT_EXP | binding.RG_FLAG_SINGLE_PIXEL])
+def test_roofgs_ingredient_toggles(tiny, flags):
+    sc, cam, gs, comp = tiny
+    img = render(gs, cam, "roofgs", flags=flags)
+    kind = oracle.EXP_EXACT if flags & binding.RG_FLAG_EXACT_EXP else oracle.EXP_FAST32
+    ref, diag, _ = oracle.render(sc, cam, oracle.ROOFGS, comp=comp, exp_kind=kind)
+    assert_close(img, ref, diag, TOL + HALF_COLOUR, label="flags %d" % flags)
+
+
+def test_roofgs_psnr_against_exact_tiny(tiny):
+    sc, cam, gs, _ = tiny
+    a = render(gs, cam, "exact")
+    b = render(gs, cam, "roofgs")
+    assert psnr(a, b) >= 46.4
+
+
+def test_deterministic_and_per_gaussian_sh_scale(tiny):
+    sc, cam, gs, _ = tiny
+    a = render(gs, cam, "roofgs")
+    b = render(gs, cam, "roofgs")
+    assert np.array_equal(a, b)
+    e1 = render(gs, cam, "exact")
+    e2 = render(gs, cam, "exact")
+    assert np.array_equal(e1, e2)
+    gp = gpu_scene(sc, per_gauss=True)
+    comp = oracle.compact(sc, True)
+    img = render(gp, cam, "roofgs")
+    ref, diag, _ = oracle.render(sc, cam, oracle.ROOFGS, comp=comp, exp_kind=oracle.EXP_FAST32)
+    assert_close(img, ref, diag, TOL + HALF_COLOUR, label="per-gaussian sh scale")
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["exact", "roofgs"])
+@pytest.mark.parametrize("wh", [(100, 37), (16, 16), (1, 1), (33, 250)])
+def test_ragged_image_sizes(mode, wh):
+    sc = small_random_scene(300, seed=21)
+    cam = synth.tiny_camera(wh[0], wh[1], bg=(0.1, 0.2, 0.3))
+    gs = gpu_scene(sc)
+    om = oracle.EXACT if mode == "exact" else oracle.ROOFGS
+    comp = oracle.compact(sc) if mode == "roofgs" else None
+    img, st = render(gs, cam, mode, stats=True)
+    ref, diag, _ = oracle.render(sc, cam, om, comp=comp, exp_kind=oracle.EXP_FAST32)
+    assert_close(img, ref, diag, TOL + (HALF_COLOUR if mode == "roofgs" else 0), max_flagged=0.05, label=str(wh))
+    _keys_equal(gs, sc, cam, om, comp)
+
+
+@pytest.mark.parametrize("mode", ["exact", "roofgs"])
+def test_empty_and_fully_culled_scenes(mode):
+    cam = synth.tiny_camera(64, 48, bg=(0.25, 0.5, 0.75))
+    empty = synth.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32),
+                        np.zeros(0, np.float32), np.zeros((0, 16, 3), np.float32))
+    img, st = render(gpu_scene(empty), cam, mode, stats=True)
+    assert st["n_entries"] == 0
+    assert np.allclose(img, np.array([0.25, 0.5, 0.75])[:, None, None])
+    behind = small_random_scene(50, seed=3)
+    behind.means[:, 2] = -10.0  # behind the camera (z < znear)
+    img, st = render(gpu_scene(behind), cam, mode, stats=True)
+    assert st["n_entries"] == 0 and st["n_front"] == 0
+    assert np.allclose(img, np.array([0.25, 0.5, 0.75])[:, None, None])
+
+
+def test_degenerate_gaussians_are_culled_consistently():
+    sc = small_random_scene(64, seed=8)
+    sc.quats[:5] = 0.0            # zero quaternion: culled on both sides
+    sc.opacities[5:10] = 1e-3     # below 1/255: culled in RoofGS mode
+    sc.opacities[10:12] = 0.0
+    sc.scales[12:15] = 0.0        # zero scale: only the 0.3 dilation remains
+    cam = synth.tiny_camera(64, 64)
+    gs = gpu_scene(sc)
+    for mode, om in (("exact", oracle.EXACT), ("roofgs", oracle.ROOFGS)):
+        comp = oracle.compact(sc) if mode == "roofgs" else None
+        img = render(gs, cam, mode)
+        ref, diag, _ = oracle.render(sc, cam, om, comp=comp, exp_kind=oracle.EXP_FAST32)
+        assert_close(img, ref, diag, TOL + HALF_COLOUR, max_flagged=0.05, label=mode)
+        _keys_equal(gs, sc, cam, om, comp)
+
+
+def test_invalid_inputs_are_rejected():
+    sc = small_random_scene(10, seed=1)
+    bad = sc.subset(np.arange(10))
+    bad.means[3, 1] = np.nan
+    with pytest.raises(binding.RgError) as e:
+        gpu_scene(bad)
+    assert e.value.status == 1
+    bad = sc.subset(np.arange(10))
+    bad.opacities[2] = 1.5
+    with pytest.raises(binding.RgError):
+        gpu_scene(bad)
+    gs = gpu_scene(sc)
+    cam = synth.tiny_camera(32, 32)
+    cam.zfar = cam.znear
+    with pytest.raises(binding.RgError):
+        gs.render(cam)
+    cam = synth.tiny_camera(32, 32)
+    c = binding.camera_struct(cam)
+    o = binding.RgOpts(binding.RG_MODE_ROOFGS, 0, 8, 8)
+    out = torch.empty((3, 32, 32), device="cuda")
+    import ctypes as C
+    assert binding.lib().rg_render(gs.handle, C.byref(c), C.byref(o), C.c_void_p(out.data_ptr()), None,
+                                   C.c_void_p(0)) == 8  # other tile shapes are not built
+
+
+def test_capacity_overflow_regrows_and_is_reported():
+    sc, cams = synth.workload("tiny_256")
+    cam = cams[0]
+    gs = gpu_scene(sc)
+    ref = render(gs, cam, "roofgs")
+    small = gpu_scene(sc)
+    small.reserve(1000)  # far below the ~27k entries of this frame
+    # asynchronous render: image incomplete, overflow recorded
+    small.render(cam)
+    torch.cuda.synchronize()
+    with pytest.raises(binding.RgError) as e:
+        small.check()
+    assert e.value.status == 4
+    small.check()  # flags were cleared
+    img, st = render(small, cam, "roofgs", stats=True)
+    assert st["regrown"] == 1 and st["capacity"] >= st["n_entries"]
+    assert np.array_equal(img, ref)
+    small.check()
+
+
+def test_stage_times_and_counters(tiny):
+    sc, cam, gs, _ = tiny
+    for _ in range(3):
+        gs.render(cam, flags=binding.RG_FLAG_STAGE_EVENTS)
+    ms, frames = gs.stage_times()
+    assert frames == 3 and all(m >= 0 for m in ms) and ms[5] > 0
+    _, st = render(gs, cam, "roofgs", stats=True)
+    assert 0 < st["n_visible"] <= st["n_front"] <= sc.n
+    assert st["n_blends"] <= st["n_pairs"]
+    assert st["n_pairs"] > 0
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads: bit-exact keys, sampled tiles against the oracle
+# ---------------------------------------------------------------------------
+
+def _sample_tiles(lay, k, seed):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(lay["tiles_x"] * lay["tiles_y"], size=k, replace=False)).astype(np.int32)
+
+
+def _tile_mask(cam, tiles):
+    lay = oracle.layout(cam)
+    m = np.zeros((cam.height, cam.width), bool)
+    for t in tiles:
+        tx, ty = t % lay["tiles_x"], t // lay["tiles_x"]
+        m[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    return m
+
+
+@pytest.mark.parametrize("name,per_gauss", [("clustered_1080p", False), ("clustered_4k", True)])
+def test_full_size_parity(name, per_gauss):
+    sc, cams = synth.workload(name)
+    cam = cams[0] if name == "clustered_1080p" else cams[7]
+    gs = gpu_scene(sc, per_gauss)
+    comp = oracle.compact(sc, per_gauss)
+    lay = oracle.layout(cam)
+    tiles = _sample_tiles(lay, 48, seed=1)
+    mask = _tile_mask(cam, tiles)
+    for mode, om in (("exact", oracle.EXACT), ("roofgs", oracle.ROOFGS)):
+        img, st = render(gs, cam, mode, stats=True)
+        assert st["n_entries"] == _keys_equal(gs, sc, cam, om, comp if mode == "roofgs" else None)
+        kind = oracle.EXP_EXACT if mode == "exact" else oracle.EXP_FAST32
+        ref, diag, _ = oracle.render(sc, cam, om, comp=comp if mode == "roofgs" else None, exp_kind=kind, tiles=tiles)
+        base = TOL if mode == "exact" else TOL + HALF_COLOUR
+        tol = base + allowance(diag)
+        err = np.abs(img - ref)[:, mask]
+        assert (err <= tol[mask][None]).all(), "%s %s: worst excess %.3g" % (name, mode, (err - tol[mask][None]).max())
+        assert np.mean(allowance(diag)[mask] > 0.1 * TOL) <= 0.05
+    a = render(gs, cam, "exact")
+    b = render(gs, cam, "roofgs")
+    assert psnr(a, b) >= 46.4, psnr(a, b)
