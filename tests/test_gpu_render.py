@@ -56,14 +56,18 @@ def allowance(diag):
 
 
 def assert_close(img, ref, diag, base, max_flagged=0.01, label=""):
+    """Every value within base + the oracle's FP32 allowance; the share of pixels
+    that exceed the strict base at all stays below max_flagged."""
     tol = base + allowance(diag)
     err = np.abs(img - ref)
     bad = err > tol[None]
-    flagged = np.mean(allowance(diag) > 0.1 * TOL)
-    assert not bad.any(), "%s: %d values over tolerance, worst %.3g (tol %.3g)" % (
-        label, int(bad.sum()), float((err - tol[None]).max()), float(tol[None].repeat(3, 0)[bad].min()))
-    assert flagged <= max_flagged, "%s: %.3f of pixels needed an FP32 allowance" % (label, flagged)
-    return float(err.max()), float(flagged)
+    over = float(np.mean((err > base).any(axis=0)))
+    print("%s: max |err| %.3g, pixels over the strict %.3g: %.5f, max allowance %.3g" % (
+        label, float(err.max()), base, over, float(allowance(diag).max())))
+    assert not bad.any(), "%s: %d values over tolerance, worst excess %.3g" % (
+        label, int(bad.sum()), float((err - tol[None]).max()))
+    assert over <= max_flagged, "%s: %.4f of pixels exceed the strict tolerance" % (label, over)
+    return float(err.max()), over
 
 
 def psnr(a, b):
@@ -327,8 +331,11 @@ def test_full_size_parity(name, per_gauss):
         base = TOL if mode == "exact" else TOL + HALF_COLOUR
         tol = base + allowance(diag)
         err = np.abs(img - ref)[:, mask]
+        over = float(np.mean((err > base).any(axis=0)))
+        print("%s %s: max |err| %.3g over %d sampled tiles, pixels over the strict %.3g: %.5f" % (
+            name, mode, float(err.max()), len(tiles), base, over))
         assert (err <= tol[mask][None]).all(), "%s %s: worst excess %.3g" % (name, mode, (err - tol[mask][None]).max())
-        assert np.mean(allowance(diag)[mask] > 0.1 * TOL) <= 0.05
+        assert over <= 0.02
     a = render(gs, cam, "exact")
     b = render(gs, cam, "roofgs")
     assert psnr(a, b) >= 46.4, psnr(a, b)
