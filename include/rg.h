@@ -210,6 +210,32 @@ rg_status rg_inspect(rg_scene* scene, int32_t what, void* host_dst, int64_t cap_
 rg_status rg_eval_fast_exp(const float* P_dev, float* out_dev, int64_t n, void* stream);
 
 /*
+ * Allocation-free sort (the paper has no counterpart: it is a service of this
+ * library for callers that must not allocate device memory -- a real-time
+ * render thread, where cudaMalloc may block on the device; a plugin whose
+ * host application owns all device memory; work being recorded into a CUDA
+ * graph). Sorts the n (key, value) pairs of the caller's device arrays in
+ * place, stably, by the low key_bits bits of the key (8, 16, 24 or 32), with
+ * the same radix-sort kernels as rg_render. All scratch memory (alternate
+ * buffers, histograms, look-back status, counters) is one static device array
+ * of about 4.3 MiB that every GPU loading the library keeps until the process
+ * exits; nothing is allocated or freed.
+ *   keys, vals  device arrays of n uint32 (input and output)
+ *   n           0 .. 524288; larger n returns RG_ERR_INVALID_ARG
+ *   error_dev   optional device uint32: receives 0, or non-zero error bits if a
+ *               bounded device wait gave up (the output is then invalid)
+ * Stream-ordered, no host synchronisation. The first call on a device looks up
+ * that device's scratch address (once per device, with the device current);
+ * make that first call before any stream capture. Every call shares the one
+ * scratch array, which keeps the previous call's contents (the sort clears
+ * what must start at zero): calls that overlap on the GPU -- on different
+ * streams, or from different host threads -- race and must be ordered by the
+ * caller.
+ */
+rg_status rg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, int64_t n, int32_t key_bits, uint32_t* error_dev,
+                                void* stream);
+
+/*
  * Not built yet (return RG_ERR_UNSUPPORTED): batched multi-view rendering,
  * the rasterizer/preprocess backward, and the request loop.
  */

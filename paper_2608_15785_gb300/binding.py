@@ -38,7 +38,7 @@ RG_INSPECT_LOG_OPACITY = 8
 # every entry point include/rg.h declares
 EXPORTS = ["rg_scene_create", "rg_scene_destroy", "rg_scene_reserve", "rg_render", "rg_scene_check",
            "rg_stage_times", "rg_inspect", "rg_eval_fast_exp", "rg_render_batch", "rg_backward", "rg_submit",
-           "rg_poll", "rg_last_error", "rg_version"]
+           "rg_poll", "rg_last_error", "rg_version", "rg_sort_pairs_noalloc"]
 
 
 class RgError(RuntimeError):
@@ -97,6 +97,7 @@ def lib():
         L.rg_backward.argtypes = [P, P, P, P, P, P]
         L.rg_submit.argtypes = [P, P, C.c_int32, P]
         L.rg_poll.argtypes = [P, C.c_uint64, P]
+        L.rg_sort_pairs_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P, P]
         L.rg_last_error.restype = C.c_char_p
         L.rg_last_error.argtypes = []
         L.rg_version.restype = C.c_int32

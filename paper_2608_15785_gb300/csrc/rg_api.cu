@@ -71,6 +71,8 @@ constexpr size_t CTRL_BYTES = sizeof(Counters) + 8 * 256 * sizeof(unsigned);
 
 } // namespace
 
+void rg::set_last_error(const char* msg) { g_err = msg; }
+
 struct rg_scene {
     int device = 0;
     int64_t n = 0;

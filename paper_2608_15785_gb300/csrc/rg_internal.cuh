@@ -383,6 +383,9 @@ void launch_raster_roofgs(const RasterArgs& a, cudaStream_t s);
 void launch_raster_exact(const RasterArgs& a, cudaStream_t s);
 void launch_fast_exp_eval(const float* P, float* out, long long n, cudaStream_t s);
 
+// Sets the message that rg_last_error() returns on this thread.
+void set_last_error(const char* msg);
+
 // Scene creation kernels
 void launch_check_finite(const float* p, long long count, unsigned* flag, cudaStream_t s);
 void launch_sh_absmax(const float* sh, long long n, unsigned* maxbits /*[12]*/, cudaStream_t s);
