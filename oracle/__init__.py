@@ -225,14 +225,16 @@ def render(scene, cam, mode=EXACT, tile=(16, 16), exp_kind=EXP_EXACT, comp: Comp
 
 
 def keys(scene, cam, mode=EXACT, tile=(16, 16), comp: Compact | None = None):
-    """Sorted entries of the frame: (keys u64, vals u32, ranges u32 [NT,2], bins i32 [N,6])."""
+    """Sorted entries of the frame: (keys u64, vals u32, ranges u32 [NT,2], bins i32 [N,7]).
+
+    bins[i] = (visible, tx0, ty0, tx1, ty1, q_d, entries of Gaussian i)."""
     lib = _load()
     m, q, s, op, _ = _inputs(scene, mode, comp)
     n = m.shape[0]
     c = cam_struct(cam)
     lay = layout(cam, tile)
     nt = lay["tiles_x"] * lay["tiles_y"]
-    bins = np.zeros((n, 6), dtype=np.int32)
+    bins = np.zeros((n, 7), dtype=np.int32)
     total = lib.orc_keys(n, _ptr(m), _ptr(q), _ptr(s), _ptr(op), C.byref(c), int(mode), int(tile[0]),
                          int(tile[1]), None, None, 0, None, _ptr(bins))
     if total < 0:

@@ -13,7 +13,9 @@
  *   - in RoofGS mode the folded exponent P = p + log o of Eq. (17)/(21), the
  *     skip of every pair outside the range of Eq. (23) [-ln 255, 0], and
  *     optionally the bit-level exponential of Eq. (24);
- *   - the tile binning and sort key in FP32 with a pinned operation order:
+ *   - the tile binning and sort key in FP32 with a pinned operation order
+ *     (RoofGS mode: the box and per-tile-row extent of the alpha = 1/255
+ *     ellipse, reading of the Speedy-Splat culling adopted in Sec. IV-A.3):
  *     the 64-bit tile|float-depth key of Sec. IV-A.2 (baseline) and the
  *     resolution-adaptive 32-bit tile|quantized-depth key of Eq. (9)
  *     depth_quant with b_t = ceil(log2(TxTy)), b_d = 32 - b_t.
@@ -73,6 +75,9 @@ typedef struct {
     float z;       /* camera-space depth (FP32) */
     float u, v;    /* projected mean (FP32) */
     float rx, ry;  /* box half-extent in pixels (FP32) */
+    /* RoofGS per-row test: level t, Sigma'_yy, and the row-extent constants */
+    float tt, isc, ys, cc, kk;
+    float xl, xh, yl, yh; /* pixel-centre box */
 } orc_bin;
 
 /* Per-Gaussian FP64 quantities for blending. */
@@ -190,6 +195,26 @@ static void bin32(const float* m, const float* qin, const float* s, float op, in
     float yl = fmaxf_(ceilf(v - ry), 0.0f);
     float yh = fminf_(floorf(v + ry), (float)(c->height - 1));
     if (xl > xh || yl > yh) return;
+    b->xl = xl; b->xh = xh; b->yl = yl; b->yh = yh;
+    if (mode == ORC_ROOFGS) {
+        /* Constants of the ellipse {d : d^T Sigma'^-1 d <= t}: for a band of
+         * rows its x-extent is u + c dy +- k sqrt(t - dy^2 / Sigma'_yy) with
+         * c = Sigma'_xy / Sigma'_yy, k = sqrt(det / Sigma'_yy), the right-most
+         * point at dy = Sigma'_xy sqrt(t / Sigma'_xx); det by the Lagrange
+         * identity det = |U0 x U1|^2 + 0.3 (|U0|^2 + |U1|^2) + 0.09. */
+        float n0 = ((U[0] * U[0] + U[1] * U[1]) + U[2] * U[2]);
+        float n1 = ((U[3] * U[3] + U[4] * U[4]) + U[5] * U[5]);
+        float c0 = U[1] * U[5] - U[2] * U[4];
+        float c1 = U[2] * U[3] - U[0] * U[5];
+        float c2 = U[0] * U[4] - U[1] * U[3];
+        float det = (((c0 * c0 + c1 * c1) + c2 * c2) + 0.3f * (n0 + n1)) + 0.09f;
+        float tt = 2.0f * (op + ORC_LN255F);
+        b->tt = tt;
+        b->isc = 1.0f / sc;
+        b->ys = sb * sqrtf(tt / sa);
+        b->cc = sb / sc;
+        b->kk = sqrtf(det / sc);
+    }
     b->tx0 = (int32_t)xl / L->tile_w;
     b->tx1 = (int32_t)xh / L->tile_w;
     b->ty0 = (int32_t)yl / L->tile_h;
@@ -217,6 +242,36 @@ static uint64_t entry_key(const orc_bin* b, int mode, const orc_layout* L, int32
     if (mode == ORC_EXACT) return ((uint64_t)(uint32_t)tile << 32) | (uint64_t)f32_bits(b->z);
     if (L->b_d >= 32) return (uint64_t)b->qd;
     return ((uint64_t)(uint32_t)tile << L->b_d) | (uint64_t)b->qd;
+}
+
+/*
+ * RoofGS tile range of one tile row ty (reading of the Speedy-Splat culling of
+ * Sec. IV-A.3): the x-extent of the alpha = 1/255 ellipse over the row's band
+ * of pixel centres, clipped to the box; returns 0 if the row has no pixel
+ * centre in it. Exact mode uses the whole rectangle row.
+ */
+static int row_range(const orc_bin* b, int mode, const orc_layout* L, int ty, int32_t* txa, int32_t* txb)
+{
+    if (mode == ORC_EXACT) {
+        *txa = b->tx0;
+        *txb = b->tx1;
+        return 1;
+    }
+    float ya = fmaxf_((float)(ty * L->tile_h), b->yl);
+    float yb = fminf_((float)(ty * L->tile_h + L->tile_h - 1), b->yh);
+    float d0 = ya - b->v, d1 = yb - b->v;
+    float dmax = fminf_(fmaxf_(b->ys, d0), d1);
+    float dmin = fminf_(fmaxf_(-b->ys, d0), d1);
+    float wr = sqrtf(fmaxf_(b->tt - (dmax * dmax) * b->isc, 0.0f));
+    float wl = sqrtf(fmaxf_(b->tt - (dmin * dmin) * b->isc, 0.0f));
+    float xr = (b->u + b->cc * dmax) + b->kk * wr;
+    float xf = (b->u + b->cc * dmin) - b->kk * wl;
+    float a0 = fmaxf_(ceilf(xf), b->xl);
+    float a1 = fminf_(floorf(xr), b->xh);
+    if (!(a0 <= a1)) return 0;
+    *txa = (int32_t)a0 / L->tile_w;
+    *txb = (int32_t)a1 / L->tile_w;
+    return 1;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -432,11 +487,14 @@ int64_t orc_render(int64_t n, const float* means, const float* quats, const floa
     int64_t* cnt = (int64_t*)calloc((size_t)NT + 1, sizeof(int64_t));
     for (int64_t i = 0; i < n; i++) {
         if (!bins[i].vis) continue;
-        for (int ty = bins[i].ty0; ty <= bins[i].ty1; ty++)
-            for (int tx = bins[i].tx0; tx <= bins[i].tx1; tx++) {
+        for (int ty = bins[i].ty0; ty <= bins[i].ty1; ty++) {
+            int32_t ta, tb;
+            if (!row_range(&bins[i], mode, &L, ty, &ta, &tb)) continue;
+            for (int tx = ta; tx <= tb; tx++) {
                 int64_t t = (int64_t)ty * L.tiles_x + tx;
                 if (want[t]) cnt[t + 1]++;
             }
+        }
     }
     for (int64_t t = 0; t < NT; t++) cnt[t + 1] += cnt[t];
     int64_t total = cnt[NT];
@@ -445,11 +503,14 @@ int64_t orc_render(int64_t n, const float* means, const float* quats, const floa
     int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(total > 0 ? total : 1));
     for (int64_t i = 0; i < n; i++) {
         if (!bins[i].vis) continue;
-        for (int ty = bins[i].ty0; ty <= bins[i].ty1; ty++)
-            for (int tx = bins[i].tx0; tx <= bins[i].tx1; tx++) {
+        for (int ty = bins[i].ty0; ty <= bins[i].ty1; ty++) {
+            int32_t ta, tb;
+            if (!row_range(&bins[i], mode, &L, ty, &ta, &tb)) continue;
+            for (int tx = ta; tx <= tb; tx++) {
                 int64_t t = (int64_t)ty * L.tiles_x + tx;
                 if (want[t]) list[fill[t]++] = i;
             }
+        }
     }
 
     /* FP64 per-Gaussian quantities, only for Gaussians that some wanted tile uses */
@@ -584,12 +645,18 @@ int64_t orc_keys(int64_t n, const float* means, const float* quats, const float*
     orc_bin* bins = (orc_bin*)malloc(sizeof(orc_bin) * (size_t)(n > 0 ? n : 1));
     for (int64_t i = 0; i < n; i++) {
         bin32(means + 3 * i, quats + 4 * i, scales + 3 * i, op[i], mode, cam, &L, &bins[i]);
+        int64_t ni = 0;
         if (bins[i].vis)
-            total += (int64_t)(bins[i].tx1 - bins[i].tx0 + 1) * (bins[i].ty1 - bins[i].ty0 + 1);
+            for (int ty = bins[i].ty0; ty <= bins[i].ty1; ty++) {
+                int32_t ta, tb;
+                if (row_range(&bins[i], mode, &L, ty, &ta, &tb)) ni += tb - ta + 1;
+            }
+        total += ni;
         if (binout) {
-            int32_t* o = binout + 6 * i;
+            int32_t* o = binout + 7 * i;
             o[0] = bins[i].vis; o[1] = bins[i].tx0; o[2] = bins[i].ty0;
             o[3] = bins[i].tx1; o[4] = bins[i].ty1; o[5] = (int32_t)bins[i].qd;
+            o[6] = (int32_t)ni;
         }
     }
     if (keys && vals && total <= cap) {
@@ -597,12 +664,15 @@ int64_t orc_keys(int64_t n, const float* means, const float* quats, const float*
         int64_t e = 0;
         for (int64_t i = 0; i < n; i++) {
             if (!bins[i].vis) continue;
-            for (int ty = bins[i].ty0; ty <= bins[i].ty1; ty++)
-                for (int tx = bins[i].tx0; tx <= bins[i].tx1; tx++) {
+            for (int ty = bins[i].ty0; ty <= bins[i].ty1; ty++) {
+                int32_t ta, tb;
+                if (!row_range(&bins[i], mode, &L, ty, &ta, &tb)) continue;
+                for (int tx = ta; tx <= tb; tx++) {
                     kv[e].key = entry_key(&bins[i], mode, &L, ty * L.tiles_x + tx);
                     kv[e].val = (uint32_t)i;
                     e++;
                 }
+            }
         }
         qsort(kv, (size_t)total, sizeof(orc_kv), cmp_kv);
         for (int64_t k = 0; k < total; k++) { keys[k] = kv[k].key; vals[k] = kv[k].val; }

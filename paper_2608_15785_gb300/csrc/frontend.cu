@@ -39,24 +39,45 @@ __device__ __forceinline__ unsigned pack_h2(float lo, float hi)
 // Fused front end (RoofGS)
 // ---------------------------------------------------------------------------
 constexpr int FE_THREADS = 256;
+constexpr int FE_WARPS = FE_THREADS / 32;
 
-__global__ void __launch_bounds__(FE_THREADS) k_frontend_fused(FrontendArgs a)
+__device__ __forceinline__ unsigned warp_sum(unsigned x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned warp_inclusive_scan(unsigned x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a)
 {
     __shared__ unsigned s_vb;
-    __shared__ unsigned s_wsum[FE_THREADS / 32];
-    __shared__ unsigned s_incl[FE_THREADS];
-    __shared__ int4 s_meta[FE_THREADS]; // tx0, ty0, width in tiles, q_d
+    __shared__ unsigned s_wsum[FE_WARPS];
+    __shared__ unsigned s_excl[FE_THREADS]; // block-local exclusive prefix of entry counts
+    __shared__ RowTest s_rt[FE_THREADS];    // per-row test of each thread's Gaussian
+    __shared__ unsigned s_q[FE_THREADS];    // quantized depth, Eq. (9)
     __shared__ unsigned long long s_base;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
     __syncthreads();
     const unsigned vb = s_vb;
     const long long i = (long long)vb * FE_THREADS + tid;
 
-    unsigned cnt = 0;
     bool front = false;
-    int4 meta = make_int4(0, 0, 1, 0);
+    RowTest rt;
+    rt.ty0 = 0;
+    rt.ty1 = -1; // no rows unless the box is non-empty
+    unsigned qd = 0;
     if (i < a.n) {
         const float4 ga = __ldg(&a.geoA[i]); // mean, log o
         const float pz = view_z(a.cam, ga.x, ga.y, ga.z);
@@ -67,9 +88,8 @@ __global__ void __launch_bounds__(FE_THREADS) k_frontend_fused(FrontendArgs a)
             Binned b;
             if (project_bin(a.cam, ga.x, ga.y, ga.z, pz, h_lo(gb.x), h_hi(gb.x), h_lo(gb.y), h_hi(gb.y), h_lo(gb.z),
                             h_hi(gb.z), h_lo(gb.w), true, ga.w, b)) {
-                const int wt = b.tx1 - b.tx0 + 1;
-                cnt = (unsigned)(wt * (b.ty1 - b.ty0 + 1));
-                meta = make_int4(b.tx0, b.ty0, wt, (int)quantize_depth(pz, a.cam.zn, a.lay));
+                rt = row_test(b);
+                qd = quantize_depth(pz, a.cam.zn, a.lay);
                 // conic in the paper's (a, b, c) of Eq. (10): b multiplies dx*dy
                 const float inv = 1.0f / b.det;
                 const float ca = b.sc * inv, cb = -2.0f * b.sb * inv, cc = b.sa * inv;
@@ -111,32 +131,63 @@ __global__ void __launch_bounds__(FE_THREADS) k_frontend_fused(FrontendArgs a)
             }
         }
     }
-    s_meta[tid] = meta;
+    s_rt[tid] = rt;
+    s_q[tid] = qd;
+    __syncwarp();
 
-    // block-level inclusive prefix sum of the entry counts
-    const int lane = tid & 31, warp = tid >> 5;
-    unsigned x = cnt;
+    // Entries per Gaussian. The warp's Gaussians have rows_l tile rows each; the
+    // warp walks all of its rows 32 at a time (lane k takes the k-th row of the
+    // chunk, whichever Gaussian it belongs to) and sums the row widths per
+    // Gaussian with a segmented reduction.
+    const int rows_l = rt.ty1 - rt.ty0 + 1 > 0 ? rt.ty1 - rt.ty0 + 1 : 0;
+    const unsigned rincl = warp_inclusive_scan((unsigned)rows_l, lane);
+    const unsigned rexcl = rincl - (unsigned)rows_l;
+    const unsigned wrows = __shfl_sync(0xffffffffu, rincl, 31);
+    unsigned cnt = 0;
+    for (unsigned r0 = 0; r0 < wrows; r0 += 32) {
+        const unsigned k = r0 + (unsigned)lane;
+        int owner = 0; // Gaussian (lane) of warp row k
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        for (int step = 16; step > 0; step >>= 1)
+            if (__shfl_sync(0xffffffffu, rincl, owner + step - 1) <= k) owner += step;
+        const unsigned rl = k - __shfl_sync(0xffffffffu, rexcl, owner);
+        unsigned w = 0;
+        int txa, txb;
+        if (k < wrows && row_range(s_rt[warp * 32 + owner], s_rt[warp * 32 + owner].ty0 + (int)rl, txa, txb))
+            w = (unsigned)(txb - txa + 1);
+        if (k >= wrows) owner = 32; // past the warp's rows: a segment of its own
+        // segmented sum of w over lanes with the same owner
+        const unsigned owner_prev = __shfl_up_sync(0xffffffffu, (unsigned)owner, 1);
+        const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || owner_prev != (unsigned)owner);
+        const unsigned wi = warp_inclusive_scan(w, lane);
+        const int seg0 = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
+        const unsigned before = __shfl_sync(0xffffffffu, wi, seg0 > 0 ? seg0 - 1 : 0);
+        const unsigned owner_next = __shfl_down_sync(0xffffffffu, (unsigned)owner, 1);
+        const bool seg_end = lane == 31 || owner_next != (unsigned)owner;
+        const unsigned seg_sum = wi - (seg0 > 0 ? before : 0u);
+        // each Gaussian (lane) collects its segment sums
+#pragma unroll 1
+        for (unsigned m = __ballot_sync(0xffffffffu, seg_end && k < wrows); m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            const unsigned o = __shfl_sync(0xffffffffu, (unsigned)owner, src);
+            const unsigned v = __shfl_sync(0xffffffffu, seg_sum, src);
+            if ((unsigned)lane == o) cnt += v;
+        }
     }
+
+    // block-level prefix sum of the entry counts
+    const unsigned x = warp_inclusive_scan(cnt, lane);
     if (lane == 31) s_wsum[warp] = x;
     const int nfront = __syncthreads_count(front);
     const int nvis = __syncthreads_count(cnt > 0);
     if (warp == 0) {
-        unsigned ws = lane < FE_THREADS / 32 ? s_wsum[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, ws, o);
-            if (lane >= o) ws += y;
-        }
-        if (lane < FE_THREADS / 32) s_wsum[lane] = ws; // inclusive warp totals
+        unsigned ws = lane < FE_WARPS ? s_wsum[lane] : 0u;
+        ws = warp_inclusive_scan(ws, lane);
+        if (lane < FE_WARPS) s_wsum[lane] = ws; // inclusive warp totals
     }
     __syncthreads();
-    const unsigned incl = x + (warp ? s_wsum[warp - 1] : 0u);
-    s_incl[tid] = incl;
-    const unsigned block_total = s_wsum[FE_THREADS / 32 - 1];
+    s_excl[tid] = x - cnt + (warp ? s_wsum[warp - 1] : 0u);
+    const unsigned block_total = s_wsum[FE_WARPS - 1];
 
     // one device-wide allocation per block, ordered by block
     if (warp == 0) {
@@ -161,25 +212,51 @@ __global__ void __launch_bounds__(FE_THREADS) k_frontend_fused(FrontendArgs a)
     __syncthreads();
     const unsigned long long base = s_base;
 
-    // cooperative emission: entry j of the block -> owner thread by binary search
+    // Emission: the warp's entries are contiguous and in (Gaussian, row, tile)
+    // order, so the warp walks its rows again 32 at a time, scans the row
+    // widths, and writes 32 consecutive entries per store instruction (lane e
+    // finds the row of its entry with a 5-step search over the scan).
     const int b_d = a.lay.b_d;
-    const int tiles_x = a.lay.tiles_x;
-    for (unsigned j = tid; j < block_total; j += FE_THREADS) {
-        int pos = 0;
+    const unsigned tiles_x = (unsigned)a.lay.tiles_x;
+    unsigned long long out = base + s_excl[warp * 32];
+    for (unsigned r0 = 0; r0 < wrows; r0 += 32) {
+        const unsigned k = r0 + (unsigned)lane;
+        int owner = 0;
 #pragma unroll
-        for (int step = FE_THREADS / 2; step > 0; step >>= 1)
-            if (s_incl[pos + step - 1] <= j) pos += step;
-        const unsigned excl = pos ? s_incl[pos - 1] : 0u;
-        const unsigned local = j - excl;
-        const int4 m = s_meta[pos];
-        const unsigned r = local / (unsigned)m.z;
-        const unsigned tile = (unsigned)(m.y + (int)r) * (unsigned)tiles_x + (unsigned)(m.x + (int)(local - r * (unsigned)m.z));
-        const unsigned key = (b_d >= 32) ? (unsigned)m.w : ((tile << b_d) | (unsigned)m.w);
-        const unsigned long long dst = base + j;
-        if (dst < (unsigned long long)a.cap) {
-            a.keys[dst] = key;
-            a.vals[dst] = vb * FE_THREADS + (unsigned)pos;
+        for (int step = 16; step > 0; step >>= 1)
+            if (__shfl_sync(0xffffffffu, rincl, owner + step - 1) <= k) owner += step;
+        const unsigned rl = k - __shfl_sync(0xffffffffu, rexcl, owner);
+        unsigned w = 0;
+        int txa = 0, txb = -1, ty = 0;
+        if (k < wrows) {
+            const RowTest& G = s_rt[warp * 32 + owner];
+            ty = G.ty0 + (int)rl;
+            if (row_range(G, ty, txa, txb)) w = (unsigned)(txb - txa + 1);
         }
+        const unsigned incl = warp_inclusive_scan(w, lane);
+        const unsigned chunk = __shfl_sync(0xffffffffu, incl, 31);
+        for (unsigned e0 = 0; e0 < chunk; e0 += 32) {
+            const unsigned e = e0 + (unsigned)lane;
+            int pos = 0; // row (lane) of entry e
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(0xffffffffu, incl, pos + step - 1) <= e) pos += step;
+            const unsigned ex = __shfl_sync(0xffffffffu, incl - w, pos);
+            const int ta = __shfl_sync(0xffffffffu, txa, pos);
+            const int tr = __shfl_sync(0xffffffffu, ty, pos);
+            const int ow = __shfl_sync(0xffffffffu, owner, pos);
+            if (e < chunk) {
+                const unsigned t = (unsigned)(warp * 32 + ow);
+                const unsigned tile = (unsigned)tr * tiles_x + (unsigned)ta + (e - ex);
+                const unsigned key = (b_d >= 32) ? s_q[t] : ((tile << b_d) | s_q[t]);
+                const unsigned long long dst = out + e;
+                if (dst < (unsigned long long)a.cap) {
+                    a.keys[dst] = key;
+                    a.vals[dst] = vb * FE_THREADS + t;
+                }
+            }
+        }
+        out += chunk;
     }
 }
 

@@ -50,7 +50,7 @@ __device__ __forceinline__ void blend(float P, float r, float g, float b, float&
     if (!done && P >= -LN255F) {
         const float e = FAST ? fast_exp(P) : expf(P);
         const float alpha = fminf(0.99f, e);
-        const float Tn = T * (1.0f - alpha);
+        const float Tn = fmaf(-T, alpha, T); // T (1 - alpha)
         if (Tn < 1e-4f) {
             done = true;
         } else {

@@ -129,7 +129,9 @@ __device__ __forceinline__ unsigned long long lookback_exclusive(unsigned long l
 struct Binned {
     float z, u, v;
     float sa, sb, sc;   // Sigma' = [[sa, sb], [sb, sc]] including the 0.3 dilation
-    float det;          // det Sigma' (Lagrange form, not pinned)
+    float det;          // det Sigma' by the Lagrange identity (pinned)
+    float tt;           // RoofGS: ellipse level t = 2 (log o + ln 255)
+    float xl, xh, yl, yh; // pixel-centre box, clipped to the image
     int tx0, ty0, tx1, ty1;
 };
 
@@ -224,16 +226,71 @@ __device__ __forceinline__ bool project_bin(const CamDev& c, float mx, float my,
     const float yl = fmaxf(ceilf(FS(v, ry)), 0.0f);
     const float yh = fminf(floorf(FA(v, ry)), (float)(c.H - 1));
     if (xl > xh || yl > yh) return false;
+    b.xl = xl;
+    b.xh = xh;
+    b.yl = yl;
+    b.yh = yh;
     b.tx0 = (int)xl / TILE;
     b.tx1 = (int)xh / TILE;
     b.ty0 = (int)yl / TILE;
     b.ty1 = (int)yh / TILE;
     // det Sigma' = |U0 x U1|^2 + 0.3 (|U0|^2 + |U1|^2) + 0.09 (Lagrange identity:
-    // no cancellation for thin Gaussians). Not part of the pinned path.
-    const float cx0 = U[1] * U[5] - U[2] * U[4];
-    const float cx1 = U[2] * U[3] - U[0] * U[5];
-    const float cx2 = U[0] * U[4] - U[1] * U[3];
-    b.det = (cx0 * cx0 + cx1 * cx1 + cx2 * cx2) + 0.3f * (n0 + n1) + 0.09f;
+    // no cancellation for thin Gaussians)
+    const float c0 = FS(FM(U[1], U[5]), FM(U[2], U[4]));
+    const float c1 = FS(FM(U[2], U[3]), FM(U[0], U[5]));
+    const float c2 = FS(FM(U[0], U[4]), FM(U[1], U[3]));
+    b.det = FA(FA(FA(FA(FM(c0, c0), FM(c1, c1)), FM(c2, c2)), FM(0.3f, FA(n0, n1))), 0.09f);
+    b.tt = snug ? FM(2.0f, FA(logo, LN255F)) : 0.0f;
+    return true;
+}
+
+// Per-Gaussian constants of the RoofGS per-row tile test: for a band of rows the
+// x-extent of the ellipse {d : d^T Sigma'^-1 d <= t} is u + c dy +- k sqrt(t - dy^2 / Sigma'_yy)
+// with c = Sigma'_xy / Sigma'_yy, k = sqrt(det / Sigma'_yy); its right-most point is at
+// dy = Sigma'_xy sqrt(t / Sigma'_xx) (left-most at minus that).
+struct RowTest {
+    float u, v, tt, isc, ys, cc, kk, xl, xh, yl, yh;
+    int ty0, ty1;
+};
+
+__device__ __forceinline__ RowTest row_test(const Binned& b)
+{
+    RowTest r;
+    r.u = b.u;
+    r.v = b.v;
+    r.tt = b.tt;
+    r.isc = FD(1.0f, b.sc);
+    r.ys = FM(b.sb, __fsqrt_rn(FD(b.tt, b.sa)));
+    r.cc = FD(b.sb, b.sc);
+    r.kk = __fsqrt_rn(FD(b.det, b.sc));
+    r.xl = b.xl;
+    r.xh = b.xh;
+    r.yl = b.yl;
+    r.yh = b.yh;
+    r.ty0 = b.ty0;
+    r.ty1 = b.ty1;
+    return r;
+}
+
+// Tile range [txa, txb] of tile row ty: the ellipse's x-extent over the row's band of
+// pixel centres, clipped to the box (reading of the Speedy-Splat culling, Sec. IV-A.3).
+// Returns false if no pixel centre of the band lies in it. Pinned FP32 order.
+__device__ __forceinline__ bool row_range(const RowTest& g, int ty, int& txa, int& txb)
+{
+    const float ya = fmaxf((float)(ty * TILE), g.yl);
+    const float yb = fminf((float)(ty * TILE + TILE - 1), g.yh);
+    const float d0 = FS(ya, g.v), d1 = FS(yb, g.v);
+    const float dmax = fminf(fmaxf(g.ys, d0), d1);
+    const float dmin = fminf(fmaxf(-g.ys, d0), d1);
+    const float wr = __fsqrt_rn(fmaxf(FS(g.tt, FM(FM(dmax, dmax), g.isc)), 0.0f));
+    const float wl = __fsqrt_rn(fmaxf(FS(g.tt, FM(FM(dmin, dmin), g.isc)), 0.0f));
+    const float xr = FA(FA(g.u, FM(g.cc, dmax)), FM(g.kk, wr));
+    const float xf = FS(FA(g.u, FM(g.cc, dmin)), FM(g.kk, wl));
+    const float a0 = fmaxf(ceilf(xf), g.xl);
+    const float a1 = fminf(floorf(xr), g.xh);
+    if (!(a0 <= a1)) return false;
+    txa = (int)a0 / TILE;
+    txb = (int)a1 / TILE;
     return true;
 }
 

@@ -18,43 +18,73 @@
 
 namespace rg {
 
-constexpr int S_THREADS = 256;
-constexpr int S_KPT = 16;
+constexpr int S_THREADS = 512;
+constexpr int S_KPT = 8;
 constexpr int S_TILE = S_THREADS * S_KPT; // 4096 entries
 constexpr int S_WARPS = S_THREADS / 32;
 constexpr int RADIX = 256;
+constexpr int LB_WINDOW = 8; // predecessors inspected per round trip of the look-back
 constexpr unsigned SF_AGG = 1u << 30, SF_PRE = 2u << 30, SF_VAL = (1u << 30) - 1u;
+constexpr int H_THREADS = 256;
 
 int sort_tile_items() { return S_TILE; }
 
+// Digit histograms of every pass in one read of the keys (vector loads; the
+// counts of equal digits within a warp are combined before the shared atomic).
 template <typename K>
-__global__ void __launch_bounds__(S_THREADS) k_sort_hist(const K* __restrict__ keys, int passes, unsigned* hist,
+__global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ keys, int passes, unsigned* hist,
                                                          unsigned* status0, const Counters* __restrict__ ctr)
 {
     __shared__ unsigned s_h[8][RADIX];
-    for (int j = threadIdx.x; j < 8 * RADIX; j += S_THREADS) (&s_h[0][0])[j] = 0u;
+    for (int j = threadIdx.x; j < 8 * RADIX; j += H_THREADS) (&s_h[0][0])[j] = 0u;
     __syncthreads();
     const long long n = ctr->n_entries;
     const long long ntiles = (n + S_TILE - 1) / S_TILE;
-    const long long gsz = (long long)gridDim.x * S_THREADS;
-    const long long gid = (long long)blockIdx.x * S_THREADS + threadIdx.x;
+    const long long gsz = (long long)gridDim.x * H_THREADS;
+    const long long gid = (long long)blockIdx.x * H_THREADS + threadIdx.x;
     // clear the look-back status words of the first pass
     for (long long j = gid; j < ntiles * RADIX; j += gsz) status0[j] = 0u;
-    for (long long j = gid; j < n; j += gsz) {
-        const K k = keys[j];
-        for (int p = 0; p < passes; p++) atomicAdd(&s_h[p][(unsigned)(k >> (8 * p)) & 0xffu], 1u);
+    constexpr int V = 16 / sizeof(K); // keys per 16-byte load
+    const long long nv = n / V;
+    // consecutive keys often share digits (entries of one Gaussian): runs of equal
+    // digits among a thread's V keys take one shared atomic
+    for (long long j = gid; j < nv; j += gsz) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(keys) + j);
+        K k[V];
+        memcpy(k, &q, 16);
+        for (int p = 0; p < passes; p++) {
+            unsigned d = (unsigned)(k[0] >> (8 * p)) & 0xffu, c = 1u;
+#pragma unroll
+            for (int u = 1; u < V; u++) {
+                const unsigned e = (unsigned)(k[u] >> (8 * p)) & 0xffu;
+                if (e == d) {
+                    c++;
+                } else {
+                    atomicAdd(&s_h[p][d], c);
+                    d = e;
+                    c = 1u;
+                }
+            }
+            atomicAdd(&s_h[p][d], c);
+        }
+    }
+    // tail (fewer than V keys)
+    for (long long j = nv * V + gid; j < n; j += gsz) {
+        const K kk = keys[j];
+        for (int p = 0; p < passes; p++) atomicAdd(&s_h[p][(unsigned)(kk >> (8 * p)) & 0xffu], 1u);
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < passes * RADIX; j += S_THREADS) {
+    for (int j = threadIdx.x; j < passes * RADIX; j += H_THREADS) {
         const unsigned c = (&s_h[0][0])[j];
         if (c) atomicAdd(&hist[j], c);
     }
 }
 
-// exclusive scan of one value per thread over the 256 threads of the block
-__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* s_w)
+// exclusive scan over the first 256 threads (one digit each) of the block;
+// every thread of the block must call it
+__device__ __forceinline__ unsigned digit_exclusive_scan(unsigned v, unsigned* s_w)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -62,16 +92,16 @@ __device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* s
         if (lane >= o) x += y;
     }
     __syncthreads();
-    if (lane == 31) s_w[warp] = x;
+    if (lane == 31 && warp < RADIX / 32) s_w[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        unsigned w = lane < S_WARPS ? s_w[lane] : 0u;
+        unsigned w = lane < RADIX / 32 ? s_w[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
-        if (lane < S_WARPS) s_w[lane] = w;
+        if (lane < RADIX / 32) s_w[lane] = w;
     }
     __syncthreads();
     return x - v + (warp ? s_w[warp - 1] : 0u);
@@ -102,14 +132,14 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
     const long long n = ctr->n_entries;
     const long long ntiles = (n + S_TILE - 1) / S_TILE;
     {
-        const unsigned h = hist[pass * RADIX + tid];
-        S.goff[tid] = block_exclusive_scan(h, S.scan);
+        const unsigned h = tid < RADIX ? hist[pass * RADIX + tid] : 0u;
+        const unsigned e = digit_exclusive_scan(h, S.scan);
+        if (tid < RADIX) S.goff[tid] = e;
     }
     const unsigned lt_mask = (1u << lane) - 1u;
     while (true) {
         if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
-#pragma unroll
-        for (int w = 0; w < S_WARPS; w++) S.whist[w][tid] = 0u;
+        for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) (&S.whist[0][0])[j] = 0u;
         __syncthreads();
         const long long tile = S.tile;
         if (tile >= ntiles) break;
@@ -142,48 +172,68 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
             __syncwarp();
         }
         __syncthreads();
-        // digit tid: tile count and per-warp exclusive offsets
+        // digit tid: tile count, per-warp exclusive offsets, publish the count
         unsigned count = 0;
+        if (tid < RADIX) {
 #pragma unroll
-        for (int w = 0; w < S_WARPS; w++) {
-            const unsigned c = S.whist[w][tid];
-            S.whist[w][tid] = count;
-            count += c;
+            for (int w = 0; w < S_WARPS; w++) {
+                const unsigned c = S.whist[w][tid];
+                S.whist[w][tid] = count;
+                count += c;
+            }
+            unsigned* st = status + tile * RADIX + tid;
+            *reinterpret_cast<volatile unsigned*>(st) = (tile == 0 ? SF_PRE : SF_AGG) | count;
         }
-        // publish, look back over earlier tiles, publish the inclusive prefix
-        unsigned* st = status + tile * RADIX + tid;
-        unsigned excl = 0;
-        if (tile == 0) {
-            *reinterpret_cast<volatile unsigned*>(st) = SF_PRE | count;
-        } else {
-            *reinterpret_cast<volatile unsigned*>(st) = SF_AGG | count;
-            long long t = tile - 1;
-            bool timed_out = false;
-            while (t >= 0) {
-                unsigned s = *reinterpret_cast<volatile unsigned*>(status + t * RADIX + tid);
+        // tile-local exclusive digit offsets (whole block)
+        const unsigned lo = digit_exclusive_scan(count, S.scan);
+        if (tid < RADIX) {
+            S.loff[tid] = lo;
+            // windowed decoupled look-back: LB_WINDOW predecessors per round trip
+            unsigned excl = 0;
+            if (tile > 0) {
+                long long t = tile - 1;
+                bool timed_out = false, found = false;
                 unsigned spins = 0;
-                while ((s >> 30) == 0u) {
-                    if (++spins > SPIN_LIMIT) {
-                        timed_out = true;
-                        s = SF_PRE;
-                        break;
+                while (!found && t >= 0) {
+                    unsigned sv[LB_WINDOW];
+#pragma unroll
+                    for (int w = 0; w < LB_WINDOW; w++)
+                        sv[w] = (t - w >= 0) ? *reinterpret_cast<volatile unsigned*>(status + (t - w) * RADIX + tid)
+                                             : (2u << 30); // before tile 0: prefix 0
+                    // use the window up to the first missing entry or the first prefix
+                    int used = 0;
+                    unsigned add = 0;
+#pragma unroll
+                    for (int w = 0; w < LB_WINDOW; w++) {
+                        if (used == w) {
+                            const unsigned f = sv[w] >> 30;
+                            if (f != 0u) {
+                                add += sv[w] & SF_VAL;
+                                used = w + 1;
+                                if (f == 2u) found = true;
+                            }
+                        }
+                        if (found) break;
                     }
-                    __nanosleep(32);
-                    s = *reinterpret_cast<volatile unsigned*>(status + t * RADIX + tid);
+                    excl += add;
+                    t -= used;
+                    if (used == 0) { // nearest predecessor not published yet
+                        if (++spins > SPIN_LIMIT) {
+                            timed_out = true;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
                 }
-                excl += s & SF_VAL;
-                if ((s >> 30) == 2u) break;
-                t--;
+                if (timed_out) {
+                    atomicOr(&ctr->error, ERR_SORT_LOOKBACK);
+                    atomicOr(&sticky->error, ERR_SORT_LOOKBACK);
+                }
+                *reinterpret_cast<volatile unsigned*>(status + tile * RADIX + tid) = SF_PRE | ((excl + count) & SF_VAL);
             }
-            if (timed_out) {
-                atomicOr(&ctr->error, ERR_SORT_LOOKBACK);
-                atomicOr(&sticky->error, ERR_SORT_LOOKBACK);
-            }
-            *reinterpret_cast<volatile unsigned*>(st) = SF_PRE | ((excl + count) & SF_VAL);
+            S.gbase[tid] = S.goff[tid] + excl;
+            if (status_next) status_next[tile * RADIX + tid] = 0u;
         }
-        S.gbase[tid] = S.goff[tid] + excl;
-        if (status_next) status_next[tile * RADIX + tid] = 0u;
-        S.loff[tid] = block_exclusive_scan(count, S.scan);
         __syncthreads();
         // reorder the tile by digit in shared memory
 #pragma unroll
@@ -227,10 +277,10 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        hist_grid = 4 * (sms > 0 ? sms : 1);
+        hist_grid = 8 * (sms > 0 ? sms : 1);
     }
     const K* kin = (const K*)a.keys[0];
-    k_sort_hist<K><<<hist_grid, S_THREADS, 0, s>>>(kin, a.passes, a.hist, a.status[0], a.ctr);
+    k_sort_hist<K><<<hist_grid, H_THREADS, 0, s>>>(kin, a.passes, a.hist, a.status[0], a.ctr);
     if (ev_after_hist) cudaEventRecord(ev_after_hist, s);
     for (int p = 0; p < a.passes; p++) {
         const int src = p & 1, dst = src ^ 1;
@@ -250,15 +300,40 @@ void launch_sort(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hist)
 // Per-tile [start, end) ranges of the sorted entries (ranges zeroed beforehand).
 // ---------------------------------------------------------------------------
 template <typename K>
+__device__ __forceinline__ void range_mark(uint2* ranges, long long ntiles, long long i, unsigned long long t,
+                                           unsigned long long tprev, unsigned long long tnext, long long n)
+{
+    if (t >= (unsigned long long)ntiles) return; // only after a failed (timed-out) sort
+    if (i == 0 || tprev != t) ranges[t].x = (unsigned)i;
+    if (i == n - 1 || tnext != t) ranges[t].y = (unsigned)(i + 1);
+}
+
+// Each thread takes 16 bytes of consecutive keys and the key after them.
+template <typename K>
 __global__ void k_ranges(const K* __restrict__ keys, int tile_shift, long long ntiles, uint2* ranges,
                          const Counters* __restrict__ ctr)
 {
+    constexpr int V = 16 / sizeof(K);
     const long long n = ctr->n_entries;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long t = (unsigned long long)keys[i] >> tile_shift;
-        if (t >= (unsigned long long)ntiles) continue; // only after a failed (timed-out) sort
-        if (i == 0 || ((unsigned long long)keys[i - 1] >> tile_shift) != t) ranges[t].x = (unsigned)i;
-        if (i == n - 1 || ((unsigned long long)keys[i + 1] >> tile_shift) != t) ranges[t].y = (unsigned)(i + 1);
+    const long long nv = (n + V - 1) / V;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nv; j += (long long)gridDim.x * blockDim.x) {
+        const long long i0 = j * V;
+        unsigned long long t[V + 2];
+        if (i0 + V <= n) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(keys) + j);
+            K k[V];
+            memcpy(k, &q, 16);
+#pragma unroll
+            for (int u = 0; u < V; u++) t[u + 1] = (unsigned long long)k[u] >> tile_shift;
+        } else {
+#pragma unroll
+            for (int u = 0; u < V; u++) t[u + 1] = (i0 + u < n) ? ((unsigned long long)keys[i0 + u] >> tile_shift) : ~0ull;
+        }
+        t[0] = i0 > 0 ? ((unsigned long long)keys[i0 - 1] >> tile_shift) : ~0ull;
+        t[V + 1] = (i0 + V < n) ? ((unsigned long long)keys[i0 + V] >> tile_shift) : ~0ull;
+#pragma unroll
+        for (int u = 0; u < V; u++)
+            if (i0 + u < n) range_mark<K>(ranges, ntiles, i0 + u, t[u + 1], t[u], t[u + 2], n);
     }
 }
 

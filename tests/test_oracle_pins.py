@@ -345,7 +345,12 @@ def test_box_contains_every_pixel_it_must(tiny, mode):
     sc, cam = tiny
     comp = oracle.compact(sc) if mode == oracle.ROOFGS else None
     src = comp if comp is not None else sc
-    _, _, _, bins = oracle.keys(sc, cam, mode, comp=comp)
+    keys_, vals_, _, bins = oracle.keys(sc, cam, mode, comp=comp)
+    lay = oracle.layout(cam)
+    shift = np.uint64(32 if mode == oracle.EXACT else lay["b_d"])
+    tiles_of = {}
+    for kk, vv in zip((keys_ >> shift).astype(np.int64), vals_):
+        tiles_of.setdefault(int(vv), set()).add(int(kk))
     checked = 0
     for i in range(0, sc.n, 7):
         pr = oracle.project64(src.means[i], src.quats[i], src.scales[i], cam)
@@ -362,10 +367,12 @@ def test_box_contains_every_pixel_it_must(tiny, mode):
             must = qq < 9.0 * (1 - 1e-5)
         if not must.any():
             continue
-        vis, tx0, ty0, tx1, ty1, _ = bins[i]
+        vis, tx0, ty0, tx1, ty1, _, _ = bins[i]
         assert vis == 1
         tx, ty = xs[must] // 16, ys[must] // 16
         assert tx.min() >= tx0 and tx.max() <= tx1 and ty.min() >= ty0 and ty.max() <= ty1
+        # every such pixel's tile is one of the Gaussian's entries (RoofGS: per-row test)
+        assert set((ty * lay["tiles_x"] + tx).tolist()) <= tiles_of[i]
         checked += 1
     assert checked > 50
 
