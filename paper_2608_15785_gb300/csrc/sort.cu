@@ -18,8 +18,17 @@
 
 namespace rg {
 
-constexpr int S_THREADS = 512;
-constexpr int S_KPT = 8;
+#ifndef RG_SORT_THREADS
+#define RG_SORT_THREADS 512
+#endif
+#ifndef RG_SORT_KPT
+#define RG_SORT_KPT 8
+#endif
+#ifndef RG_SORT_BALLOT_RANK
+#define RG_SORT_BALLOT_RANK 0
+#endif
+constexpr int S_THREADS = RG_SORT_THREADS;
+constexpr int S_KPT = RG_SORT_KPT;
 constexpr int S_TILE = S_THREADS * S_KPT; // 4096 entries
 constexpr int S_WARPS = S_THREADS / 32;
 constexpr int RADIX = 256;
@@ -160,7 +169,17 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
 #pragma unroll
         for (int i = 0; i < S_KPT; i++) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+#if RG_SORT_BALLOT_RANK
+            unsigned peers = 0xffffffffu; // lanes with the same digit: one ballot per digit bit
+#pragma unroll
+            for (int bit = 0; bit < 8; bit++) {
+                const bool on = (d >> bit) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, on);
+                peers &= on ? bal : ~bal;
+            }
+#else
             const unsigned peers = __match_any_sync(0xffffffffu, d);
+#endif
             const int leader = __ffs(peers) - 1;
             unsigned b = 0;
             if (lane == leader) {
