@@ -141,9 +141,12 @@ def stage_work(mode, st, W, H):
     tiles = st["tiles_x"] * st["tiles_y"]
     passes = st["sort_passes"]
     if mode == "roofgs":
-        # 16 B mean+log o per Gaussian; 16 B FP16 geometry if inside the depth/opacity range;
-        # 48 B INT8 SH + 32 B record if visible; 8 B key+value per entry
-        front = 16 * N + 16 * nf + 80 * nv + 8 * nd
+        # depth keys: 16 B mean+log o read, 8 B (q_d, index) written per Gaussian; depth sort of the
+        # N pairs: 4 B histogram + 16 B per pass; fused kernel: 4 B order + 16 B mean+log o per
+        # Gaussian, 16 B FP16 geometry if inside the depth/opacity range, 48 B INT8 SH + 32 B
+        # record if visible, 8 B key+value per entry
+        gpasses = (st["b_d"] + 7) // 8
+        front = 24 * N + (4 + 16 * gpasses) * N + 20 * N + 16 * nf + 80 * nv + 8 * nd
         sort = 4 * nd + passes * 16 * nd
         ranges = 4 * nd + 8 * tiles
     else:
@@ -160,7 +163,7 @@ def stage_work(mode, st, W, H):
 
 def mean_stats(stats, poses_used):
     keys = ["n_gaussians", "n_front", "n_visible", "n_entries", "n_pairs", "n_blends", "tiles_x", "tiles_y",
-            "sort_passes"]
+            "sort_passes", "b_d"]
     return {k: sum(stats[p][k] for p in poses_used) / len(poses_used) for k in keys}
 
 

@@ -110,6 +110,10 @@ typedef struct {
 /* RoofGS-mode ingredient flags (ignored in exact mode) */
 #define RG_FLAG_EXACT_EXP (1u << 0)    /* use expf instead of the bit-level exponential of Eq. (24) */
 #define RG_FLAG_SINGLE_PIXEL (1u << 1) /* one pixel per thread instead of the dual-pixel scheme, Eq. (20) */
+/* sort the entries in 4 radix passes over the full 32-bit key, in Gaussian order (the
+ * paper's scheme, Sec. IV-A.2), instead of ordering the Gaussians by quantized depth
+ * first and sorting only the b_t tile bits of the entries; both give the same order */
+#define RG_FLAG_SORT_FULL_KEY (1u << 2)
 /* flags for both modes */
 #define RG_FLAG_STAGE_EVENTS (1u << 8) /* record per-stage CUDA events (rg_stage_times) */
 

@@ -6,7 +6,8 @@ synthetic scenes and cameras. Importing this package does not load the
 library; the first call that needs it does, and raises if it is missing.
 """
 from . import synth  # noqa: F401
-from .binding import (RG_FLAG_EXACT_EXP, RG_FLAG_SINGLE_PIXEL, RG_FLAG_STAGE_EVENTS,  # noqa: F401
+from .binding import (RG_FLAG_EXACT_EXP, RG_FLAG_SINGLE_PIXEL, RG_FLAG_SORT_FULL_KEY,  # noqa: F401
+                      RG_FLAG_STAGE_EVENTS,
                       RG_MODE_EXACT, RG_MODE_ROOFGS, RG_SH_SCALE_BAND, RG_SH_SCALE_BAND_GAUSS,
                       RG_STORE_COMPACT, RG_STORE_FP32, RgError, Scene, eval_fast_exp, lib, version)
 

@@ -25,6 +25,7 @@ RG_MODE_EXACT = 0
 RG_MODE_ROOFGS = 1
 RG_FLAG_EXACT_EXP = 1 << 0
 RG_FLAG_SINGLE_PIXEL = 1 << 1
+RG_FLAG_SORT_FULL_KEY = 1 << 2
 RG_FLAG_STAGE_EVENTS = 1 << 8
 RG_INSPECT_KEYS = 1
 RG_INSPECT_VALUES = 2

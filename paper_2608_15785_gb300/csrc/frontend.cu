@@ -65,13 +65,17 @@ __global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a
     __shared__ unsigned s_excl[FE_THREADS]; // block-local exclusive prefix of entry counts
     __shared__ RowTest s_rt[FE_THREADS];    // per-row test of each thread's Gaussian
     __shared__ unsigned s_q[FE_THREADS];    // quantized depth, Eq. (9)
+    __shared__ unsigned s_id[FE_THREADS];   // Gaussian index of each slot
     __shared__ unsigned long long s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
     __syncthreads();
     const unsigned vb = s_vb;
-    const long long i = (long long)vb * FE_THREADS + tid;
+    const long long slot = (long long)vb * FE_THREADS + tid;
+    // Gaussian of this slot: slots follow depth order when an order is given, so
+    // the entries come out sorted by depth and only the tile bits remain to sort
+    const long long i = slot < a.n ? (a.order ? (long long)a.order[slot] : slot) : a.n;
 
     bool front = false;
     RowTest rt;
@@ -133,6 +137,7 @@ __global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a
     }
     s_rt[tid] = rt;
     s_q[tid] = qd;
+    s_id[tid] = (unsigned)i;
     __syncwarp();
 
     // Entries per Gaussian. The warp's Gaussians have rows_l tile rows each; the
@@ -252,12 +257,30 @@ __global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a
                 const unsigned long long dst = out + e;
                 if (dst < (unsigned long long)a.cap) {
                     a.keys[dst] = key;
-                    a.vals[dst] = vb * FE_THREADS + t;
+                    a.vals[dst] = s_id[t];
                 }
             }
         }
         out += chunk;
     }
+}
+
+__global__ void __launch_bounds__(256) k_depth_keys(FrontendArgs a, unsigned* keys, unsigned* vals, Counters* ctr)
+{
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i == 0) ctr->n_entries = (unsigned)a.n;
+    if (i >= a.n) return;
+    const float4 ga = __ldg(&a.geoA[i]);
+    const float pz = view_z(a.cam, ga.x, ga.y, ga.z);
+    const bool front = pz > a.cam.zn && pz <= a.cam.zf && ga.w >= -LN255F;
+    keys[i] = front ? quantize_depth(pz, a.cam.zn, a.lay) : a.lay.qmax;
+    vals[i] = (unsigned)i;
+}
+
+void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((a.n + 255) / 256);
+    k_depth_keys<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(a, keys, vals, ctr);
 }
 
 void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s)

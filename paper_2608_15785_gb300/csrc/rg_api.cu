@@ -68,6 +68,7 @@ constexpr int EV_RING = 512;
 constexpr int EV_PER_FRAME = 6; // start, front end, histogram, sort, ranges, raster
 constexpr long long MAX_CAP = (1ll << 30) - 1;
 constexpr size_t CTRL_BYTES = sizeof(Counters) + 8 * 256 * sizeof(unsigned);
+constexpr size_t CTRL_ALLOC = 2 * CTRL_BYTES; // frame counters + the per-Gaussian depth sort's
 
 } // namespace
 
@@ -94,6 +95,7 @@ struct rg_scene {
     DevBuf sort_status[2];
     DevBuf xy, depth, conic, rgb, rect, touched, offsets; // exact per-Gaussian
     DevBuf rec;                                           // RoofGS raster records
+    DevBuf gkeys[2], gvals[2], gstatus[2];                // RoofGS per-Gaussian depth sort
     // last frame
     int last_mode = -1;
     int last_passes = 0;
@@ -175,7 +177,7 @@ rg_status ensure_workspace(rg_scene* s, int mode, int tiles, int64_t cap)
         s->cap = cap;
     }
     RG_TRY(ensure(s->ranges, (size_t)tiles * sizeof(uint2), "ranges"));
-    RG_TRY(ensure(s->ctrl, CTRL_BYTES, "counters"));
+    RG_TRY(ensure(s->ctrl, CTRL_ALLOC, "counters"));
     RG_TRY(ensure(s->lb_status, (size_t)((n + 255) / 256 + 1) * 8, "look-back status"));
     if (mode == RG_MODE_EXACT) {
         RG_TRY(ensure(s->xy, (size_t)n * 8, "xy"));
@@ -187,6 +189,12 @@ rg_status ensure_workspace(rg_scene* s, int mode, int tiles, int64_t cap)
         RG_TRY(ensure(s->offsets, (size_t)n * 4, "offsets"));
     } else {
         RG_TRY(ensure(s->rec, (size_t)n * 32, "records"));
+        for (int k = 0; k < 2; k++) {
+            RG_TRY(ensure(s->gkeys[k], (size_t)n * 4, "depth keys"));
+            RG_TRY(ensure(s->gvals[k], (size_t)n * 4, "depth order"));
+            RG_TRY(ensure(s->gstatus[k], (size_t)((n + sort_tile_items() - 1) / sort_tile_items()) * 256 * 4,
+                          "depth sort status"));
+        }
     }
     return RG_OK;
 }
@@ -215,7 +223,7 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
         if (s->ev_pending < EV_RING) s->ev_pending++;
         RG_CK(cudaEventRecord(E[0], st));
     }
-    RG_CK(cudaMemsetAsync(s->ctrl.p, 0, CTRL_BYTES, st));
+    RG_CK(cudaMemsetAsync(s->ctrl.p, 0, CTRL_ALLOC, st));
     RG_CK(cudaMemsetAsync(s->ranges.p, 0, (size_t)F.tiles * sizeof(uint2), st));
     const long long n = s->n;
     SortArgs sa;
@@ -283,9 +291,38 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
         a.ctr = ctr;
         a.sticky = sticky;
         RG_CK(cudaMemsetAsync(s->lb_status.p, 0, (size_t)((n + 255) / 256 + 1) * 8, st));
-        launch_frontend_fused(a, st);
         sa.key_bytes = 4;
-        sa.passes = 4; // 32-bit key, 8-bit digits
+        if (flags & RG_FLAG_SORT_FULL_KEY) {
+            // the paper's scheme: entries in Gaussian order, 4 passes over the 32-bit key
+            sa.passes = 4;
+            sa.bit0 = 0;
+        } else {
+            // Gaussians sorted by quantized depth first (stable, ties by index); the
+            // entries then come out in (q_d, index) order and a stable sort of the
+            // b_t tile bits alone yields the order of the full 32-bit key
+            SortArgs ga;
+            memset(&ga, 0, sizeof(ga));
+            for (int k = 0; k < 2; k++) {
+                ga.keys[k] = s->gkeys[k].p;
+                ga.vals[k] = s->gvals[k].as<unsigned>();
+                ga.status[k] = s->gstatus[k].as<unsigned>();
+            }
+            Counters* gctr = reinterpret_cast<Counters*>(s->ctrl.as<unsigned char>() + CTRL_BYTES);
+            ga.cap = n;
+            ga.key_bytes = 4;
+            ga.passes = (F.lay.b_d + 7) / 8;
+            ga.bit0 = 0;
+            ga.hist = reinterpret_cast<unsigned*>(s->ctrl.as<unsigned char>() + CTRL_BYTES + sizeof(Counters));
+            ga.max_tiles = (n + sort_tile_items() - 1) / sort_tile_items();
+            ga.ctr = gctr;
+            ga.sticky = sticky;
+            launch_depth_keys(a, s->gkeys[0].as<unsigned>(), s->gvals[0].as<unsigned>(), gctr, st);
+            launch_sort(ga, st, nullptr);
+            a.order = s->gvals[ga.passes & 1].as<unsigned>();
+            sa.passes = (F.lay.b_t + 7) / 8;
+            sa.bit0 = F.lay.b_d;
+        }
+        launch_frontend_fused(a, st);
         tile_shift = F.lay.b_d;
     }
     if (ev) RG_CK(cudaEventRecord(E[1], st));
@@ -339,7 +376,8 @@ rg_status upload(DevBuf& dst, const float* src, size_t count, int on_device, cud
 
 void destroy_scene(rg_scene* s)
 {
-    DevBuf* bufs[] = {&s->means, &s->scales, &s->quats, &s->opac, &s->sh, &s->geoA, &s->geoB, &s->shq, &s->keys[0],
+    DevBuf* bufs[] = {&s->gkeys[0], &s->gkeys[1], &s->gvals[0], &s->gvals[1], &s->gstatus[0], &s->gstatus[1],
+                      &s->means, &s->scales, &s->quats, &s->opac, &s->sh, &s->geoA, &s->geoB, &s->shq, &s->keys[0],
                       &s->keys[1], &s->vals[0], &s->vals[1], &s->ranges, &s->ctrl, &s->sticky, &s->lb_status,
                       &s->sort_status[0], &s->sort_status[1], &s->xy, &s->depth, &s->conic, &s->rgb, &s->rect,
                       &s->touched, &s->offsets, &s->rec};

@@ -347,6 +347,7 @@ __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f),
 // Host-side launchers (defined in the .cu files).
 // ---------------------------------------------------------------------------
 struct FrontendArgs {
+    const unsigned* order; // [N] Gaussian processed by thread slot i (depth order), or null (index order)
     const float4* geoA;    // [N] (mean.xyz, log o)
     const uint4* geoB;     // [N] FP16 (qw,qx | qy,qz | s0,s1 | s2,g)
     const uint4* shq;      // [3][N] INT8 SH codes, 48 bytes per Gaussian in 3 planes
@@ -365,6 +366,9 @@ struct FrontendArgs {
     Sticky* sticky;
 };
 void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s);
+// quantized depth (Eq. (9)) of every Gaussian as a sort key, Gaussian index as value;
+// culled Gaussians get 2^b_d - 1 (the fused front end skips them); writes n to ctr
+void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, cudaStream_t s);
 
 struct ExactArgs {
     const float* means;
@@ -399,7 +403,8 @@ struct SortArgs {
     unsigned* vals[2];
     long long cap;
     int key_bytes;        // 4 or 8
-    int passes;           // 8-bit digits from bit 0
+    int passes;           // 8-bit digits
+    int bit0;             // lowest key bit sorted (digit p = bits bit0 + 8p ..)
     unsigned* hist;       // [8][256]
     unsigned* status[2];  // [max_tiles][256] look-back status per pass (alternating)
     long long max_tiles;

@@ -41,8 +41,9 @@ int sort_tile_items() { return S_TILE; }
 // Digit histograms of every pass in one read of the keys (vector loads; the
 // counts of equal digits within a warp are combined before the shared atomic).
 template <typename K>
-__global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ keys, int passes, unsigned* hist,
-                                                         unsigned* status0, const Counters* __restrict__ ctr)
+__global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ keys, int passes, int bit0,
+                                                         unsigned* hist, unsigned* status0,
+                                                         const Counters* __restrict__ ctr)
 {
     __shared__ unsigned s_h[8][RADIX];
     for (int j = threadIdx.x; j < 8 * RADIX; j += H_THREADS) (&s_h[0][0])[j] = 0u;
@@ -62,10 +63,10 @@ __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ k
         K k[V];
         memcpy(k, &q, 16);
         for (int p = 0; p < passes; p++) {
-            unsigned d = (unsigned)(k[0] >> (8 * p)) & 0xffu, c = 1u;
+            unsigned d = (unsigned)(k[0] >> (bit0 + 8 * p)) & 0xffu, c = 1u;
 #pragma unroll
             for (int u = 1; u < V; u++) {
-                const unsigned e = (unsigned)(k[u] >> (8 * p)) & 0xffu;
+                const unsigned e = (unsigned)(k[u] >> (bit0 + 8 * p)) & 0xffu;
                 if (e == d) {
                     c++;
                 } else {
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ k
     // tail (fewer than V keys)
     for (long long j = nv * V + gid; j < n; j += gsz) {
         const K kk = keys[j];
-        for (int p = 0; p < passes; p++) atomicAdd(&s_h[p][(unsigned)(kk >> (8 * p)) & 0xffu], 1u);
+        for (int p = 0; p < passes; p++) atomicAdd(&s_h[p][(unsigned)(kk >> (bit0 + 8 * p)) & 0xffu], 1u);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < passes * RADIX; j += H_THREADS) {
@@ -131,13 +132,13 @@ struct SortSmem {
 template <typename K>
 __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ kin, const unsigned* __restrict__ vin,
                                                         K* __restrict__ kout, unsigned* __restrict__ vout, int pass,
-                                                        const unsigned* __restrict__ hist, unsigned* status,
+                                                        int bit0, const unsigned* __restrict__ hist, unsigned* status,
                                                         unsigned* status_next, Counters* ctr, Sticky* sticky)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int shift = 8 * pass;
+    const int shift = bit0 + 8 * pass;
     const long long n = ctr->n_entries;
     const long long ntiles = (n + S_TILE - 1) / S_TILE;
     {
@@ -299,13 +300,14 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
         hist_grid = 8 * (sms > 0 ? sms : 1);
     }
     const K* kin = (const K*)a.keys[0];
-    k_sort_hist<K><<<hist_grid, H_THREADS, 0, s>>>(kin, a.passes, a.hist, a.status[0], a.ctr);
+    if (a.passes <= 0) return;
+    k_sort_hist<K><<<hist_grid, H_THREADS, 0, s>>>(kin, a.passes, a.bit0, a.hist, a.status[0], a.ctr);
     if (ev_after_hist) cudaEventRecord(ev_after_hist, s);
     for (int p = 0; p < a.passes; p++) {
         const int src = p & 1, dst = src ^ 1;
         unsigned* nxt = (p + 1 < a.passes) ? a.status[(p + 1) & 1] : nullptr;
         k_onesweep<K><<<grid, S_THREADS, smem, s>>>((const K*)a.keys[src], a.vals[src], (K*)a.keys[dst], a.vals[dst], p,
-                                                    a.hist, a.status[p & 1], nxt, a.ctr, a.sticky);
+                                                    a.bit0, a.hist, a.status[p & 1], nxt, a.ctr, a.sticky);
     }
 }
 

@@ -127,7 +127,13 @@ def test_keys_values_ranges_bit_exact_tiny(mode):
     _, st = render(gs, cams[0], mode, stats=True)
     n = _keys_equal(gs, sc, cams[0], mode, comp)
     assert st["n_entries"] == n
-    assert st["sort_passes"] == (4 if mode == oracle.ROOFGS else 5)  # 32 + 8 tile bits -> 5 digits
+    # RoofGS: Gaussians depth-ordered first, then one 8-bit pass over the 8 tile bits;
+    # exact: 32 depth bits + 8 tile bits -> 5 digits
+    assert st["sort_passes"] == (1 if mode == oracle.ROOFGS else 5)
+    if mode == oracle.ROOFGS:  # the paper's 4-pass full-key sort gives the same entries
+        _, st4 = render(gs, cams[0], "roofgs", flags=binding.RG_FLAG_SORT_FULL_KEY, stats=True)
+        assert st4["sort_passes"] == 4
+        _keys_equal(gs, sc, cams[0], mode, comp)
 
 
 # ---------------------------------------------------------------------------
@@ -159,7 +165,8 @@ def test_roofgs_mode_within_fast_exp_bound_tiny(tiny):
 
 
 @pytest.mark.parametrize("flags", [binding.RG_FLAG_EXACT_EXP, binding.RG_FLAG_SINGLE_PIXEL,
-                                   binding.RG_FLAG_EXACT_EXP | binding.RG_FLAG_SINGLE_PIXEL])
+                                   binding.RG_FLAG_EXACT_EXP | binding.RG_FLAG_SINGLE_PIXEL,
+                                   binding.RG_FLAG_SORT_FULL_KEY])
 def test_roofgs_ingredient_toggles(tiny, flags):
     sc, cam, gs, comp = tiny
     img = render(gs, cam, "roofgs", flags=flags)
