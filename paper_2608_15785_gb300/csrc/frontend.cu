@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a
     __shared__ RowTest s_rt[FE_THREADS];    // per-row test of each thread's Gaussian
     __shared__ unsigned s_q[FE_THREADS];    // quantized depth, Eq. (9)
     __shared__ unsigned s_id[FE_THREADS];   // Gaussian index of each slot
+    __shared__ unsigned s_cnt[FE_THREADS];  // entries of each slot's Gaussian
     __shared__ unsigned long long s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -148,7 +149,8 @@ __global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a
     const unsigned rincl = warp_inclusive_scan((unsigned)rows_l, lane);
     const unsigned rexcl = rincl - (unsigned)rows_l;
     const unsigned wrows = __shfl_sync(0xffffffffu, rincl, 31);
-    unsigned cnt = 0;
+    s_cnt[tid] = 0u;
+    __syncwarp();
     for (unsigned r0 = 0; r0 < wrows; r0 += 32) {
         const unsigned k = r0 + (unsigned)lane;
         int owner = 0; // Gaussian (lane) of warp row k
@@ -161,24 +163,18 @@ __global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a
         if (k < wrows && row_range(s_rt[warp * 32 + owner], s_rt[warp * 32 + owner].ty0 + (int)rl, txa, txb))
             w = (unsigned)(txb - txa + 1);
         if (k >= wrows) owner = 32; // past the warp's rows: a segment of its own
-        // segmented sum of w over lanes with the same owner
+        // segmented sum of w over the lanes of one owner; its last lane adds it
         const unsigned owner_prev = __shfl_up_sync(0xffffffffu, (unsigned)owner, 1);
         const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || owner_prev != (unsigned)owner);
         const unsigned wi = warp_inclusive_scan(w, lane);
         const int seg0 = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
         const unsigned before = __shfl_sync(0xffffffffu, wi, seg0 > 0 ? seg0 - 1 : 0);
         const unsigned owner_next = __shfl_down_sync(0xffffffffu, (unsigned)owner, 1);
-        const bool seg_end = lane == 31 || owner_next != (unsigned)owner;
-        const unsigned seg_sum = wi - (seg0 > 0 ? before : 0u);
-        // each Gaussian (lane) collects its segment sums
-#pragma unroll 1
-        for (unsigned m = __ballot_sync(0xffffffffu, seg_end && k < wrows); m; m &= m - 1) {
-            const int src = __ffs(m) - 1;
-            const unsigned o = __shfl_sync(0xffffffffu, (unsigned)owner, src);
-            const unsigned v = __shfl_sync(0xffffffffu, seg_sum, src);
-            if ((unsigned)lane == o) cnt += v;
-        }
+        if ((lane == 31 || owner_next != (unsigned)owner) && k < wrows)
+            s_cnt[warp * 32 + owner] += wi - (seg0 > 0 ? before : 0u);
+        __syncwarp();
     }
+    const unsigned cnt = s_cnt[tid];
 
     // block-level prefix sum of the entry counts
     const unsigned x = warp_inclusive_scan(cnt, lane);

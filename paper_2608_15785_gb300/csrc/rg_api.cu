@@ -321,6 +321,9 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
             a.order = s->gvals[ga.passes & 1].as<unsigned>();
             sa.passes = (F.lay.b_t + 7) / 8;
             sa.bit0 = F.lay.b_d;
+            // depth-ordered entries of one Gaussian row carry consecutive tiles, so the warp
+            // holds many distinct low tile digits: rank that pass with ballots
+            sa.ballot_mask = 1;
         }
         launch_frontend_fused(a, st);
         tile_shift = F.lay.b_d;

@@ -405,6 +405,7 @@ struct SortArgs {
     int key_bytes;        // 4 or 8
     int passes;           // 8-bit digits
     int bit0;             // lowest key bit sorted (digit p = bits bit0 + 8p ..)
+    int ballot_mask;      // bit p: rank pass p with ballots instead of match_any
     unsigned* hist;       // [8][256]
     unsigned* status[2];  // [max_tiles][256] look-back status per pass (alternating)
     long long max_tiles;

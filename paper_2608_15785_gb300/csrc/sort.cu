@@ -24,9 +24,6 @@ namespace rg {
 #ifndef RG_SORT_KPT
 #define RG_SORT_KPT 8
 #endif
-#ifndef RG_SORT_BALLOT_RANK
-#define RG_SORT_BALLOT_RANK 0
-#endif
 constexpr int S_THREADS = RG_SORT_THREADS;
 constexpr int S_KPT = RG_SORT_KPT;
 constexpr int S_TILE = S_THREADS * S_KPT; // 4096 entries
@@ -132,7 +129,8 @@ struct SortSmem {
 template <typename K>
 __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ kin, const unsigned* __restrict__ vin,
                                                         K* __restrict__ kout, unsigned* __restrict__ vout, int pass,
-                                                        int bit0, const unsigned* __restrict__ hist, unsigned* status,
+                                                        int bit0, int ballot_rank, const unsigned* __restrict__ hist,
+                                                        unsigned* status,
                                                         unsigned* status_next, Counters* ctr, Sticky* sticky)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -170,17 +168,18 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
 #pragma unroll
         for (int i = 0; i < S_KPT; i++) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-#if RG_SORT_BALLOT_RANK
-            unsigned peers = 0xffffffffu; // lanes with the same digit: one ballot per digit bit
+            unsigned peers;
+            if (ballot_rank) { // lanes with the same digit: one ballot per digit bit (constant cost)
+                peers = 0xffffffffu;
 #pragma unroll
-            for (int bit = 0; bit < 8; bit++) {
-                const bool on = (d >> bit) & 1u;
-                const unsigned bal = __ballot_sync(0xffffffffu, on);
-                peers &= on ? bal : ~bal;
+                for (int bit = 0; bit < 8; bit++) {
+                    const bool on = (d >> bit) & 1u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, on);
+                    peers &= on ? bal : ~bal;
+                }
+            } else { // hardware match: fast when the warp holds few distinct digits
+                peers = __match_any_sync(0xffffffffu, d);
             }
-#else
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-#endif
             const int leader = __ffs(peers) - 1;
             unsigned b = 0;
             if (lane == leader) {
@@ -307,7 +306,8 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
         const int src = p & 1, dst = src ^ 1;
         unsigned* nxt = (p + 1 < a.passes) ? a.status[(p + 1) & 1] : nullptr;
         k_onesweep<K><<<grid, S_THREADS, smem, s>>>((const K*)a.keys[src], a.vals[src], (K*)a.keys[dst], a.vals[dst], p,
-                                                    a.bit0, a.hist, a.status[p & 1], nxt, a.ctr, a.sticky);
+                                                    a.bit0, (a.ballot_mask >> p) & 1, a.hist, a.status[p & 1], nxt,
+                                                    a.ctr, a.sticky);
     }
 }
 
