@@ -48,6 +48,11 @@ REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_powe
 #     (~9) + o*e + min + alpha test + 1-alpha + T(1-alpha) + stop test + alpha*T
 #     + 3 FFMA + T update = 20.
 OPS = {"roofgs": (5, 11), "exact": (10, 20)}
+STAGES = ["depth_order", "front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"]
+# DRAM bytes per entry of one tile-bit one-sweep pass: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the first tile-bit pass on the 1M-Gaussian 4K case
+# (218.6 MB + 178.7 MB for 27.03 M entries), scaled by the entries of the launch
+SORT_PASS_TRAFFIC_PER_ENTRY = 14.7
 
 
 def parse():
@@ -141,24 +146,28 @@ def stage_work(mode, st, W, H):
     tiles = st["tiles_x"] * st["tiles_y"]
     passes = st["sort_passes"]
     if mode == "roofgs":
-        # depth keys: 16 B mean+log o read, 8 B (q_d, index) written per Gaussian; depth sort of the
-        # N pairs: 4 B histogram + 16 B per pass; fused kernel: 4 B order + 16 B mean+log o per
-        # Gaussian, 16 B FP16 geometry if inside the depth/opacity range, 48 B INT8 SH + 32 B
-        # record if visible, 8 B key+value per entry
+        # depth order: 16 B mean+log o read, 8 B (q_d, index) written per Gaussian, then the stable
+        # sort of those N pairs (4 B histogram + 16 B per pass)
         gpasses = (st["b_d"] + 7) // 8
-        front = 24 * N + (4 + 16 * gpasses) * N + 20 * N + 16 * nf + 80 * nv + 8 * nd
-        sort = 4 * nd + passes * 16 * nd
+        depth = 24 * N + (4 + 16 * gpasses) * N
+        # fused front end: 4 B order + 16 B mean+log o per Gaussian, 16 B FP16 geometry if inside the
+        # depth/opacity range, 48 B INT8 SH + 32 B record if visible, 8 B key+value per entry
+        front = 20 * N + 16 * nf + 80 * nv + 8 * nd
+        sort_pass = 16 * nd  # one pass: each (key, value) entry read once and written once
+        hist = 4 * nd
         ranges = 4 * nd + 8 * tiles
     else:
+        depth = 0
         # preprocess: 44 B geometry per Gaussian, 192 B FP32 SH + 56 B outputs if visible, 4 B count;
         # scan: 8 B per Gaussian; duplicate: 4 B per Gaussian + 24 B per visible + 12 B per entry
         front = 44 * N + 248 * nv + 4 * N + 8 * N + 4 * N + 24 * nv + 12 * nd
-        sort = 8 * nd + passes * 24 * nd
+        sort_pass = 24 * nd
+        hist = 8 * nd
         ranges = 8 * nd + 8 * tiles
     a, b = OPS[mode]
     raster_ops = a * st["n_pairs"] + b * st["n_blends"]
-    return {"front": front, "sort": sort, "ranges": ranges, "raster_ops": raster_ops,
-            "raster_bytes": 36 * nd + 12 * W * H}
+    return {"depth": depth, "front": front, "hist": hist, "sort_pass": sort_pass, "passes": passes,
+            "ranges": ranges, "raster_ops": raster_ops}
 
 
 def mean_stats(stats, poses_used):
@@ -266,19 +275,20 @@ def run_ours(a, rank, world, local_rank):
            "resolution": [a.width, a.height], "tile": [16, 16], "poses": a.poses, "parallelism": "replicas",
            "l2": "inputs larger than L2: 240 MB compact scene read per frame, 99.5 MB image written per frame",
            "entries_per_frame": round(r["stats"]["n_entries"]),
-           "stage_ms": dict(zip(["front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"],
-                                [round(x, 4) for x in r["stage_ms"]]))}
+           "stage_ms": dict(zip(STAGES, [round(x, 4) for x in r["stage_ms"]]))}
     if "exact" in results:
         ex = results["exact"]
         ex_fps = world * ex["steps"] / (ex["ms"] / 1000.0)
         cfg["exact_fps"] = round(ex_fps, 2)
         cfg["speedup_vs_exact"] = round(fps / ex_fps, 3)
-        cfg["exact_stage_ms"] = dict(zip(["front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"],
-                                         [round(x, 4) for x in ex["stage_ms"]]))
+        cfg["exact_stage_ms"] = dict(zip(STAGES, [round(x, 4) for x in ex["stage_ms"]]))
         cfg["exact_entries_per_frame"] = round(ex["stats"]["n_entries"])
     line["config"] = cfg
     line["roofline"], line["stages"] = rooflines(r, a, props, clocks)
-    line["gpu_launches"] = r["steps"] * 8  # front end, histogram, 4 sort passes, ranges, raster
+    # per frame: depth keys, depth-sort histogram + passes, fused front end, entry histogram +
+    # tile-bit passes, ranges, rasterizer
+    gp = (int(r["stats"]["b_d"]) + 7) // 8
+    line["gpu_launches"] = r["steps"] * (1 + 1 + gp + 1 + 1 + int(r["stats"]["sort_passes"]) + 1 + 1)
     line["e2e"] = {"value": round(world * e2e_steps / e2e_s, 2), "unit": UNIT,
                    "h2d_bytes_per_step": 100,  # the rg_camera struct, passed by value per call
                    "d2h_bytes_per_step": 3 * a.width * a.height * 4}
@@ -293,33 +303,47 @@ def run_ours(a, rank, world, local_rank):
 def rooflines(r, a, props, clocks):
     hbm, src = measured_peaks()
     W, H = a.width, a.height
-    work = stage_work("roofgs", r["stats"], W, H)
+    st = r["stats"]
+    work = stage_work("roofgs", st, W, H)
     sms = props.multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     alu_peak = sms * 128 * mhz * 1e6 / 1e9  # FP32-pipe instructions per second (G/s): 128 lanes per SM
-    st_ms = dict(zip(["front", "hist", "passes", "ranges", "raster"], r["stage_ms"][:5]))
-    sort_ms = st_ms["hist"] + st_ms["passes"]
+    ms = dict(zip(STAGES, r["stage_ms"]))
+
+    def hbm_stage(bytes_, t_ms):
+        return {"bound": "hbm", "achieved": bytes_ / (t_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s", "ms": t_ms,
+                "bytes": bytes_}
+
+    passes = max(work["passes"], 1)
     stages = {
-        "front_end": {"bound": "hbm", "achieved": work["front"] / (st_ms["front"] * 1e-3) / 1e9, "peak": hbm,
-                      "unit": "GB/s", "ms": st_ms["front"], "bytes": work["front"]},
-        "sort": {"bound": "hbm", "achieved": work["sort"] / (sort_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                 "ms": sort_ms, "bytes": work["sort"]},
-        "ranges": {"bound": "hbm", "achieved": work["ranges"] / (st_ms["ranges"] * 1e-3) / 1e9, "peak": hbm,
-                   "unit": "GB/s", "ms": st_ms["ranges"], "bytes": work["ranges"]},
-        "raster": {"bound": "alu", "achieved": work["raster_ops"] / (st_ms["raster"] * 1e-3) / 1e9, "peak": alu_peak,
-                   "unit": "Gop/s", "ms": st_ms["raster"], "ops": work["raster_ops"]},
+        "depth_order": hbm_stage(work["depth"], ms["depth_order"]),
+        "front_end": hbm_stage(work["front"], ms["front_end"]),
+        "sort_hist": hbm_stage(work["hist"], ms["sort_hist"]),
+        "sort_pass": hbm_stage(work["sort_pass"], ms["sort_passes"] / passes),
+        "ranges": hbm_stage(work["ranges"], ms["ranges"]),
+        "raster": {"bound": "alu", "achieved": work["raster_ops"] / (ms["raster"] * 1e-3) / 1e9, "peak": alu_peak,
+                   "unit": "Gop/s", "ms": ms["raster"], "ops": work["raster_ops"]},
     }
+    stages["sort_pass"]["launches_per_frame"] = work["passes"]
     for v in stages.values():
         v["frac"] = round(v["achieved"] / v["peak"], 4)
         v["achieved"] = round(v["achieved"], 1)
         v["peak"] = round(v["peak"], 1)
         v["ms"] = round(v["ms"], 4)
-    dom = max(stages, key=lambda k: stages[k]["ms"])
+    # dominant kernel: largest device time per frame (launches x duration)
+    share = {k: v["ms"] * v.get("launches_per_frame", 1) for k, v in stages.items()}
+    dom = max(share, key=share.get)
     d = stages[dom]
-    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-            "frac": d["frac"], "traffic": None,
-            "peak_source": (src + " HBM copy bandwidth") if d["bound"] == "hbm"
-            else "%d SMs x 128 FP32 lanes x %.0f MHz median SM clock under load" % (sms, mhz)}
+    traffic = None
+    if dom == "sort_pass" and SORT_PASS_TRAFFIC_PER_ENTRY:
+        traffic = round(SORT_PASS_TRAFFIC_PER_ENTRY * st["n_entries"])
+    names = {"sort_pass": "k_onesweep<uint32> (one tile-bit pass)", "raster": "k_raster_roofgs<fast, dual>",
+             "front_end": "k_frontend_fused", "depth_order": "k_depth_keys + per-Gaussian sort",
+             "sort_hist": "k_sort_hist<uint32>", "ranges": "k_ranges<uint32>"}
+    roof = {"kernel": names[dom], "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+            "unit": d["unit"], "frac": d["frac"], "traffic": traffic,
+            "peak_source": ("of measured HBM copy bandwidth" if src == "measured" else "of fallback HBM bandwidth")
+            if d["bound"] == "hbm" else "%d SMs x 128 FP32 lanes x %.0f MHz median SM clock under load" % (sms, mhz)}
     return roof, stages
 
 

@@ -183,11 +183,13 @@ rg_status rg_scene_check(rg_scene* scene, void* stream);
 
 /*
  * Per-stage device times (ms) of the frames rendered with RG_FLAG_STAGE_EVENTS
- * since the last call, summed: ms[0..5] = front end (exact: preprocess + scan +
- * duplicate), sort histogram, sort passes, tile ranges, rasterizer, whole frame.
- * *frames receives the number of frames summed. Synchronises the recorded events.
+ * since the last call (at most the last 512 frames), summed: ms7[0] = depth order of
+ * the Gaussians (RoofGS; 0 otherwise), ms7[1] = front end (RoofGS fused kernel; exact
+ * preprocess + scan + duplicate), ms7[2] = sort histogram, ms7[3] = sort passes,
+ * ms7[4] = tile ranges, ms7[5] = rasterizer, ms7[6] = whole frame. *frames receives
+ * the number of frames summed. Synchronises the recorded events.
  */
-rg_status rg_stage_times(rg_scene* scene, float* ms6, int32_t* frames);
+rg_status rg_stage_times(rg_scene* scene, float* ms7, int32_t* frames);
 
 /* rg_inspect selectors: copy internal buffers of the last frame to host memory */
 #define RG_INSPECT_KEYS 1        /* sorted keys: uint32 (RoofGS) or uint64 (exact), n_entries of them */
@@ -240,13 +242,39 @@ rg_status rg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, int64_t n, int32
                                 void* stream);
 
 /*
- * Not built yet (return RG_ERR_UNSUPPORTED): batched multi-view rendering,
- * the rasterizer/preprocess backward, and the request loop.
+ * Gradients of an exact-mode render (not in the paper: the backward of the
+ * forward of Sec. III-D, Eqs. (7), (10)-(12)). Output arrays are caller-owned
+ * device buffers with the layout of rg_scene_desc; every value is written.
+ */
+typedef struct {
+    float* means;     /* [n][3] dL/dmeans */
+    float* scales;    /* [n][3] dL/dscales (activated scales) */
+    float* quats;     /* [n][4] dL/dquats (raw quaternion, through the normalisation) */
+    float* opacities; /* [n]    dL/dopacities (activated) */
+    float* sh;        /* [n][16][3] dL/dSH */
+} rg_grads;
+
+/*
+ * Given dL/dimage (device [3][H][W]) for the image rg_render produces for this
+ * scene, camera and opts, write the gradients of L with respect to the scene's
+ * FP32 attributes. Runs the front end, sort and ranges of the frame again,
+ * then a rasterizer backward that replays each pixel's front-to-back blend to
+ * recover its transmittance (nothing is stored between forward and backward),
+ * walks the pairs back to front, and a per-Gaussian backward through the conic,
+ * the EWA covariance, the quaternion rotation, the projected mean and the SH
+ * colour. Synchronises the stream once (to check the entry capacity).
+ * Errors: RG_ERR_UNSUPPORTED for RoofGS mode (INT8/FP16 storage and the
+ * bit-level exponential are not differentiated), RG_ERR_INVALID_ARG, ...
+ */
+rg_status rg_backward(rg_scene* scene, const rg_camera* cam, const rg_render_opts* opts, const float* dL_dimg,
+                      const rg_grads* grads, void* stream);
+
+/*
+ * Not built yet (return RG_ERR_UNSUPPORTED): batched multi-view rendering and
+ * the request loop.
  */
 rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
                           const rg_render_opts* opts, float* const* outs, void* stream);
-rg_status rg_backward(rg_scene* scene, const rg_camera* cam, const rg_render_opts* opts, const float* dL_dimg,
-                      float* grads, void* stream);
 rg_status rg_submit(rg_server* server, const rg_camera* cam, int32_t scene_slot, uint64_t* ticket);
 rg_status rg_poll(rg_server* server, uint64_t ticket, float* out_chw);
 

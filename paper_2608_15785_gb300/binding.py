@@ -64,6 +64,11 @@ class RgOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("flags", C.c_uint32), ("tile_w", C.c_int32), ("tile_h", C.c_int32)]
 
 
+class RgGrads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacities", C.c_void_p),
+                ("sh", C.c_void_p)]
+
+
 class RgStats(C.Structure):
     _fields_ = [("n_gaussians", C.c_int64), ("n_front", C.c_int64), ("n_visible", C.c_int64),
                 ("n_entries", C.c_int64), ("capacity", C.c_int64), ("n_pairs", C.c_int64), ("n_blends", C.c_int64),
@@ -95,7 +100,7 @@ def lib():
         L.rg_inspect.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
         L.rg_eval_fast_exp.argtypes = [P, P, C.c_int64, P]
         L.rg_render_batch.argtypes = [P, P, P, C.c_int32, P, P, P]
-        L.rg_backward.argtypes = [P, P, P, P, P, P]
+        L.rg_backward.argtypes = [P, C.POINTER(RgCamera), C.POINTER(RgOpts), P, C.POINTER(RgGrads), P]
         L.rg_submit.argtypes = [P, P, C.c_int32, P]
         L.rg_poll.argtypes = [P, C.c_uint64, P]
         L.rg_sort_pairs_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P, P]
@@ -195,6 +200,20 @@ class Scene:
                               C.byref(st) if st is not None else None, _stream_ptr(stream)))
         return (out, st.as_dict()) if stats else out
 
+    def backward(self, cam, dL_dimg, stream=None) -> dict:
+        """Gradients of L w.r.t. the FP32 attributes, given dL/dimage of the exact-mode render."""
+        import torch
+        g = {"means": torch.empty((self.n, 3), device="cuda"), "scales": torch.empty((self.n, 3), device="cuda"),
+             "quats": torch.empty((self.n, 4), device="cuda"), "opacities": torch.empty((self.n,), device="cuda"),
+             "sh": torch.empty((self.n, 16, 3), device="cuda")}
+        gg = RgGrads(*(g[k].data_ptr() for k in ("means", "scales", "quats", "opacities", "sh")))
+        c = camera_struct(cam)
+        o = RgOpts(RG_MODE_EXACT, 0, 16, 16)
+        d = dL_dimg.contiguous().float()
+        check(lib().rg_backward(self._h, C.byref(c), C.byref(o), C.c_void_p(d.data_ptr()), C.byref(gg),
+                                _stream_ptr(stream)))
+        return g
+
     def reserve(self, n_entries: int):
         check(lib().rg_scene_reserve(self._h, int(n_entries)))
 
@@ -202,7 +221,7 @@ class Scene:
         check(lib().rg_scene_check(self._h, _stream_ptr(stream)))
 
     def stage_times(self):
-        ms = (C.c_float * 6)()
+        ms = (C.c_float * 7)()
         fr = C.c_int32()
         check(lib().rg_stage_times(self._h, ms, C.byref(fr)))
         return list(ms), fr.value

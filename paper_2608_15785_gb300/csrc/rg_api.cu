@@ -65,7 +65,7 @@ rg_status ensure(DevBuf& b, size_t bytes, const char* what)
 }
 
 constexpr int EV_RING = 512;
-constexpr int EV_PER_FRAME = 6; // start, front end, histogram, sort, ranges, raster
+constexpr int EV_PER_FRAME = 7; // start, depth order, front end, histogram, sort, ranges, raster
 constexpr long long MAX_CAP = (1ll << 30) - 1;
 constexpr size_t CTRL_BYTES = sizeof(Counters) + 8 * 256 * sizeof(unsigned);
 constexpr size_t CTRL_ALLOC = 2 * CTRL_BYTES; // frame counters + the per-Gaussian depth sort's
@@ -96,6 +96,7 @@ struct rg_scene {
     DevBuf xy, depth, conic, rgb, rect, touched, offsets; // exact per-Gaussian
     DevBuf rec;                                           // RoofGS raster records
     DevBuf gkeys[2], gvals[2], gstatus[2];                // RoofGS per-Gaussian depth sort
+    DevBuf gbuf;                                          // backward: image-space gradients [n][9]
     // last frame
     int last_mode = -1;
     int last_passes = 0;
@@ -265,6 +266,7 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
         a.ctr = ctr;
         a.sticky = sticky;
         RG_CK(cudaMemsetAsync(s->lb_status.p, 0, (size_t)((n + 2047) / 2048 + 1) * 8, st));
+        if (ev) RG_CK(cudaEventRecord(E[1], st));
         launch_exact_preprocess(a, st);
         launch_exact_scan(a, st);
         launch_exact_duplicate(a, st);
@@ -296,6 +298,7 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
             // the paper's scheme: entries in Gaussian order, 4 passes over the 32-bit key
             sa.passes = 4;
             sa.bit0 = 0;
+            if (ev) RG_CK(cudaEventRecord(E[1], st));
         } else {
             // Gaussians sorted by quantized depth first (stable, ties by index); the
             // entries then come out in (q_d, index) order and a stable sort of the
@@ -319,6 +322,7 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
             launch_depth_keys(a, s->gkeys[0].as<unsigned>(), s->gvals[0].as<unsigned>(), gctr, st);
             launch_sort(ga, st, nullptr);
             a.order = s->gvals[ga.passes & 1].as<unsigned>();
+            if (ev) RG_CK(cudaEventRecord(E[1], st));
             sa.passes = (F.lay.b_t + 7) / 8;
             sa.bit0 = F.lay.b_d;
             // depth-ordered entries of one Gaussian row carry consecutive tiles, so the warp
@@ -328,9 +332,10 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
         launch_frontend_fused(a, st);
         tile_shift = F.lay.b_d;
     }
-    if (ev) RG_CK(cudaEventRecord(E[1], st));
-    launch_sort(sa, st, ev ? E[2] : nullptr);
-    if (ev) RG_CK(cudaEventRecord(E[3], st));
+    if (ev) RG_CK(cudaEventRecord(E[2], st));
+    if (ev && sa.passes <= 0) RG_CK(cudaEventRecord(E[3], st));
+    launch_sort(sa, st, ev ? E[3] : nullptr);
+    if (ev) RG_CK(cudaEventRecord(E[4], st));
     const int fin = sa.passes & 1;
     RangeArgs ra;
     ra.keys = s->keys[fin].p;
@@ -340,7 +345,15 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
     ra.ranges = s->ranges.as<uint2>();
     ra.ctr = ctr;
     launch_ranges(ra, st);
-    if (ev) RG_CK(cudaEventRecord(E[4], st));
+    if (ev) RG_CK(cudaEventRecord(E[5], st));
+    s->last_mode = mode;
+    s->last_passes = sa.passes;
+    s->last_tiles = F.tiles;
+    if (!out) { // front end, sort and ranges only (the backward replays the blend itself)
+        if (ev) RG_CK(cudaEventRecord(E[6], st));
+        RG_CK(cudaGetLastError());
+        return RG_OK;
+    }
     RasterArgs r;
     memset(&r, 0, sizeof(r));
     r.ranges = s->ranges.as<uint2>();
@@ -362,7 +375,7 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
         r.dual_pixel = (flags & RG_FLAG_SINGLE_PIXEL) ? 0 : 1;
         launch_raster_roofgs(r, st);
     }
-    if (ev) RG_CK(cudaEventRecord(E[5], st));
+    if (ev) RG_CK(cudaEventRecord(E[6], st));
     RG_CK(cudaGetLastError());
     s->last_mode = mode;
     s->last_passes = sa.passes;
@@ -379,7 +392,7 @@ rg_status upload(DevBuf& dst, const float* src, size_t count, int on_device, cud
 
 void destroy_scene(rg_scene* s)
 {
-    DevBuf* bufs[] = {&s->gkeys[0], &s->gkeys[1], &s->gvals[0], &s->gvals[1], &s->gstatus[0], &s->gstatus[1],
+    DevBuf* bufs[] = {&s->gbuf, &s->gkeys[0], &s->gkeys[1], &s->gvals[0], &s->gvals[1], &s->gstatus[0], &s->gstatus[1],
                       &s->means, &s->scales, &s->quats, &s->opac, &s->sh, &s->geoA, &s->geoB, &s->shq, &s->keys[0],
                       &s->keys[1], &s->vals[0], &s->vals[1], &s->ranges, &s->ctrl, &s->sticky, &s->lb_status,
                       &s->sort_status[0], &s->sort_status[1], &s->xy, &s->depth, &s->conic, &s->rgb, &s->rect,
@@ -599,24 +612,24 @@ rg_status rg_scene_check(rg_scene* s, void* stream)
     return RG_OK;
 }
 
-rg_status rg_stage_times(rg_scene* s, float* ms6, int32_t* frames)
+rg_status rg_stage_times(rg_scene* s, float* ms7, int32_t* frames)
 {
-    if (!s || !ms6) return fail(RG_ERR_INVALID_ARG, "NULL argument");
-    for (int k = 0; k < 6; k++) ms6[k] = 0.0f;
+    if (!s || !ms7) return fail(RG_ERR_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < 7; k++) ms7[k] = 0.0f;
     const int cnt = s->ev_pending;
     if (frames) *frames = cnt;
     if (!s->ev_init || cnt == 0) return RG_OK;
     for (int f = 0; f < cnt; f++) {
         const int slot = ((s->ev_next - 1 - f) % EV_RING + EV_RING) % EV_RING;
         cudaEvent_t* E = s->ev[slot];
-        RG_CK(cudaEventSynchronize(E[5]));
+        RG_CK(cudaEventSynchronize(E[6]));
         float t;
-        RG_CK(cudaEventElapsedTime(&t, E[0], E[1])); ms6[0] += t;
-        RG_CK(cudaEventElapsedTime(&t, E[1], E[2])); ms6[1] += t;
-        RG_CK(cudaEventElapsedTime(&t, E[2], E[3])); ms6[2] += t;
-        RG_CK(cudaEventElapsedTime(&t, E[3], E[4])); ms6[3] += t;
-        RG_CK(cudaEventElapsedTime(&t, E[4], E[5])); ms6[4] += t;
-        RG_CK(cudaEventElapsedTime(&t, E[0], E[5])); ms6[5] += t;
+        for (int k = 0; k < 6; k++) {
+            RG_CK(cudaEventElapsedTime(&t, E[k], E[k + 1]));
+            ms7[k] += t;
+        }
+        RG_CK(cudaEventElapsedTime(&t, E[0], E[6]));
+        ms7[6] += t;
     }
     s->ev_pending = 0;
     return RG_OK;
@@ -718,9 +731,67 @@ rg_status rg_render_batch(rg_scene* const*, const int32_t*, const rg_camera*, in
     return fail(RG_ERR_UNSUPPORTED, "rg_render_batch is not built yet");
 }
 
-rg_status rg_backward(rg_scene*, const rg_camera*, const rg_render_opts*, const float*, float*, void*)
+rg_status rg_backward(rg_scene* s, const rg_camera* cam, const rg_render_opts* opts, const float* dL_dimg,
+                      const rg_grads* grads, void* stream)
 {
-    return fail(RG_ERR_UNSUPPORTED, "rg_backward is not built yet");
+    if (!s || !opts || !dL_dimg || !grads) return fail(RG_ERR_INVALID_ARG, "NULL argument");
+    if (opts->mode != RG_MODE_EXACT)
+        return fail(RG_ERR_UNSUPPORTED, "rg_backward differentiates exact mode only (RoofGS storage is INT8/FP16)");
+    if (!(s->storage & RG_STORE_FP32)) return fail(RG_ERR_INVALID_ARG, "rg_backward needs RG_STORE_FP32");
+    const int tw = opts->tile_w ? opts->tile_w : TILE, th = opts->tile_h ? opts->tile_h : TILE;
+    if (tw != TILE || th != TILE) return fail(RG_ERR_UNSUPPORTED, "only 16x16 tiles are built");
+    if (s->n > 0 && (!grads->means || !grads->scales || !grads->quats || !grads->opacities || !grads->sh))
+        return fail(RG_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    FrameLayout F;
+    RG_TRY(make_layout(cam, F));
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t cap = s->cap > 0 ? s->cap : std::max<int64_t>(1 << 20, 4 * s->n);
+    if (cap > MAX_CAP) cap = MAX_CAP;
+    RG_TRY(ensure_workspace(s, RG_MODE_EXACT, F.tiles, cap));
+    // forward front end, sort and ranges of this camera (checked: the gradient needs every entry)
+    for (int attempt = 0; attempt < 2; attempt++) {
+        RG_TRY(render_once(s, F, RG_MODE_EXACT, 0u, nullptr, st));
+        Counters c;
+        RG_CK(cudaMemcpyAsync(&c, s->ctrl.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+        RG_CK(cudaStreamSynchronize(st));
+        if (c.error) return fail(RG_ERR_TIMEOUT, "a bounded device wait gave up");
+        if (c.n_entries_total <= (unsigned long long)s->cap) break;
+        if (attempt == 1) return fail(RG_ERR_CAPACITY, "workspace could not grow enough");
+        int64_t want = (int64_t)(c.n_entries_total + c.n_entries_total / 4 + 1024);
+        if (want > MAX_CAP) return fail(RG_ERR_CAPACITY, "frame needs more than 2^30 - 1 entries");
+        RG_TRY(rg_scene_reserve(s, want));
+    }
+    RG_TRY(ensure(s->gbuf, (size_t)(s->n > 0 ? s->n : 1) * 9 * 4, "gradient buffer"));
+    RG_CK(cudaMemsetAsync(s->gbuf.p, 0, (size_t)(s->n > 0 ? s->n : 1) * 9 * 4, st));
+    BackwardArgs b;
+    memset(&b, 0, sizeof(b));
+    const int fin = s->last_passes & 1;
+    b.ranges = s->ranges.as<uint2>();
+    b.vals = s->vals[fin].as<unsigned>();
+    b.n = s->n;
+    b.tiles_x = F.lay.tiles_x;
+    b.tiles_y = F.lay.tiles_y;
+    b.cam = F.cam;
+    b.xy = s->xy.as<float2>();
+    b.conic_op = s->conic.as<float4>();
+    b.rgb = s->rgb.as<float>();
+    b.touched = s->touched.as<unsigned>();
+    b.means = s->means.as<float>();
+    b.scales = s->scales.as<float>();
+    b.quats = s->quats.as<float>();
+    b.sh = s->sh.as<float>();
+    b.sh_degree = s->sh_degree;
+    b.dL_dimg = dL_dimg;
+    b.gbuf = s->gbuf.as<float>();
+    b.dmeans = grads->means;
+    b.dscales = grads->scales;
+    b.dquats = grads->quats;
+    b.dopac = grads->opacities;
+    b.dsh = grads->sh;
+    launch_raster_backward(b, st);
+    launch_preprocess_backward(b, st);
+    RG_CK(cudaGetLastError());
+    return RG_OK;
 }
 
 rg_status rg_submit(rg_server*, const rg_camera*, int32_t, uint64_t*)

@@ -446,6 +446,37 @@ void launch_raster_roofgs(const RasterArgs& a, cudaStream_t s);
 void launch_raster_exact(const RasterArgs& a, cudaStream_t s);
 void launch_fast_exp_eval(const float* P, float* out, long long n, cudaStream_t s);
 
+struct BackwardArgs {
+    // forward state of the frame (exact mode)
+    const uint2* ranges;
+    const unsigned* vals;
+    long long n;
+    int tiles_x, tiles_y;
+    CamDev cam;
+    const float2* xy;
+    const float4* conic_op;
+    const float* rgb;
+    const unsigned* touched;
+    // scene attributes (FP32)
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* sh;
+    int sh_degree;
+    // dL/dimage [3][H][W] and per-Gaussian image-space gradients [n][9]:
+    // d(u, v), d(conic A, B, C), d(opacity), d(rgb)
+    const float* dL_dimg;
+    float* gbuf;
+    // outputs
+    float* dmeans;
+    float* dscales;
+    float* dquats;
+    float* dopac;
+    float* dsh;
+};
+void launch_raster_backward(const BackwardArgs& a, cudaStream_t s);
+void launch_preprocess_backward(const BackwardArgs& a, cudaStream_t s);
+
 // Sets the message that rg_last_error() returns on this thread.
 void set_last_error(const char* msg);
 

@@ -59,7 +59,7 @@ def test_bad_arguments_are_rejected_without_a_gpu(L):
     assert L.rg_scene_create(C.byref(d), None, C.byref(out)) == 1  # NULL attribute pointers
     assert L.rg_render(None, None, None, None, None, None) == 1
     assert L.rg_render_batch(None, None, None, 0, None, None, None) == 8  # RG_ERR_UNSUPPORTED
-    assert L.rg_backward(None, None, None, None, None, None) == 8
+    assert L.rg_backward(None, None, None, None, None, None) == 1  # NULL arguments
     assert L.rg_submit(None, None, 0, None) == 8
     assert L.rg_poll(None, 0, None) == 8
     assert L.rg_eval_fast_exp(None, None, -1, None) == 1

@@ -1,0 +1,158 @@
+"""Backward of the exact-mode render (rg_backward), through the C ABI.
+
+Reference: central finite differences of the FP64 oracle render of
+L = sum(w * image) with fixed random weights w, on a 256x256 view of a
+1,000-Gaussian subset. The forward is piecewise smooth (the 1/255 skip, the
+1e-4 stop and the 0.99 clamp are kinks or steps), so every finite difference is
+taken with two step sizes and a sample whose two estimates disagree (it sits
+on a step) is set aside and counted; the rest must match the GPU gradient.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_15785_gb300 import binding, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_15785_gb300.build import build
+    build()
+
+
+def _scene():
+    full = synth.tiny_scene(10_000, seed=0)
+    rng = np.random.default_rng(4)
+    idx = np.sort(rng.choice(full.n, 1000, replace=False))
+    sc = full.subset(idx)
+    sc.scales = (sc.scales * 2.5).astype(np.float32)  # fewer, larger Gaussians: more pixels per gradient
+    return sc
+
+
+def _loss_oracle(sc, cam, w):
+    img, _, _ = oracle.render(sc, cam, oracle.EXACT, with_diag=False)
+    return float(np.sum(w * img))
+
+
+FIELDS = {"means": 3, "scales": 3, "quats": 4, "opacities": 1, "sh": 48}
+
+
+def _perturbed(sc, field, i, k, value):
+    out = sc.subset(np.arange(sc.n))
+    arr = getattr(out, field)
+    if field == "sh":
+        arr[i].reshape(-1)[k] = value
+    elif arr.ndim == 1:
+        arr[i] = value
+    else:
+        arr[i, k] = value
+    return out
+
+
+def _get(sc, field, i, k):
+    arr = getattr(sc, field)
+    if field == "sh":
+        return float(arr[i].reshape(-1)[k])
+    return float(arr[i] if arr.ndim == 1 else arr[i, k])
+
+
+def _fd(sc, cam, w, field, i, k, rel):
+    x0 = _get(sc, field, i, k)
+    h = rel * max(abs(x0), 0.05 if field != "sh" else 0.3)
+    xp, xm = np.float32(x0 + h), np.float32(x0 - h)
+    lp = _loss_oracle(_perturbed(sc, field, i, k, xp), cam, w)
+    lm = _loss_oracle(_perturbed(sc, field, i, k, xm), cam, w)
+    return (lp - lm) / (float(xp) - float(xm))
+
+
+def test_backward_matches_fp64_finite_differences():
+    sc = _scene()
+    cam = synth.tiny_camera(256, 256, bg=(0.1, 0.3, 0.2))
+    rng = np.random.default_rng(7)
+    w = rng.normal(size=(3, 256, 256))
+    gs = binding.Scene(sc, storage=binding.RG_STORE_FP32)
+    g = gs.backward(cam, torch.from_numpy(w.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+    # Gaussians that reach the image
+    k_, v_, _, _ = oracle.keys(sc, cam, oracle.EXACT)
+    vis = np.unique(v_)
+    samples = []
+    for field, dim in FIELDS.items():
+        for _ in range(8 if field != "sh" else 10):
+            i = int(rng.choice(vis))
+            k = int(rng.integers(dim))
+            if field == "sh":
+                k = int(rng.integers(3)) if _ < 4 else k  # include DC terms
+            samples.append((field, i, k))
+    checked = skipped = 0
+    scale = {f: np.abs(g[f][vis]).mean() + 1e-12 for f in FIELDS}
+    for field, i, k in samples:
+        a = _fd(sc, cam, w, field, i, k, 1e-4)
+        b = _fd(sc, cam, w, field, i, k, 5e-5)
+        if abs(a - b) > 1e-3 * (abs(a) + scale[field]):
+            skipped += 1  # a skip/stop/clamp step lies within the difference interval
+            continue
+        gv = g[field][i].reshape(-1)[k] if field == "sh" else (g[field][i] if g[field].ndim == 1 else g[field][i, k])
+        assert abs(gv - a) <= 2e-3 * abs(a) + 2e-3 * scale[field], (field, i, k, gv, a)
+        checked += 1
+    print("backward: %d gradients checked against FP64 finite differences, %d on a step set aside" %
+          (checked, skipped))
+    assert checked >= 0.8 * len(samples)
+
+
+def test_backward_matches_fp32_gpu_finite_differences():
+    """Coarse second reference: central differences of the GPU forward itself."""
+    sc = _scene()
+    cam = synth.tiny_camera(256, 256)
+    rng = np.random.default_rng(9)
+    w = torch.from_numpy(rng.normal(size=(3, 256, 256)).astype(np.float32)).cuda()
+    g = binding.Scene(sc, storage=binding.RG_STORE_FP32).backward(cam, w)
+    gm = g["means"].cpu().numpy()
+    top = np.argsort(-np.abs(gm[:, 0]))[:8]  # the largest x-gradients are well above FP32 noise
+
+    def fd(i, h):
+        vals = []
+        for sgn in (+1, -1):
+            s2 = sc.subset(np.arange(sc.n))
+            s2.means[i, 0] = np.float32(s2.means[i, 0] + sgn * h)
+            img = binding.Scene(s2, storage=binding.RG_STORE_FP32).render(cam, mode="exact")
+            vals.append(float((img.double() * w.double()).sum()))
+        return (vals[0] - vals[1]) / (2 * h)
+
+    checked = 0
+    for i in top:
+        a, b = fd(i, 1e-3), fd(i, 5e-4)
+        if abs(a - b) > 0.02 * abs(a):
+            continue  # a step of the forward lies within the interval
+        assert abs(a - gm[i, 0]) <= 0.05 * abs(gm[i, 0]), (i, a, gm[i, 0])
+        checked += 1
+    assert checked >= 4
+
+
+def test_autograd_function_and_unsupported_mode():
+    from paper_2608_15785_gb300.autograd import render_exact
+    sc = _scene()
+    cam = synth.tiny_camera(128, 96)
+    t = {f: torch.from_numpy(getattr(sc, f)).cuda().requires_grad_(True)
+         for f in ("means", "scales", "quats", "opacities", "sh")}
+    w = torch.randn(3, 96, 128, device="cuda")
+    img = render_exact(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], cam)
+    (img * w).sum().backward()
+    ref = binding.Scene(sc, storage=binding.RG_STORE_FP32).backward(cam, w)
+    for f in t:
+        assert torch.allclose(t[f].grad, ref[f], rtol=1e-5, atol=1e-7), f
+    gs = binding.Scene(sc)
+    import ctypes as C
+    o = binding.RgOpts(binding.RG_MODE_ROOFGS, 0, 16, 16)
+    c = binding.camera_struct(cam)
+    gg = binding.RgGrads(*(ref[k].data_ptr() for k in ("means", "scales", "quats", "opacities", "sh")))
+    assert binding.lib().rg_backward(gs.handle, C.byref(c), C.byref(o), C.c_void_p(w.data_ptr()), C.byref(gg),
+                                     None) == 8

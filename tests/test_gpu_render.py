@@ -296,7 +296,8 @@ def test_stage_times_and_counters(tiny):
     for _ in range(3):
         gs.render(cam, flags=binding.RG_FLAG_STAGE_EVENTS)
     ms, frames = gs.stage_times()
-    assert frames == 3 and all(m >= 0 for m in ms) and ms[5] > 0
+    assert frames == 3 and all(m >= 0 for m in ms) and ms[6] > 0
+    assert abs(sum(ms[:6]) - ms[6]) < 0.05 * ms[6] + 1e-3
     _, st = render(gs, cam, "roofgs", stats=True)
     assert 0 < st["n_visible"] <= st["n_front"] <= sc.n
     assert st["n_blends"] <= st["n_pairs"]
