@@ -148,7 +148,8 @@ def test_autograd_function_and_unsupported_mode():
     (img * w).sum().backward()
     ref = binding.Scene(sc, storage=binding.RG_STORE_FP32).backward(cam, w)
     for f in t:
-        assert torch.allclose(t[f].grad, ref[f], rtol=1e-5, atol=1e-7), f
+        # the per-Gaussian sums use atomics, so two backward runs agree to rounding only
+        assert torch.allclose(t[f].grad, ref[f], rtol=1e-4, atol=1e-5 * float(ref[f].abs().max())), f
     gs = binding.Scene(sc)
     import ctypes as C
     o = binding.RgOpts(binding.RG_MODE_ROOFGS, 0, 16, 16)
