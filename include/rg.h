@@ -116,6 +116,7 @@ typedef struct {
 #define RG_FLAG_SORT_FULL_KEY (1u << 2)
 /* flags for both modes */
 #define RG_FLAG_STAGE_EVENTS (1u << 8) /* record per-stage CUDA events (rg_stage_times) */
+#define RG_FLAG_BATCH_CHECKED (1u << 9) /* rg_render_batch: synchronise, and re-size and render again on overflow */
 
 typedef struct {
     int32_t mode;   /* RG_MODE_EXACT or RG_MODE_ROOFGS */
@@ -270,11 +271,32 @@ rg_status rg_backward(rg_scene* scene, const rg_camera* cam, const rg_render_opt
                       const rg_grads* grads, void* stream);
 
 /*
- * Not built yet (return RG_ERR_UNSUPPORTED): batched multi-view rendering and
- * the request loop.
+ * Batched multi-view rendering (not in the paper; serving-oriented). View v is
+ * rendered from scenes[scene_idx[v]] with cams[v] (any resolution) into outs[v]
+ * (device [3][H][W], caller-owned), all in opts->mode. The first call for a set of
+ * (scenes, resolutions, mode, flags) creates a plan: lanes of stream + workspace,
+ * sized by rendering every view once (synchronous), then an autotuner times the
+ * captured batch with 1, 2 and 4 lanes and with 1 or 2 pixels per thread (RoofGS)
+ * and keeps the fastest. Every call captures each view's pipeline on its lane
+ * (view v on lane v mod lanes) into one CUDA graph, updates the plan's instantiated
+ * graph in place (cameras are kernel parameters) and launches it once on `stream`:
+ * no host synchronisation (unless RG_FLAG_BATCH_CHECKED). Images are identical to
+ * rg_render's. An entry overflow is recorded in the scene's sticky flags
+ * (rg_scene_check), as for rg_render without stats. Views of one lane run in
+ * order; lanes run concurrently, so scenes may repeat across views freely.
+ * A plan keeps its workspaces until one of its scenes is destroyed (at most 8
+ * plans are kept). Tile shape is fixed (16x16).
  */
 rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
                           const rg_render_opts* opts, float* const* outs, void* stream);
+
+/* The autotuned lane count and pixels per thread of the plan for these views (0, 0 if none). */
+rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
+                             const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread);
+
+/*
+ * Not built yet (return RG_ERR_UNSUPPORTED): the request loop.
+ */
 rg_status rg_submit(rg_server* server, const rg_camera* cam, int32_t scene_slot, uint64_t* ticket);
 rg_status rg_poll(rg_server* server, uint64_t ticket, float* out_chw);
 

@@ -27,6 +27,7 @@ RG_FLAG_EXACT_EXP = 1 << 0
 RG_FLAG_SINGLE_PIXEL = 1 << 1
 RG_FLAG_SORT_FULL_KEY = 1 << 2
 RG_FLAG_STAGE_EVENTS = 1 << 8
+RG_FLAG_BATCH_CHECKED = 1 << 9
 RG_INSPECT_KEYS = 1
 RG_INSPECT_VALUES = 2
 RG_INSPECT_RANGES = 3
@@ -39,7 +40,7 @@ RG_INSPECT_LOG_OPACITY = 8
 # every entry point include/rg.h declares
 EXPORTS = ["rg_scene_create", "rg_scene_destroy", "rg_scene_reserve", "rg_render", "rg_scene_check",
            "rg_stage_times", "rg_inspect", "rg_eval_fast_exp", "rg_render_batch", "rg_backward", "rg_submit",
-           "rg_poll", "rg_last_error", "rg_version", "rg_sort_pairs_noalloc"]
+           "rg_poll", "rg_last_error", "rg_version", "rg_sort_pairs_noalloc", "rg_batch_plan_info"]
 
 
 class RgError(RuntimeError):
@@ -99,7 +100,8 @@ def lib():
         L.rg_stage_times.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_int32)]
         L.rg_inspect.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
         L.rg_eval_fast_exp.argtypes = [P, P, C.c_int64, P]
-        L.rg_render_batch.argtypes = [P, P, P, C.c_int32, P, P, P]
+        L.rg_render_batch.argtypes = [P, P, P, C.c_int32, C.POINTER(RgOpts), P, P]
+        L.rg_batch_plan_info.argtypes = [P, P, P, C.c_int32, C.POINTER(RgOpts), P, P]
         L.rg_backward.argtypes = [P, C.POINTER(RgCamera), C.POINTER(RgOpts), P, C.POINTER(RgGrads), P]
         L.rg_submit.argtypes = [P, P, C.c_int32, P]
         L.rg_poll.argtypes = [P, C.c_uint64, P]
@@ -235,6 +237,32 @@ class Scene:
         buf = np.zeros(nb.value, dtype=np.uint8)
         check(lib().rg_inspect(self._h, int(what), buf.ctypes.data_as(C.c_void_p), nb.value, C.byref(nb)))
         return buf.view(dtype)
+
+
+def render_batch(scenes, scene_idx, cams, mode="roofgs", flags: int = 0, outs=None, stream=None):
+    """Render many views in one captured graph (rg_render_batch); returns the list of [3, H, W] tensors."""
+    import torch
+    n = len(cams)
+    if outs is None:
+        outs = [torch.empty((3, int(c.height), int(c.width)), dtype=torch.float32, device="cuda") for c in cams]
+    hs = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    idx = (C.c_int32 * n)(*[int(i) for i in scene_idx])
+    cs = (RgCamera * n)(*[camera_struct(c) for c in cams])
+    ptrs = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    o = RgOpts(_mode(mode), int(flags), 16, 16)
+    check(lib().rg_render_batch(hs, idx, cs, n, C.byref(o), ptrs, _stream_ptr(stream)))
+    return outs
+
+
+def batch_plan_info(scenes, scene_idx, cams, mode="roofgs", flags: int = 0):
+    n = len(cams)
+    hs = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    idx = (C.c_int32 * n)(*[int(i) for i in scene_idx])
+    cs = (RgCamera * n)(*[camera_struct(c) for c in cams])
+    o = RgOpts(_mode(mode), int(flags), 16, 16)
+    lanes, ppt = C.c_int32(), C.c_int32()
+    check(lib().rg_batch_plan_info(hs, idx, cs, n, C.byref(o), C.byref(lanes), C.byref(ppt)))
+    return lanes.value, ppt.value
 
 
 def eval_fast_exp(P, stream=None):

@@ -1,7 +1,10 @@
 // rg_api.cu -- C ABI of the renderer: resident scenes, frame workspace and the
 // per-frame launch sequence of both modes (see include/rg.h).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <memory>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -74,23 +77,13 @@ constexpr size_t CTRL_ALLOC = 2 * CTRL_BYTES; // frame counters + the per-Gaussi
 
 void rg::set_last_error(const char* msg) { g_err = msg; }
 
-struct rg_scene {
-    int device = 0;
-    int64_t n = 0;
-    int sh_degree = 3;
-    uint32_t storage = 0;
-    int sh_scale_mode = 0;
-    // exact-mode attributes (FP32)
-    DevBuf means, scales, quats, opac, sh;
-    // compact attributes (RoofGS mode)
-    DevBuf geoA, geoB, shq;
-    float band_scale[12] = {0};
-    // frame workspace
+// Frame workspace: everything one frame in flight needs besides the scene.
+// rg_render uses the scene's own workspace; a batch lane or a server slot owns one.
+struct Workspace {
     int64_t cap = 0;
     DevBuf keys[2], vals[2];
     DevBuf ranges;
-    DevBuf ctrl;   // Counters followed by hist[8][256]
-    DevBuf sticky; // Sticky
+    DevBuf ctrl; // Counters followed by hist[8][256] (twice: frame, depth sort)
     DevBuf lb_status;
     DevBuf sort_status[2];
     DevBuf xy, depth, conic, rgb, rect, touched, offsets; // exact per-Gaussian
@@ -106,6 +99,34 @@ struct rg_scene {
     cudaEvent_t ev[EV_RING][EV_PER_FRAME];
     int ev_next = 0;
     int ev_pending = 0;
+
+    void release()
+    {
+        DevBuf* bufs[] = {&keys[0], &keys[1], &vals[0], &vals[1], &ranges, &ctrl, &lb_status, &sort_status[0],
+                          &sort_status[1], &xy, &depth, &conic, &rgb, &rect, &touched, &offsets, &rec, &gkeys[0],
+                          &gkeys[1], &gvals[0], &gvals[1], &gstatus[0], &gstatus[1], &gbuf};
+        for (DevBuf* b : bufs) b->release();
+        if (ev_init)
+            for (int f = 0; f < EV_RING; f++)
+                for (int k = 0; k < EV_PER_FRAME; k++) cudaEventDestroy(ev[f][k]);
+        ev_init = false;
+        cap = 0;
+    }
+};
+
+struct rg_scene {
+    int device = 0;
+    int64_t n = 0;
+    int sh_degree = 3;
+    uint32_t storage = 0;
+    int sh_scale_mode = 0;
+    // exact-mode attributes (FP32)
+    DevBuf means, scales, quats, opac, sh;
+    // compact attributes (RoofGS mode)
+    DevBuf geoA, geoB, shq;
+    float band_scale[12] = {0};
+    DevBuf sticky; // Sticky flags of every frame rendered from this scene
+    Workspace ws;  // frame workspace of rg_render / rg_backward
 };
 
 namespace {
@@ -164,79 +185,79 @@ rg_status make_layout(const rg_camera* c, FrameLayout& f)
     return RG_OK;
 }
 
-rg_status ensure_workspace(rg_scene* s, int mode, int tiles, int64_t cap)
+rg_status ensure_workspace(Workspace& w, int64_t n_gauss, int mode, int tiles, int64_t cap)
 {
-    const int64_t n = s->n > 0 ? s->n : 1;
+    const int64_t n = n_gauss > 0 ? n_gauss : 1;
     if (cap > MAX_CAP) return fail(RG_ERR_CAPACITY, "entry capacity above 2^30 - 1");
-    if (cap > s->cap || !s->keys[0].p) {
+    if (cap > w.cap || !w.keys[0].p) {
         for (int k = 0; k < 2; k++) {
-            RG_TRY(ensure(s->keys[k], (size_t)cap * 8, "keys"));
-            RG_TRY(ensure(s->vals[k], (size_t)cap * 4, "values"));
+            RG_TRY(ensure(w.keys[k], (size_t)cap * 8, "keys"));
+            RG_TRY(ensure(w.vals[k], (size_t)cap * 4, "values"));
         }
         const int64_t max_tiles = (cap + sort_tile_items() - 1) / sort_tile_items();
-        for (int k = 0; k < 2; k++) RG_TRY(ensure(s->sort_status[k], (size_t)max_tiles * 256 * 4, "sort status"));
-        s->cap = cap;
+        for (int k = 0; k < 2; k++) RG_TRY(ensure(w.sort_status[k], (size_t)max_tiles * 256 * 4, "sort status"));
+        w.cap = cap;
     }
-    RG_TRY(ensure(s->ranges, (size_t)tiles * sizeof(uint2), "ranges"));
-    RG_TRY(ensure(s->ctrl, CTRL_ALLOC, "counters"));
-    RG_TRY(ensure(s->lb_status, (size_t)((n + 255) / 256 + 1) * 8, "look-back status"));
+    RG_TRY(ensure(w.ranges, (size_t)tiles * sizeof(uint2), "ranges"));
+    RG_TRY(ensure(w.ctrl, CTRL_ALLOC, "counters"));
+    RG_TRY(ensure(w.lb_status, (size_t)((n + 255) / 256 + 1) * 8, "look-back status"));
     if (mode == RG_MODE_EXACT) {
-        RG_TRY(ensure(s->xy, (size_t)n * 8, "xy"));
-        RG_TRY(ensure(s->depth, (size_t)n * 4, "depth"));
-        RG_TRY(ensure(s->conic, (size_t)n * 16, "conic"));
-        RG_TRY(ensure(s->rgb, (size_t)n * 12, "rgb"));
-        RG_TRY(ensure(s->rect, (size_t)n * 16, "rect"));
-        RG_TRY(ensure(s->touched, (size_t)n * 4, "touched"));
-        RG_TRY(ensure(s->offsets, (size_t)n * 4, "offsets"));
+        RG_TRY(ensure(w.xy, (size_t)n * 8, "xy"));
+        RG_TRY(ensure(w.depth, (size_t)n * 4, "depth"));
+        RG_TRY(ensure(w.conic, (size_t)n * 16, "conic"));
+        RG_TRY(ensure(w.rgb, (size_t)n * 12, "rgb"));
+        RG_TRY(ensure(w.rect, (size_t)n * 16, "rect"));
+        RG_TRY(ensure(w.touched, (size_t)n * 4, "touched"));
+        RG_TRY(ensure(w.offsets, (size_t)n * 4, "offsets"));
     } else {
-        RG_TRY(ensure(s->rec, (size_t)n * 32, "records"));
+        RG_TRY(ensure(w.rec, (size_t)n * 32, "records"));
         for (int k = 0; k < 2; k++) {
-            RG_TRY(ensure(s->gkeys[k], (size_t)n * 4, "depth keys"));
-            RG_TRY(ensure(s->gvals[k], (size_t)n * 4, "depth order"));
-            RG_TRY(ensure(s->gstatus[k], (size_t)((n + sort_tile_items() - 1) / sort_tile_items()) * 256 * 4,
+            RG_TRY(ensure(w.gkeys[k], (size_t)n * 4, "depth keys"));
+            RG_TRY(ensure(w.gvals[k], (size_t)n * 4, "depth order"));
+            RG_TRY(ensure(w.gstatus[k], (size_t)((n + sort_tile_items() - 1) / sort_tile_items()) * 256 * 4,
                           "depth sort status"));
         }
     }
     return RG_OK;
 }
 
-void init_events(rg_scene* s)
+void init_events(Workspace& w)
 {
-    if (s->ev_init) return;
+    if (w.ev_init) return;
     for (int f = 0; f < EV_RING; f++)
-        for (int k = 0; k < EV_PER_FRAME; k++) cudaEventCreate(&s->ev[f][k]);
-    s->ev_init = true;
+        for (int k = 0; k < EV_PER_FRAME; k++) cudaEventCreate(&w.ev[f][k]);
+    w.ev_init = true;
 }
 
 // One frame on `st`; the caller has checked arguments and the workspace.
-rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flags, float* out, cudaStream_t st,
-                      bool count = false)
+rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode, uint32_t flags, float* out,
+                      cudaStream_t st, bool count = false)
 {
-    Counters* ctr = s->ctrl.as<Counters>();
-    unsigned* hist = reinterpret_cast<unsigned*>(s->ctrl.as<unsigned char>() + sizeof(Counters));
+    Counters* ctr = w.ctrl.as<Counters>();
+    unsigned* hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + sizeof(Counters));
     Sticky* sticky = s->sticky.as<Sticky>();
     const bool ev = (flags & RG_FLAG_STAGE_EVENTS) != 0;
     cudaEvent_t* E = nullptr;
     if (ev) {
-        init_events(s);
-        E = s->ev[s->ev_next];
-        s->ev_next = (s->ev_next + 1) % EV_RING;
-        if (s->ev_pending < EV_RING) s->ev_pending++;
+        init_events(w);
+        E = w.ev[w.ev_next];
+        w.ev_next = (w.ev_next + 1) % EV_RING;
+        if (w.ev_pending < EV_RING) w.ev_pending++;
         RG_CK(cudaEventRecord(E[0], st));
     }
-    RG_CK(cudaMemsetAsync(s->ctrl.p, 0, CTRL_ALLOC, st));
-    RG_CK(cudaMemsetAsync(s->ranges.p, 0, (size_t)F.tiles * sizeof(uint2), st));
+    RG_CK(cudaMemsetAsync(w.ctrl.p, 0, CTRL_ALLOC, st));
+    RG_CK(cudaMemsetAsync(w.ranges.p, 0, (size_t)F.tiles * sizeof(uint2), st));
     const long long n = s->n;
     SortArgs sa;
     memset(&sa, 0, sizeof(sa));
     for (int k = 0; k < 2; k++) {
-        sa.keys[k] = s->keys[k].p;
-        sa.vals[k] = s->vals[k].as<unsigned>();
-        sa.status[k] = s->sort_status[k].as<unsigned>();
+        sa.keys[k] = w.keys[k].p;
+        sa.vals[k] = w.vals[k].as<unsigned>();
+        sa.status[k] = w.sort_status[k].as<unsigned>();
     }
-    sa.cap = s->cap;
+    sa.cap = w.cap;
     sa.hist = hist;
-    sa.max_tiles = (s->cap + sort_tile_items() - 1) / sort_tile_items();
+    sa.max_tiles = (w.cap + sort_tile_items() - 1) / sort_tile_items();
     sa.ctr = ctr;
     sa.sticky = sticky;
     int tile_shift;
@@ -252,20 +273,20 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
         a.n = n;
         a.cam = F.cam;
         a.lay = F.lay;
-        a.xy = s->xy.as<float2>();
-        a.depth = s->depth.as<float>();
-        a.conic_op = s->conic.as<float4>();
-        a.rgb = s->rgb.as<float>();
-        a.rect = s->rect.as<int4>();
-        a.touched = s->touched.as<unsigned>();
-        a.offsets = s->offsets.as<unsigned>();
-        a.keys = s->keys[0].as<unsigned long long>();
-        a.vals = s->vals[0].as<unsigned>();
-        a.cap = s->cap;
-        a.status = s->lb_status.as<unsigned long long>();
+        a.xy = w.xy.as<float2>();
+        a.depth = w.depth.as<float>();
+        a.conic_op = w.conic.as<float4>();
+        a.rgb = w.rgb.as<float>();
+        a.rect = w.rect.as<int4>();
+        a.touched = w.touched.as<unsigned>();
+        a.offsets = w.offsets.as<unsigned>();
+        a.keys = w.keys[0].as<unsigned long long>();
+        a.vals = w.vals[0].as<unsigned>();
+        a.cap = w.cap;
+        a.status = w.lb_status.as<unsigned long long>();
         a.ctr = ctr;
         a.sticky = sticky;
-        RG_CK(cudaMemsetAsync(s->lb_status.p, 0, (size_t)((n + 2047) / 2048 + 1) * 8, st));
+        RG_CK(cudaMemsetAsync(w.lb_status.p, 0, (size_t)((n + 2047) / 2048 + 1) * 8, st));
         if (ev) RG_CK(cudaEventRecord(E[1], st));
         launch_exact_preprocess(a, st);
         launch_exact_scan(a, st);
@@ -285,14 +306,14 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
         a.n = n;
         a.cam = F.cam;
         a.lay = F.lay;
-        a.rec = s->rec.as<float4>();
-        a.keys = s->keys[0].as<unsigned>();
-        a.vals = s->vals[0].as<unsigned>();
-        a.cap = s->cap;
-        a.status = s->lb_status.as<unsigned long long>();
+        a.rec = w.rec.as<float4>();
+        a.keys = w.keys[0].as<unsigned>();
+        a.vals = w.vals[0].as<unsigned>();
+        a.cap = w.cap;
+        a.status = w.lb_status.as<unsigned long long>();
         a.ctr = ctr;
         a.sticky = sticky;
-        RG_CK(cudaMemsetAsync(s->lb_status.p, 0, (size_t)((n + 255) / 256 + 1) * 8, st));
+        RG_CK(cudaMemsetAsync(w.lb_status.p, 0, (size_t)((n + 255) / 256 + 1) * 8, st));
         sa.key_bytes = 4;
         if (flags & RG_FLAG_SORT_FULL_KEY) {
             // the paper's scheme: entries in Gaussian order, 4 passes over the 32-bit key
@@ -306,22 +327,22 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
             SortArgs ga;
             memset(&ga, 0, sizeof(ga));
             for (int k = 0; k < 2; k++) {
-                ga.keys[k] = s->gkeys[k].p;
-                ga.vals[k] = s->gvals[k].as<unsigned>();
-                ga.status[k] = s->gstatus[k].as<unsigned>();
+                ga.keys[k] = w.gkeys[k].p;
+                ga.vals[k] = w.gvals[k].as<unsigned>();
+                ga.status[k] = w.gstatus[k].as<unsigned>();
             }
-            Counters* gctr = reinterpret_cast<Counters*>(s->ctrl.as<unsigned char>() + CTRL_BYTES);
+            Counters* gctr = reinterpret_cast<Counters*>(w.ctrl.as<unsigned char>() + CTRL_BYTES);
             ga.cap = n;
             ga.key_bytes = 4;
             ga.passes = (F.lay.b_d + 7) / 8;
             ga.bit0 = 0;
-            ga.hist = reinterpret_cast<unsigned*>(s->ctrl.as<unsigned char>() + CTRL_BYTES + sizeof(Counters));
+            ga.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + CTRL_BYTES + sizeof(Counters));
             ga.max_tiles = (n + sort_tile_items() - 1) / sort_tile_items();
             ga.ctr = gctr;
             ga.sticky = sticky;
-            launch_depth_keys(a, s->gkeys[0].as<unsigned>(), s->gvals[0].as<unsigned>(), gctr, st);
+            launch_depth_keys(a, w.gkeys[0].as<unsigned>(), w.gvals[0].as<unsigned>(), gctr, st);
             launch_sort(ga, st, nullptr);
-            a.order = s->gvals[ga.passes & 1].as<unsigned>();
+            a.order = w.gvals[ga.passes & 1].as<unsigned>();
             if (ev) RG_CK(cudaEventRecord(E[1], st));
             sa.passes = (F.lay.b_t + 7) / 8;
             sa.bit0 = F.lay.b_d;
@@ -338,17 +359,17 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
     if (ev) RG_CK(cudaEventRecord(E[4], st));
     const int fin = sa.passes & 1;
     RangeArgs ra;
-    ra.keys = s->keys[fin].p;
+    ra.keys = w.keys[fin].p;
     ra.key_bytes = sa.key_bytes;
     ra.tile_shift = tile_shift;
     ra.ntiles = F.tiles;
-    ra.ranges = s->ranges.as<uint2>();
+    ra.ranges = w.ranges.as<uint2>();
     ra.ctr = ctr;
     launch_ranges(ra, st);
     if (ev) RG_CK(cudaEventRecord(E[5], st));
-    s->last_mode = mode;
-    s->last_passes = sa.passes;
-    s->last_tiles = F.tiles;
+    w.last_mode = mode;
+    w.last_passes = sa.passes;
+    w.last_tiles = F.tiles;
     if (!out) { // front end, sort and ranges only (the backward replays the blend itself)
         if (ev) RG_CK(cudaEventRecord(E[6], st));
         RG_CK(cudaGetLastError());
@@ -356,8 +377,8 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
     }
     RasterArgs r;
     memset(&r, 0, sizeof(r));
-    r.ranges = s->ranges.as<uint2>();
-    r.vals = s->vals[fin].as<unsigned>();
+    r.ranges = w.ranges.as<uint2>();
+    r.vals = w.vals[fin].as<unsigned>();
     r.n = n;
     r.tiles_x = F.lay.tiles_x;
     r.tiles_y = F.lay.tiles_y;
@@ -365,21 +386,21 @@ rg_status render_once(rg_scene* s, const FrameLayout& F, int mode, uint32_t flag
     r.out = out;
     r.count = count ? ctr : nullptr;
     if (mode == RG_MODE_EXACT) {
-        r.xy = s->xy.as<float2>();
-        r.conic_op = s->conic.as<float4>();
-        r.rgb = s->rgb.as<float>();
+        r.xy = w.xy.as<float2>();
+        r.conic_op = w.conic.as<float4>();
+        r.rgb = w.rgb.as<float>();
         launch_raster_exact(r, st);
     } else {
-        r.rec = s->rec.as<float4>();
+        r.rec = w.rec.as<float4>();
         r.fast_exp = (flags & RG_FLAG_EXACT_EXP) ? 0 : 1;
         r.dual_pixel = (flags & RG_FLAG_SINGLE_PIXEL) ? 0 : 1;
         launch_raster_roofgs(r, st);
     }
     if (ev) RG_CK(cudaEventRecord(E[6], st));
     RG_CK(cudaGetLastError());
-    s->last_mode = mode;
-    s->last_passes = sa.passes;
-    s->last_tiles = F.tiles;
+    w.last_mode = mode;
+    w.last_passes = sa.passes;
+    w.last_tiles = F.tiles;
     return RG_OK;
 }
 
@@ -392,16 +413,208 @@ rg_status upload(DevBuf& dst, const float* src, size_t count, int on_device, cud
 
 void destroy_scene(rg_scene* s)
 {
-    DevBuf* bufs[] = {&s->gbuf, &s->gkeys[0], &s->gkeys[1], &s->gvals[0], &s->gvals[1], &s->gstatus[0], &s->gstatus[1],
-                      &s->means, &s->scales, &s->quats, &s->opac, &s->sh, &s->geoA, &s->geoB, &s->shq, &s->keys[0],
-                      &s->keys[1], &s->vals[0], &s->vals[1], &s->ranges, &s->ctrl, &s->sticky, &s->lb_status,
-                      &s->sort_status[0], &s->sort_status[1], &s->xy, &s->depth, &s->conic, &s->rgb, &s->rect,
-                      &s->touched, &s->offsets, &s->rec};
+    DevBuf* bufs[] = {&s->means, &s->scales, &s->quats, &s->opac, &s->sh, &s->geoA, &s->geoB, &s->shq, &s->sticky};
     for (DevBuf* b : bufs) b->release();
-    if (s->ev_init)
-        for (int f = 0; f < EV_RING; f++)
-            for (int k = 0; k < EV_PER_FRAME; k++) cudaEventDestroy(s->ev[f][k]);
+    s->ws.release();
     delete s;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched rendering: a plan per (scenes, resolutions, mode, flags) owns L lanes,
+// each a stream and a workspace; a call captures every view's pipeline on the
+// lanes (view v on lane v mod L) into one CUDA graph, updates the plan's
+// instantiated graph in place and launches it once on the caller's stream.
+// ---------------------------------------------------------------------------
+constexpr int BATCH_MAX_LANES = 4;
+
+struct BatchPlan {
+    int device = 0;
+    std::vector<rg_scene*> scenes;
+    std::vector<int> widths, heights;
+    int mode = 0;
+    uint32_t flags = 0;
+    int lanes = 1;
+    uint32_t raster_flags = 0; // autotuned: 0 (two pixels per thread) or RG_FLAG_SINGLE_PIXEL
+    bool tuned = false;
+    std::unique_ptr<Workspace[]> ws{new Workspace[BATCH_MAX_LANES]};
+    cudaStream_t streams[BATCH_MAX_LANES] = {nullptr};
+    cudaEvent_t join[BATCH_MAX_LANES] = {nullptr};
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int exec_lanes = 0;
+    uint32_t exec_raster = 0;
+
+    ~BatchPlan()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (int l = 0; l < BATCH_MAX_LANES; l++) {
+            if (streams[l]) cudaStreamDestroy(streams[l]);
+            if (join[l]) cudaEventDestroy(join[l]);
+            ws[l].release();
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+std::mutex g_batch_mu;
+std::vector<std::unique_ptr<BatchPlan>> g_plans;
+
+// drop every plan that renders from scene s (called when s is destroyed)
+void drop_plans_of(const rg_scene* s)
+{
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (size_t k = 0; k < g_plans.size();) {
+        bool uses = false;
+        for (rg_scene* x : g_plans[k]->scenes) uses |= (x == s);
+        if (uses) g_plans.erase(g_plans.begin() + k);
+        else k++;
+    }
+}
+
+rg_status plan_init(BatchPlan& P)
+{
+    for (int l = 0; l < BATCH_MAX_LANES; l++) {
+        RG_CK(cudaStreamCreateWithFlags(&P.streams[l], cudaStreamNonBlocking));
+        RG_CK(cudaEventCreateWithFlags(&P.join[l], cudaEventDisableTiming));
+    }
+    RG_CK(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
+    RG_CK(cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking));
+    return RG_OK;
+}
+
+// Size every lane for every view: render each view once on lane 0's workspace with
+// the checked path, then give all lanes the largest capacity (+25 % headroom for
+// other poses). Also runs each kernel once outside capture (first-use set-up).
+rg_status plan_size(BatchPlan& P, const std::vector<FrameLayout>& F, float* const* outs, cudaStream_t st)
+{
+    int64_t cap = 0;
+    int max_tiles = 1;
+    int64_t max_n = 1;
+    for (size_t v = 0; v < F.size(); v++) {
+        rg_scene* s = P.scenes[v];
+        max_tiles = std::max(max_tiles, F[v].tiles);
+        max_n = std::max<int64_t>(max_n, s->n);
+        int64_t c = P.ws[0].cap > 0 ? P.ws[0].cap : std::max<int64_t>(1 << 20, 4 * s->n);
+        if (c > MAX_CAP) c = MAX_CAP;
+        RG_TRY(ensure_workspace(P.ws[0], s->n, P.mode, F[v].tiles, c));
+        for (int attempt = 0; attempt < 2; attempt++) {
+            RG_TRY(render_once(s, P.ws[0], F[v], P.mode, P.flags, outs[v], st));
+            Counters c2;
+            RG_CK(cudaMemcpyAsync(&c2, P.ws[0].ctrl.p, sizeof(c2), cudaMemcpyDeviceToHost, st));
+            RG_CK(cudaStreamSynchronize(st));
+            if (c2.error) return fail(RG_ERR_TIMEOUT, "a bounded device wait gave up");
+            cap = std::max<int64_t>(cap, (int64_t)c2.n_entries_total);
+            if (c2.n_entries_total <= (unsigned long long)P.ws[0].cap) break;
+            int64_t want = (int64_t)(c2.n_entries_total + c2.n_entries_total / 4 + 1024);
+            if (want > MAX_CAP) return fail(RG_ERR_CAPACITY, "a view needs more than 2^30 - 1 entries");
+            RG_TRY(ensure_workspace(P.ws[0], s->n, P.mode, F[v].tiles, want));
+        }
+    }
+    cap = std::min<int64_t>(MAX_CAP, cap + cap / 4 + 1024);
+    for (int l = 0; l < BATCH_MAX_LANES; l++) {
+        for (size_t v = 0; v < F.size(); v++)
+            RG_TRY(ensure_workspace(P.ws[l], P.scenes[v]->n, P.mode, max_tiles, std::max(cap, P.ws[l].cap)));
+    }
+    // the scenes' sticky flags of the sizing frames are not errors
+    for (rg_scene* s : P.scenes) RG_CK(cudaMemsetAsync(s->sticky.p, 0, sizeof(Sticky), st));
+    RG_CK(cudaStreamSynchronize(st));
+    return RG_OK;
+}
+
+// Capture all views on `lanes` lanes and bring P.exec up to date.
+rg_status plan_capture(BatchPlan& P, const std::vector<FrameLayout>& F, float* const* outs, int lanes,
+                       uint32_t raster_flags)
+{
+    RG_CK(cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal));
+    rg_status err = RG_OK;
+    cudaError_t ce = cudaEventRecord(P.fork, P.cap);
+    for (int l = 0; l < lanes && ce == cudaSuccess; l++) ce = cudaStreamWaitEvent(P.streams[l], P.fork, 0);
+    const uint32_t fl = (P.flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL)) | raster_flags;
+    for (size_t v = 0; v < F.size() && ce == cudaSuccess && err == RG_OK; v++)
+        err = render_once(P.scenes[v], P.ws[v % lanes], F[v], P.mode, fl, outs[v], P.streams[v % lanes]);
+    for (int l = 0; l < lanes && ce == cudaSuccess; l++) {
+        ce = cudaEventRecord(P.join[l], P.streams[l]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(P.cap, P.join[l], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(P.cap, &g);
+    if (err != RG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return err;
+    }
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(RG_ERR_CUDA, std::string("batch capture failed: ") +
+                                     cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    bool fresh = !P.exec || P.exec_lanes != lanes || P.exec_raster != raster_flags;
+    if (!fresh) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(P.exec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            fresh = true;
+        }
+    }
+    if (fresh) {
+        if (P.exec) cudaGraphExecDestroy(P.exec);
+        P.exec = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&P.exec, g, 0);
+        if (ie != cudaSuccess) {
+            cudaGraphDestroy(g);
+            P.exec = nullptr;
+            return fail(RG_ERR_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(ie));
+        }
+        P.exec_lanes = lanes;
+        P.exec_raster = raster_flags;
+    }
+    cudaGraphDestroy(g);
+    return RG_OK;
+}
+
+// Pick the lane count and pixels per thread by timing the captured batch.
+rg_status plan_tune(BatchPlan& P, const std::vector<FrameLayout>& F, float* const* outs, cudaStream_t st)
+{
+    const int V = (int)F.size();
+    float best = 1e30f;
+    int best_l = 1;
+    uint32_t best_r = 0;
+    cudaEvent_t e0, e1;
+    RG_CK(cudaEventCreate(&e0));
+    RG_CK(cudaEventCreate(&e1));
+    for (int lanes : {1, 2, 4}) {
+        if (lanes > V && lanes > 1) continue;
+        for (uint32_t r : {0u, (uint32_t)RG_FLAG_SINGLE_PIXEL}) {
+            if (P.mode != RG_MODE_ROOFGS && r) continue;
+            rg_status e = plan_capture(P, F, outs, lanes, r);
+            if (e != RG_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return e;
+            }
+            RG_CK(cudaGraphLaunch(P.exec, st)); // warm
+            RG_CK(cudaEventRecord(e0, st));
+            RG_CK(cudaGraphLaunch(P.exec, st));
+            RG_CK(cudaEventRecord(e1, st));
+            RG_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            RG_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_l = lanes;
+                best_r = r;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P.lanes = best_l;
+    P.raster_flags = best_r;
+    P.tuned = true;
+    return RG_OK;
 }
 
 } // namespace
@@ -517,6 +730,7 @@ rg_status rg_scene_destroy(rg_scene* scene)
 {
     if (!scene) return RG_OK;
     cudaDeviceSynchronize();
+    drop_plans_of(scene);
     destroy_scene(scene);
     return RG_OK;
 }
@@ -524,16 +738,16 @@ rg_status rg_scene_destroy(rg_scene* scene)
 rg_status rg_scene_reserve(rg_scene* scene, int64_t n_entries)
 {
     if (!scene || n_entries < 0) return fail(RG_ERR_INVALID_ARG, "bad scene or size");
-    if (n_entries <= scene->cap) return RG_OK;
+    if (n_entries <= scene->ws.cap) return RG_OK;
     RG_CK(cudaDeviceSynchronize());
     const int64_t cap = n_entries;
     for (int k = 0; k < 2; k++) {
-        RG_TRY(ensure(scene->keys[k], (size_t)cap * 8, "keys"));
-        RG_TRY(ensure(scene->vals[k], (size_t)cap * 4, "values"));
+        RG_TRY(ensure(scene->ws.keys[k], (size_t)cap * 8, "keys"));
+        RG_TRY(ensure(scene->ws.vals[k], (size_t)cap * 4, "values"));
     }
     const int64_t max_tiles = (cap + sort_tile_items() - 1) / sort_tile_items();
-    for (int k = 0; k < 2; k++) RG_TRY(ensure(scene->sort_status[k], (size_t)max_tiles * 256 * 4, "sort status"));
-    scene->cap = cap;
+    for (int k = 0; k < 2; k++) RG_TRY(ensure(scene->ws.sort_status[k], (size_t)max_tiles * 256 * 4, "sort status"));
+    scene->ws.cap = cap;
     return RG_OK;
 }
 
@@ -554,27 +768,27 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, const rg_render_opts* opt
     FrameLayout F;
     RG_TRY(make_layout(cam, F));
     cudaStream_t st = (cudaStream_t)stream;
-    int64_t cap = s->cap > 0 ? s->cap : std::max<int64_t>(1 << 20, 4 * s->n);
+    int64_t cap = s->ws.cap > 0 ? s->ws.cap : std::max<int64_t>(1 << 20, 4 * s->n);
     if (cap > MAX_CAP) cap = MAX_CAP;
-    RG_TRY(ensure_workspace(s, mode, F.tiles, cap));
-    RG_TRY(render_once(s, F, mode, opts->flags, out_chw, st, stats != nullptr));
+    RG_TRY(ensure_workspace(s->ws, s->n, mode, F.tiles, cap));
+    RG_TRY(render_once(s, s->ws, F, mode, opts->flags, out_chw, st, stats != nullptr));
     if (!stats) return RG_OK;
     Counters c;
-    RG_CK(cudaMemcpyAsync(&c, s->ctrl.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+    RG_CK(cudaMemcpyAsync(&c, s->ws.ctrl.p, sizeof(c), cudaMemcpyDeviceToHost, st));
     RG_CK(cudaStreamSynchronize(st));
     int regrown = 0;
     if (c.error) return fail(RG_ERR_TIMEOUT, "a bounded device wait gave up");
-    if (c.n_entries_total > (unsigned long long)s->cap) {
+    if (c.n_entries_total > (unsigned long long)s->ws.cap) {
         int64_t want = (int64_t)(c.n_entries_total + c.n_entries_total / 4 + 1024);
         if ((unsigned long long)want > (unsigned long long)MAX_CAP) want = MAX_CAP;
         if ((unsigned long long)want < c.n_entries_total)
             return fail(RG_ERR_CAPACITY, "frame needs more than 2^30 - 1 entries");
         RG_TRY(rg_scene_reserve(s, want));
-        RG_TRY(render_once(s, F, mode, opts->flags, out_chw, st, true));
-        RG_CK(cudaMemcpyAsync(&c, s->ctrl.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+        RG_TRY(render_once(s, s->ws, F, mode, opts->flags, out_chw, st, true));
+        RG_CK(cudaMemcpyAsync(&c, s->ws.ctrl.p, sizeof(c), cudaMemcpyDeviceToHost, st));
         RG_CK(cudaStreamSynchronize(st));
         if (c.error) return fail(RG_ERR_TIMEOUT, "a bounded device wait gave up");
-        if (c.n_entries_total > (unsigned long long)s->cap) return fail(RG_ERR_CAPACITY, "workspace could not grow enough");
+        if (c.n_entries_total > (unsigned long long)s->ws.cap) return fail(RG_ERR_CAPACITY, "workspace could not grow enough");
         regrown = 1;
     }
     // the overflow of the first attempt is not an error once re-rendered
@@ -589,9 +803,9 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, const rg_render_opts* opt
     stats->n_blends = (int64_t)c.n_blends;
     stats->n_visible = c.n_visible;
     stats->n_entries = (int64_t)c.n_entries_total;
-    stats->capacity = s->cap;
+    stats->capacity = s->ws.cap;
     stats->regrown = regrown;
-    stats->sort_passes = s->last_passes;
+    stats->sort_passes = s->ws.last_passes;
     stats->b_t = F.lay.b_t;
     stats->b_d = mode == RG_MODE_ROOFGS ? F.lay.b_d : 32;
     stats->tiles_x = F.lay.tiles_x;
@@ -616,12 +830,12 @@ rg_status rg_stage_times(rg_scene* s, float* ms7, int32_t* frames)
 {
     if (!s || !ms7) return fail(RG_ERR_INVALID_ARG, "NULL argument");
     for (int k = 0; k < 7; k++) ms7[k] = 0.0f;
-    const int cnt = s->ev_pending;
+    const int cnt = s->ws.ev_pending;
     if (frames) *frames = cnt;
-    if (!s->ev_init || cnt == 0) return RG_OK;
+    if (!s->ws.ev_init || cnt == 0) return RG_OK;
     for (int f = 0; f < cnt; f++) {
-        const int slot = ((s->ev_next - 1 - f) % EV_RING + EV_RING) % EV_RING;
-        cudaEvent_t* E = s->ev[slot];
+        const int slot = ((s->ws.ev_next - 1 - f) % EV_RING + EV_RING) % EV_RING;
+        cudaEvent_t* E = s->ws.ev[slot];
         RG_CK(cudaEventSynchronize(E[6]));
         float t;
         for (int k = 0; k < 6; k++) {
@@ -631,7 +845,7 @@ rg_status rg_stage_times(rg_scene* s, float* ms7, int32_t* frames)
         RG_CK(cudaEventElapsedTime(&t, E[0], E[6]));
         ms7[6] += t;
     }
-    s->ev_pending = 0;
+    s->ws.ev_pending = 0;
     return RG_OK;
 }
 
@@ -648,19 +862,19 @@ rg_status rg_inspect(rg_scene* s, int32_t what, void* host_dst, int64_t cap_byte
     case RG_INSPECT_KEYS:
     case RG_INSPECT_VALUES:
     case RG_INSPECT_RANGES: {
-        if (s->last_mode < 0) return fail(RG_ERR_INVALID_ARG, "no frame rendered yet");
+        if (s->ws.last_mode < 0) return fail(RG_ERR_INVALID_ARG, "no frame rendered yet");
         Counters c;
-        RG_CK(cudaMemcpy(&c, s->ctrl.p, sizeof(c), cudaMemcpyDeviceToHost));
-        const int fin = s->last_passes & 1;
+        RG_CK(cudaMemcpy(&c, s->ws.ctrl.p, sizeof(c), cudaMemcpyDeviceToHost));
+        const int fin = s->ws.last_passes & 1;
         if (what == RG_INSPECT_KEYS) {
-            src = s->keys[fin].p;
-            bytes = (int64_t)c.n_entries * (s->last_mode == RG_MODE_EXACT ? 8 : 4);
+            src = s->ws.keys[fin].p;
+            bytes = (int64_t)c.n_entries * (s->ws.last_mode == RG_MODE_EXACT ? 8 : 4);
         } else if (what == RG_INSPECT_VALUES) {
-            src = s->vals[fin].p;
+            src = s->ws.vals[fin].p;
             bytes = (int64_t)c.n_entries * 4;
         } else {
-            src = s->ranges.p;
-            bytes = (int64_t)s->last_tiles * 8;
+            src = s->ws.ranges.p;
+            bytes = (int64_t)s->ws.last_tiles * 8;
         }
         break;
     }
@@ -725,10 +939,110 @@ rg_status rg_eval_fast_exp(const float* P_dev, float* out_dev, int64_t n, void* 
     return RG_OK;
 }
 
-rg_status rg_render_batch(rg_scene* const*, const int32_t*, const rg_camera*, int32_t, const rg_render_opts*,
-                          float* const*, void*)
+rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
+                          const rg_render_opts* opts, float* const* outs, void* stream)
 {
-    return fail(RG_ERR_UNSUPPORTED, "rg_render_batch is not built yet");
+    if (n < 0) return fail(RG_ERR_INVALID_ARG, "negative view count");
+    if (n == 0) return RG_OK;
+    if (!scenes || !scene_idx || !cams || !opts || !outs) return fail(RG_ERR_INVALID_ARG, "NULL argument");
+    const int mode = opts->mode;
+    if (mode != RG_MODE_EXACT && mode != RG_MODE_ROOFGS) return fail(RG_ERR_INVALID_ARG, "unknown mode");
+    const int tw = opts->tile_w ? opts->tile_w : TILE, th = opts->tile_h ? opts->tile_h : TILE;
+    if (tw != TILE || th != TILE) return fail(RG_ERR_UNSUPPORTED, "only 16x16 tiles are built");
+    std::vector<FrameLayout> F((size_t)n);
+    std::vector<rg_scene*> vs((size_t)n);
+    for (int v = 0; v < n; v++) {
+        if (scene_idx[v] < 0) return fail(RG_ERR_INVALID_ARG, "negative scene index");
+        rg_scene* s = scenes[scene_idx[v]];
+        if (!s || !outs[v]) return fail(RG_ERR_INVALID_ARG, "NULL scene or output");
+        if (mode == RG_MODE_EXACT && !(s->storage & RG_STORE_FP32))
+            return fail(RG_ERR_INVALID_ARG, "exact mode needs RG_STORE_FP32");
+        if (mode == RG_MODE_ROOFGS && !(s->storage & RG_STORE_COMPACT))
+            return fail(RG_ERR_INVALID_ARG, "RoofGS mode needs RG_STORE_COMPACT");
+        RG_TRY(make_layout(&cams[v], F[v]));
+        vs[v] = s;
+    }
+    int dev = 0;
+    RG_CK(cudaGetDevice(&dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchPlan* P = nullptr;
+    const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_BATCH_CHECKED);
+    for (auto& p : g_plans) {
+        if (p->device != dev || p->mode != mode || p->flags != key_flags || p->scenes != vs) continue;
+        bool same = true;
+        for (int v = 0; v < n && same; v++) same = p->widths[v] == F[v].cam.W && p->heights[v] == F[v].cam.H;
+        if (same) {
+            P = p.get();
+            break;
+        }
+    }
+    const bool fresh = P == nullptr;
+    if (fresh) {
+        std::unique_ptr<BatchPlan> np(new BatchPlan());
+        np->device = dev;
+        np->scenes = vs;
+        np->mode = mode;
+        np->flags = key_flags;
+        for (int v = 0; v < n; v++) {
+            np->widths.push_back(F[v].cam.W);
+            np->heights.push_back(F[v].cam.H);
+        }
+        RG_TRY(plan_init(*np));
+        RG_TRY(plan_size(*np, F, outs, st));
+        RG_TRY(plan_tune(*np, F, outs, st));
+        if (g_plans.size() >= 8) g_plans.erase(g_plans.begin());
+        g_plans.push_back(std::move(np));
+        P = g_plans.back().get();
+    }
+    RG_TRY(plan_capture(*P, F, outs, P->lanes, P->raster_flags));
+    RG_CK(cudaGraphLaunch(P->exec, st));
+    if (opts->flags & RG_FLAG_BATCH_CHECKED) {
+        // synchronous check: resize and render again if a view overflowed its lane
+        bool over = false;
+        for (rg_scene* s : P->scenes) {
+            Sticky h;
+            RG_CK(cudaMemcpyAsync(&h, s->sticky.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+            RG_CK(cudaStreamSynchronize(st));
+            if (h.error) return fail(RG_ERR_TIMEOUT, "a bounded device wait gave up");
+            over |= h.overflow != 0;
+        }
+        if (over) {
+            for (int l = 0; l < BATCH_MAX_LANES; l++) P->ws[l].cap = 0;
+            RG_TRY(plan_size(*P, F, outs, st));
+            RG_TRY(plan_capture(*P, F, outs, P->lanes, P->raster_flags));
+            RG_CK(cudaGraphLaunch(P->exec, st));
+            RG_CK(cudaStreamSynchronize(st));
+        }
+    }
+    return RG_OK;
+}
+
+// Lane count and pixels per thread the autotuner chose for the plan of these views
+// (0 lanes if no plan exists yet).
+rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
+                             const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread)
+{
+    if (!scenes || !scene_idx || !cams || !opts || !lanes || !pixels_per_thread || n <= 0)
+        return fail(RG_ERR_INVALID_ARG, "bad arguments");
+    *lanes = 0;
+    *pixels_per_thread = 0;
+    int dev = 0;
+    RG_CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_BATCH_CHECKED);
+    for (auto& p : g_plans) {
+        if (p->device != dev || p->mode != opts->mode || p->flags != key_flags || (int)p->scenes.size() != n) continue;
+        bool same = true;
+        for (int v = 0; v < n && same; v++)
+            same = p->scenes[v] == scenes[scene_idx[v]] && p->widths[v] == cams[v].width && p->heights[v] == cams[v].height;
+        if (same) {
+            *lanes = p->lanes;
+            *pixels_per_thread = (p->raster_flags & RG_FLAG_SINGLE_PIXEL) ? 1 : 2;
+            return RG_OK;
+        }
+    }
+    return RG_OK;
 }
 
 rg_status rg_backward(rg_scene* s, const rg_camera* cam, const rg_render_opts* opts, const float* dL_dimg,
@@ -745,44 +1059,44 @@ rg_status rg_backward(rg_scene* s, const rg_camera* cam, const rg_render_opts* o
     FrameLayout F;
     RG_TRY(make_layout(cam, F));
     cudaStream_t st = (cudaStream_t)stream;
-    int64_t cap = s->cap > 0 ? s->cap : std::max<int64_t>(1 << 20, 4 * s->n);
+    int64_t cap = s->ws.cap > 0 ? s->ws.cap : std::max<int64_t>(1 << 20, 4 * s->n);
     if (cap > MAX_CAP) cap = MAX_CAP;
-    RG_TRY(ensure_workspace(s, RG_MODE_EXACT, F.tiles, cap));
+    RG_TRY(ensure_workspace(s->ws, s->n, RG_MODE_EXACT, F.tiles, cap));
     // forward front end, sort and ranges of this camera (checked: the gradient needs every entry)
     for (int attempt = 0; attempt < 2; attempt++) {
-        RG_TRY(render_once(s, F, RG_MODE_EXACT, 0u, nullptr, st));
+        RG_TRY(render_once(s, s->ws, F, RG_MODE_EXACT, 0u, nullptr, st));
         Counters c;
-        RG_CK(cudaMemcpyAsync(&c, s->ctrl.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+        RG_CK(cudaMemcpyAsync(&c, s->ws.ctrl.p, sizeof(c), cudaMemcpyDeviceToHost, st));
         RG_CK(cudaStreamSynchronize(st));
         if (c.error) return fail(RG_ERR_TIMEOUT, "a bounded device wait gave up");
-        if (c.n_entries_total <= (unsigned long long)s->cap) break;
+        if (c.n_entries_total <= (unsigned long long)s->ws.cap) break;
         if (attempt == 1) return fail(RG_ERR_CAPACITY, "workspace could not grow enough");
         int64_t want = (int64_t)(c.n_entries_total + c.n_entries_total / 4 + 1024);
         if (want > MAX_CAP) return fail(RG_ERR_CAPACITY, "frame needs more than 2^30 - 1 entries");
         RG_TRY(rg_scene_reserve(s, want));
     }
-    RG_TRY(ensure(s->gbuf, (size_t)(s->n > 0 ? s->n : 1) * 9 * 4, "gradient buffer"));
-    RG_CK(cudaMemsetAsync(s->gbuf.p, 0, (size_t)(s->n > 0 ? s->n : 1) * 9 * 4, st));
+    RG_TRY(ensure(s->ws.gbuf, (size_t)(s->n > 0 ? s->n : 1) * 9 * 4, "gradient buffer"));
+    RG_CK(cudaMemsetAsync(s->ws.gbuf.p, 0, (size_t)(s->n > 0 ? s->n : 1) * 9 * 4, st));
     BackwardArgs b;
     memset(&b, 0, sizeof(b));
-    const int fin = s->last_passes & 1;
-    b.ranges = s->ranges.as<uint2>();
-    b.vals = s->vals[fin].as<unsigned>();
+    const int fin = s->ws.last_passes & 1;
+    b.ranges = s->ws.ranges.as<uint2>();
+    b.vals = s->ws.vals[fin].as<unsigned>();
     b.n = s->n;
     b.tiles_x = F.lay.tiles_x;
     b.tiles_y = F.lay.tiles_y;
     b.cam = F.cam;
-    b.xy = s->xy.as<float2>();
-    b.conic_op = s->conic.as<float4>();
-    b.rgb = s->rgb.as<float>();
-    b.touched = s->touched.as<unsigned>();
+    b.xy = s->ws.xy.as<float2>();
+    b.conic_op = s->ws.conic.as<float4>();
+    b.rgb = s->ws.rgb.as<float>();
+    b.touched = s->ws.touched.as<unsigned>();
     b.means = s->means.as<float>();
     b.scales = s->scales.as<float>();
     b.quats = s->quats.as<float>();
     b.sh = s->sh.as<float>();
     b.sh_degree = s->sh_degree;
     b.dL_dimg = dL_dimg;
-    b.gbuf = s->gbuf.as<float>();
+    b.gbuf = s->ws.gbuf.as<float>();
     b.dmeans = grads->means;
     b.dscales = grads->scales;
     b.dquats = grads->quats;

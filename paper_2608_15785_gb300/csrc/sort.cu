@@ -35,6 +35,19 @@ constexpr int H_THREADS = 256;
 
 int sort_tile_items() { return S_TILE; }
 
+// SMs of the current device, looked up once (kept out of stream capture)
+static int sm_count()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        sms = v > 0 ? v : 1;
+    }
+    return sms;
+}
+
 // Digit histograms of every pass in one read of the keys (vector loads; the
 // counts of equal digits within a warp are combined before the shared atomic).
 template <typename K>
@@ -291,13 +304,7 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K>, S_THREADS, smem);
         grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     }
-    int hist_grid = 0;
-    {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        hist_grid = 8 * (sms > 0 ? sms : 1);
-    }
+    const int hist_grid = 8 * sm_count();
     const K* kin = (const K*)a.keys[0];
     if (a.passes <= 0) return;
     k_sort_hist<K><<<hist_grid, H_THREADS, 0, s>>>(kin, a.passes, a.bit0, a.hist, a.status[0], a.ctr);
@@ -360,10 +367,7 @@ __global__ void k_ranges(const K* __restrict__ keys, int tile_shift, long long n
 
 void launch_ranges(const RangeArgs& a, cudaStream_t s)
 {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = 8 * (sms > 0 ? sms : 1);
+    const int grid = 8 * sm_count();
     if (a.key_bytes == 4)
         k_ranges<unsigned><<<grid, 256, 0, s>>>((const unsigned*)a.keys, a.tile_shift, a.ntiles, a.ranges, a.ctr);
     else

@@ -58,7 +58,8 @@ def test_bad_arguments_are_rejected_without_a_gpu(L):
     d.sh_degree = 3
     assert L.rg_scene_create(C.byref(d), None, C.byref(out)) == 1  # NULL attribute pointers
     assert L.rg_render(None, None, None, None, None, None) == 1
-    assert L.rg_render_batch(None, None, None, 0, None, None, None) == 8  # RG_ERR_UNSUPPORTED
+    assert L.rg_render_batch(None, None, None, 0, None, None, None) == 0  # empty batch
+    assert L.rg_render_batch(None, None, None, 2, None, None, None) == 1
     assert L.rg_backward(None, None, None, None, None, None) == 1  # NULL arguments
     assert L.rg_submit(None, None, 0, None) == 8
     assert L.rg_poll(None, 0, None) == 8
