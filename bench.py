@@ -68,6 +68,9 @@ def parse():
     p.add_argument("--seed", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-exact", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-backward", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
 
 
@@ -258,6 +261,13 @@ def run_ours(a, rank, world, local_rank):
     barrier()
     e2e_s = time.perf_counter() - t0
     gs.check()
+    extra = {}
+    if rank == 0 and not a.no_batch:
+        extra["batch"] = run_batch(a, sc, gs, dev)
+    if rank == 0 and not a.no_backward:
+        extra["backward"] = run_backward(dev)
+    if rank == 0 and not a.no_serve:
+        extra["serve"] = run_serve(dev, gs)
     clocks = sampler.stop() if sampler else None
     if dist is not None:
         dist.barrier()
@@ -293,11 +303,176 @@ def run_ours(a, rank, world, local_rank):
                    "h2d_bytes_per_step": 100,  # the rg_camera struct, passed by value per call
                    "d2h_bytes_per_step": 3 * a.width * a.height * 4}
     line["clocks"] = {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if clocks else None
+    line.update(extra)
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, sc, cams, budget_tiles=64)
     if dist is not None:
         dist.destroy_process_group()
     return line
+
+
+def run_batch(a, sc3, gs3, dev):
+    """Batched multi-view: 2 resident scenes (1M and the 3M bench scene), 32 cameras 720p-4K."""
+    import numpy as np
+    import torch
+
+    from paper_2608_15785_gb300 import binding, synth
+    sc1 = synth.clustered_scene(1_000_000, 3)
+    gs1 = binding.Scene(sc1, sh_scale_mode=binding.RG_SH_SCALE_BAND_GAUSS)
+    rng = np.random.default_rng(3)
+    sizes = [(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
+    idx = [int(v % 2) for v in range(32)]
+    poses = rng.integers(0, 30, size=(2, 32))
+
+    def cams(r):
+        return [synth.orbit_camera(int(poses[r, v]), *sizes[v % 4]) for v in range(32)]
+
+    scenes = [gs1, gs3]
+    t0 = time.perf_counter()
+    binding.render_batch(scenes, idx, cams(0), mode="roofgs")  # plan: size, autotune, capture
+    torch.cuda.synchronize(dev)
+    plan_s = time.perf_counter() - t0
+    # checked calls size the lanes for both pose sets; checked single renders size the scenes
+    for r in (0, 1):
+        binding.render_batch(scenes, idx, cams(r), mode="roofgs", flags=binding.RG_FLAG_BATCH_CHECKED)
+        for v, c in enumerate(cams(r)):
+            scenes[idx[v]].render(c, mode="roofgs", stats=True)
+    torch.cuda.synchronize(dev)
+    lanes, ppt = binding.batch_plan_info(scenes, idx, cams(0), mode="roofgs")
+    outs = [torch.empty((3, h, w), device=dev) for (w, h) in [sizes[v % 4] for v in range(32)]]
+    reps = 6
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    binding.render_batch(scenes, idx, cams(1), mode="roofgs", outs=outs)
+    e0.record()
+    for r in range(reps):
+        binding.render_batch(scenes, idx, cams(r % 2), mode="roofgs", outs=outs)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    batch_ms = e0.elapsed_time(e1) / reps
+    # the same 32 views one rg_render at a time
+    e0.record()
+    for r in range(reps):
+        for v, c in enumerate(cams(r % 2)):
+            scenes[idx[v]].render(c, mode="roofgs", out=outs[v])
+    e1.record()
+    torch.cuda.synchronize(dev)
+    seq_ms = e0.elapsed_time(e1) / reps
+    for g in scenes:
+        g.check()
+    gs1.close()
+    return {"workload": "2 resident scenes (1M and 3M clustered Gaussians), 32 cameras on orbits, "
+                        "8 each of 1280x720, 1920x1080, 2560x1440, 3840x2160; RoofGS mode",
+            "views_per_s": round(32 / (batch_ms * 1e-3), 1), "ms_per_batch": round(batch_ms, 3),
+            "sequential_views_per_s": round(32 / (seq_ms * 1e-3), 1), "speedup_vs_sequential": round(seq_ms / batch_ms, 3),
+            "autotuned": {"lanes": lanes, "pixels_per_thread": ppt}, "plan_seconds": round(plan_s, 2)}
+
+
+def run_backward(dev):
+    """rg_backward on a 256x256 view of a 1k-Gaussian subset (the gradient-check size) and at 1080p/500k."""
+    import numpy as np
+    import torch
+
+    from paper_2608_15785_gb300 import binding, synth
+    res = {}
+    for name, sc, cam in (("256x256, 1k Gaussians", synth.tiny_scene(10_000, 0).subset(np.arange(0, 10_000, 10)),
+                           synth.tiny_camera(256, 256)),
+                          ("1920x1080, 500k clustered Gaussians", synth.clustered_scene(500_000, 1),
+                           synth.orbit_camera(0, 1920, 1080))):
+        gs = binding.Scene(sc, storage=binding.RG_STORE_FP32)
+        w = torch.randn(3, cam.height, cam.width, device=dev)
+        gs.render(cam, mode="exact")
+        gs.backward(cam, w)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            gs.render(cam, mode="exact")
+        e1.record()
+        torch.cuda.synchronize(dev)
+        fwd = e0.elapsed_time(e1) / 5
+        t0 = time.perf_counter()
+        for _ in range(5):
+            gs.backward(cam, w)
+        torch.cuda.synchronize(dev)
+        bwd = (time.perf_counter() - t0) * 1e3 / 5
+        res[name] = {"forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3)}
+        gs.close()
+    res["note"] = "exact mode; backward replays front end, sort and per-pixel blend (one host sync per call)"
+    return res
+
+
+def run_serve(dev, gs3):
+    """Request loop: 4 resident scenes (0.5M, 1M, 3M, 6M), Poisson arrivals of 720p/1080p/4K requests
+    with random orbit poses; p50/p99 latency (submit -> image ready) and FPS at several request rates."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2608_15785_gb300 import binding, synth
+    extra = [binding.Scene(synth.clustered_scene(n, 10 + k), sh_scale_mode=binding.RG_SH_SCALE_BAND_GAUSS)
+             for k, n in enumerate((500_000, 1_000_000, 6_000_000))]
+    scenes = [extra[0], extra[1], gs3, extra[2]]
+    sizes = [(1280, 720), (1920, 1080), (3840, 2160)]
+    srv = binding.Server(scenes, 3840, 2160, mode="roofgs", max_slots=8, memory_budget=96 << 30,
+                         calibration=synth.orbit_camera(0, 3840, 2160))
+    pool = [torch.empty((3, 2160, 3840), device=dev) for _ in range(16)]
+    rng = np.random.default_rng(11)
+    results = []
+    for rate in (100.0, 200.0, 400.0):
+        n_req = int(rate * 2.0)  # about two seconds of arrivals
+        gaps = rng.exponential(1.0 / rate, size=n_req)
+        reqs = []
+        for k in range(n_req):
+            w, h = sizes[int(rng.integers(3))]
+            reqs.append((synth.orbit_camera(float(rng.uniform(0, 30)), w, h), int(rng.integers(4))))
+        srv.reset_stats()
+        tickets, lock = [], threading.Lock()
+        finished = {"n": 0}
+
+        def submitter():
+            t_next = time.perf_counter()
+            for (cam, sidx), gap in zip(reqs, gaps):
+                t_next += gap
+                while time.perf_counter() < t_next:
+                    time.sleep(0.0002)
+                t = srv.submit(cam, sidx)
+                with lock:
+                    tickets.append((t, cam))
+
+        th = threading.Thread(target=submitter)
+        t0 = time.perf_counter()
+        th.start()
+        done = 0
+        outstanding = []
+        while done < n_req:
+            with lock:
+                while tickets:
+                    outstanding.append(tickets.pop(0))
+            still = []
+            for t, cam in outstanding:
+                if srv.poll(t, pool[t % len(pool)]):  # the pool buffers hold the largest image
+                    done += 1
+                else:
+                    still.append((t, cam))
+            outstanding = still
+            time.sleep(0.0003)
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        results.append({"offered_req_per_s": rate, "requests": n_req, "fps": round(n_req / wall, 1),
+                        "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                        "max_in_flight": st["max_in_flight"]})
+    slots = srv.stats()["slots"]
+    srv.close()
+    for g in scenes:
+        g.check()
+    for g in extra:
+        g.close()
+    return {"workload": "4 resident scenes (0.5M, 1M, 3M, 6M clustered Gaussians), Poisson arrivals, "
+                        "1280x720 / 1920x1080 / 3840x2160 equally likely, uniform orbit azimuth; RoofGS mode",
+            "slots": slots, "rates": results,
+            "latency": "submit to image ready in the slot, host clock of the dispatcher"}
 
 
 def rooflines(r, a, props, clocks):

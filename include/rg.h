@@ -295,10 +295,50 @@ rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, 
                              const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread);
 
 /*
- * Not built yet (return RG_ERR_UNSUPPORTED): the request loop.
+ * Request loop (serving; not in the paper). A server keeps its scenes resident and
+ * owns slots: one CUDA stream, one frame workspace and one result buffer of the
+ * largest resolution each. The slot count is cfg->max_slots (0 = 8), cut down to
+ * what cfg->memory_budget (0 = 8 GiB) holds at the calibrated slot size (the
+ * largest scene rendered once at the largest resolution from cfg->calibration's
+ * pose, +50 % headroom): admission by device memory. A dispatcher thread takes
+ * queued requests in submission order into free slots as earlier ones complete,
+ * so requests that arrive while others run are admitted and overlap on the
+ * device (continuous batching); a request whose entries overflow its slot is
+ * rendered again after the slot grows. Results are those of rg_render.
  */
+typedef struct {
+    int32_t max_slots;           /* concurrent requests (0 = 8) */
+    int64_t memory_budget;       /* device bytes for slots (0 = 8 GiB) */
+    int32_t max_width, max_height; /* largest request resolution */
+    int32_t mode;                /* RG_MODE_* for every request */
+    uint32_t flags;              /* RG_FLAG_* (ingredient flags) for every request */
+    const rg_camera* calibration; /* pose used to size slots (NULL: start small, grow on demand) */
+} rg_server_config;
+
+typedef struct {
+    int64_t completed;     /* requests finished since the last reset */
+    int64_t pending;       /* requests waiting for a slot */
+    int32_t slots;         /* slots admitted by the memory budget */
+    int32_t max_in_flight; /* most requests rendering at once since the last reset */
+    double p50_ms, p99_ms; /* submit -> result ready latency percentiles since the last reset */
+    int64_t slot_bytes;    /* calibrated bytes per slot */
+} rg_server_stats_t;
+
+/* Create a server over n_scenes resident scenes (the scenes must outlive it). Synchronous. */
+rg_status rg_server_create(rg_scene* const* scenes, int32_t n_scenes, const rg_server_config* cfg, rg_server** out);
+/* Finish queued and running requests, stop the dispatcher, free the slots. */
+rg_status rg_server_destroy(rg_server* server);
+/* Queue one request (camera of at most the maximum resolution, scene index); non-blocking. */
 rg_status rg_submit(rg_server* server, const rg_camera* cam, int32_t scene_slot, uint64_t* ticket);
+/*
+ * RG_ERR_NOT_READY while the request waits or renders. When it is done, copy its
+ * image into out_chw (device [3][H][W] of the request's camera), free the slot and
+ * return RG_OK (or the request's error: RG_ERR_TIMEOUT, RG_ERR_CAPACITY, ...).
+ * A ticket can be collected once.
+ */
 rg_status rg_poll(rg_server* server, uint64_t ticket, float* out_chw);
+rg_status rg_server_stats(rg_server* server, rg_server_stats_t* stats);
+rg_status rg_server_reset_stats(rg_server* server);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* rg_last_error(void);

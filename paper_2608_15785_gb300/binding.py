@@ -40,7 +40,8 @@ RG_INSPECT_LOG_OPACITY = 8
 # every entry point include/rg.h declares
 EXPORTS = ["rg_scene_create", "rg_scene_destroy", "rg_scene_reserve", "rg_render", "rg_scene_check",
            "rg_stage_times", "rg_inspect", "rg_eval_fast_exp", "rg_render_batch", "rg_backward", "rg_submit",
-           "rg_poll", "rg_last_error", "rg_version", "rg_sort_pairs_noalloc", "rg_batch_plan_info"]
+           "rg_poll", "rg_last_error", "rg_version", "rg_sort_pairs_noalloc", "rg_batch_plan_info",
+           "rg_server_create", "rg_server_destroy", "rg_server_stats", "rg_server_reset_stats"]
 
 
 class RgError(RuntimeError):
@@ -68,6 +69,19 @@ class RgOpts(C.Structure):
 class RgGrads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacities", C.c_void_p),
                 ("sh", C.c_void_p)]
+
+
+class RgServerConfig(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("memory_budget", C.c_int64), ("max_width", C.c_int32),
+                ("max_height", C.c_int32), ("mode", C.c_int32), ("flags", C.c_uint32), ("calibration", C.c_void_p)]
+
+
+class RgServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("pending", C.c_int64), ("slots", C.c_int32), ("max_in_flight", C.c_int32),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("slot_bytes", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class RgStats(C.Structure):
@@ -103,8 +117,12 @@ def lib():
         L.rg_render_batch.argtypes = [P, P, P, C.c_int32, C.POINTER(RgOpts), P, P]
         L.rg_batch_plan_info.argtypes = [P, P, P, C.c_int32, C.POINTER(RgOpts), P, P]
         L.rg_backward.argtypes = [P, C.POINTER(RgCamera), C.POINTER(RgOpts), P, C.POINTER(RgGrads), P]
-        L.rg_submit.argtypes = [P, P, C.c_int32, P]
+        L.rg_submit.argtypes = [P, C.POINTER(RgCamera), C.c_int32, C.POINTER(C.c_uint64)]
         L.rg_poll.argtypes = [P, C.c_uint64, P]
+        L.rg_server_create.argtypes = [P, C.c_int32, C.POINTER(RgServerConfig), C.POINTER(P)]
+        L.rg_server_destroy.argtypes = [P]
+        L.rg_server_stats.argtypes = [P, C.POINTER(RgServerStats)]
+        L.rg_server_reset_stats.argtypes = [P]
         L.rg_sort_pairs_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P, P]
         L.rg_last_error.restype = C.c_char_p
         L.rg_last_error.argtypes = []
@@ -263,6 +281,53 @@ def batch_plan_info(scenes, scene_idx, cams, mode="roofgs", flags: int = 0):
     lanes, ppt = C.c_int32(), C.c_int32()
     check(lib().rg_batch_plan_info(hs, idx, cs, n, C.byref(o), C.byref(lanes), C.byref(ppt)))
     return lanes.value, ppt.value
+
+
+class Server:
+    """Request loop over resident scenes (rg_server_create / rg_submit / rg_poll)."""
+
+    def __init__(self, scenes, max_width, max_height, mode="roofgs", flags=0, max_slots=0, memory_budget=0,
+                 calibration=None):
+        self._scenes = list(scenes)
+        hs = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+        self._cal = camera_struct(calibration) if calibration is not None else None
+        cfg = RgServerConfig(int(max_slots), int(memory_budget), int(max_width), int(max_height), _mode(mode),
+                             int(flags), C.cast(C.pointer(self._cal), C.c_void_p) if self._cal is not None else None)
+        h = C.c_void_p()
+        check(lib().rg_server_create(hs, len(scenes), C.byref(cfg), C.byref(h)))
+        self._h = h
+
+    def submit(self, cam, scene: int) -> int:
+        t = C.c_uint64()
+        check(lib().rg_submit(self._h, C.byref(camera_struct(cam)), int(scene), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, out) -> bool:
+        """True once the image has been copied into `out` ([3, H, W] CUDA tensor); False while not ready."""
+        st = lib().rg_poll(self._h, C.c_uint64(ticket), C.c_void_p(out.data_ptr()))
+        if st == 7:  # RG_ERR_NOT_READY
+            return False
+        check(st)
+        return True
+
+    def stats(self) -> dict:
+        s = RgServerStats()
+        check(lib().rg_server_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def reset_stats(self):
+        check(lib().rg_server_reset_stats(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def eval_fast_exp(P, stream=None):

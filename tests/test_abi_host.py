@@ -61,8 +61,10 @@ def test_bad_arguments_are_rejected_without_a_gpu(L):
     assert L.rg_render_batch(None, None, None, 0, None, None, None) == 0  # empty batch
     assert L.rg_render_batch(None, None, None, 2, None, None, None) == 1
     assert L.rg_backward(None, None, None, None, None, None) == 1  # NULL arguments
-    assert L.rg_submit(None, None, 0, None) == 8
-    assert L.rg_poll(None, 0, None) == 8
+    assert L.rg_submit(None, None, 0, None) == 1
+    assert L.rg_poll(None, 0, None) == 1
+    assert L.rg_server_create(None, 0, None, None) == 1
+    assert L.rg_server_destroy(None) == 0
     assert L.rg_eval_fast_exp(None, None, -1, None) == 1
     assert L.rg_stage_times(None, None, None) == 1
     assert L.rg_scene_destroy(None) == 0
@@ -72,7 +74,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     """ctypes mirrors of the public structs have the C compiler's sizes and offsets."""
     import subprocess
     structs = {"rg_camera": binding.RgCamera, "rg_scene_desc": binding.RgSceneDesc,
-               "rg_render_opts": binding.RgOpts, "rg_stats": binding.RgStats}
+               "rg_render_opts": binding.RgOpts, "rg_stats": binding.RgStats, "rg_grads": binding.RgGrads,
+               "rg_server_config": binding.RgServerConfig, "rg_server_stats_t": binding.RgServerStats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rg.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append('printf("%%s %%zu\\n", "%s", sizeof(%s));' % (cname, cname))

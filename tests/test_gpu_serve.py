@@ -1,0 +1,95 @@
+"""Request loop (rg_server_create / rg_submit / rg_poll) through the C ABI.
+
+Continuous batching: requests submitted while others render are admitted into
+slots as slots free up and overlap on the device. Every result must equal, bit
+for bit, the same request rendered alone (rg_render, and the same request sent
+to an idle server), whatever else was in the mix.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import pytest
+
+from paper_2608_15785_gb300 import binding, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_15785_gb300.build import build
+    build()
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    return [binding.Scene(synth.tiny_scene(10_000, seed=0)), binding.Scene(synth.clustered_scene(60_000, seed=5))]
+
+
+SIZES = [(640, 360), (320, 200), (256, 256), (100, 37)]
+
+
+def _request(k):
+    w, h = SIZES[k % 4]
+    if k % 2 == 0:
+        return synth.look_at_camera((0.2 * np.sin(k), -0.1 * k % 0.4, -3.0), w, h, zfar=4.8), 0
+    return synth.orbit_camera(k, w, h, radius=4.0 if k % 3 else 2.5), 1
+
+
+def _collect(server, tickets, outs, timeout=60.0):
+    done = set()
+    t0 = time.time()
+    while len(done) < len(tickets) and time.time() - t0 < timeout:
+        for k, t in enumerate(tickets):
+            if k not in done and server.poll(t, outs[k]):
+                done.add(k)
+        time.sleep(0.001)
+    assert len(done) == len(tickets), "requests did not finish"
+
+
+@pytest.mark.parametrize("mode", ["roofgs", "exact"])
+def test_results_alone_equal_results_in_the_mix(scenes, mode):
+    srv = binding.Server(scenes, 640, 360, mode=mode, max_slots=3)
+    reqs = [_request(k) for k in range(14)]
+    outs = [torch.empty((3, c.height, c.width), device="cuda") for c, _ in reqs]
+    tickets = [srv.submit(c, s) for c, s in reqs]  # all at once: more requests than slots
+    _collect(srv, tickets, outs)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["slots"] == 3
+    assert st["max_in_flight"] >= 2  # requests overlapped on the device
+    assert 0 < st["p50_ms"] <= st["p99_ms"]
+    for k, (cam, s) in enumerate(reqs):
+        ref = scenes[s].render(cam, mode=mode)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[k], ref), k
+    # the same request alone on the idle server
+    cam, s = reqs[5]
+    alone = torch.empty_like(outs[5])
+    _collect(srv, [srv.submit(cam, s)], [alone])
+    assert torch.equal(alone, outs[5])
+    srv.close()
+    for sc in scenes:
+        sc.check()
+
+
+def test_slot_growth_and_admission_errors(scenes):
+    # no calibration: slots start at 2^20 entries and grow when a close-up overflows
+    srv = binding.Server(scenes, 1280, 720, mode="roofgs", max_slots=2)
+    near = synth.orbit_camera(3, 1280, 720, radius=1.6)
+    out = torch.empty((3, 720, 1280), device="cuda")
+    _collect(srv, [srv.submit(near, 1)], [out])
+    ref = scenes[1].render(near)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    with pytest.raises(binding.RgError):
+        srv.submit(synth.orbit_camera(0, 1920, 1080), 1)  # above the maximum resolution
+    with pytest.raises(binding.RgError):
+        srv.submit(near, 5)  # no such scene
+    with pytest.raises(binding.RgError):
+        srv.poll(12345, out)  # unknown ticket
+    srv.close()
