@@ -6,8 +6,8 @@
 // that can be non-zero are sorted).
 //
 // One histogram kernel reads every key once and counts the digits of all
-// passes. Each pass is then ONE kernel over tiles of 4096 entries (one-sweep
-// scheme): a persistent grid takes tiles in order from an atomic counter,
+// passes. Each pass is then ONE kernel over tiles of 6144 (32-bit keys) or
+// 4096 (64-bit keys) entries (one-sweep scheme): a persistent grid takes tiles in order from an atomic counter,
 // ranks the tile's digits in shared memory (per-warp counters with match_any,
 // stable), publishes its per-digit counts, obtains the counts of all earlier
 // tiles by decoupled look-back (bounded waits), reorders the tile in shared
@@ -18,22 +18,31 @@
 
 namespace rg {
 
-#ifndef RG_SORT_THREADS
-#define RG_SORT_THREADS 512
-#endif
-#ifndef RG_SORT_KPT
-#define RG_SORT_KPT 8
-#endif
-constexpr int S_THREADS = RG_SORT_THREADS;
-constexpr int S_KPT = RG_SORT_KPT;
-constexpr int S_TILE = S_THREADS * S_KPT; // 4096 entries
-constexpr int S_WARPS = S_THREADS / 32;
+// Tile shape per key width: (threads, keys per thread, resident blocks per SM).
+// Larger tiles amortise the per-tile barriers and look-back; two resident blocks
+// per SM keep one block's loads in flight while the other waits at a barrier.
+// 32-bit keys: 384 x 16 = 6144 entries at 80 registers; 64-bit keys: 512 x 8 =
+// 4096 entries at 64 registers (16 keys of 64 bits would spill).
+template <typename K>
+struct SortCfg;
+template <>
+struct SortCfg<unsigned> {
+    static constexpr int THREADS = 384, KPT = 16, MIN_BLOCKS = 2;
+};
+template <>
+struct SortCfg<unsigned long long> {
+    static constexpr int THREADS = 512, KPT = 8, MIN_BLOCKS = 2;
+};
+template <typename K>
+constexpr int tile_of() { return SortCfg<K>::THREADS * SortCfg<K>::KPT; }
+
 constexpr int RADIX = 256;
 constexpr int LB_WINDOW = 8; // predecessors inspected per round trip of the look-back
 constexpr unsigned SF_AGG = 1u << 30, SF_PRE = 2u << 30, SF_VAL = (1u << 30) - 1u;
 constexpr int H_THREADS = 256;
 
-int sort_tile_items() { return S_TILE; }
+// smallest tile of any key width: sizes the per-tile look-back status arrays
+int sort_tile_items() { return tile_of<unsigned long long>() < tile_of<unsigned>() ? tile_of<unsigned long long>() : tile_of<unsigned>(); }
 
 // SMs of the current device, looked up once (kept out of stream capture)
 static int sm_count()
@@ -59,6 +68,7 @@ __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ k
     for (int j = threadIdx.x; j < 8 * RADIX; j += H_THREADS) (&s_h[0][0])[j] = 0u;
     __syncthreads();
     const long long n = ctr->n_entries;
+    constexpr int S_TILE = tile_of<K>();
     const long long ntiles = (n + S_TILE - 1) / S_TILE;
     const long long gsz = (long long)gridDim.x * H_THREADS;
     const long long gid = (long long)blockIdx.x * H_THREADS + threadIdx.x;
@@ -129,24 +139,27 @@ __device__ __forceinline__ unsigned digit_exclusive_scan(unsigned v, unsigned* s
 
 template <typename K>
 struct SortSmem {
-    K keys[S_TILE];
-    unsigned vals[S_TILE];
-    unsigned whist[S_WARPS][RADIX]; // per-warp digit counters, then per-warp exclusive offsets
-    unsigned goff[RADIX];           // global exclusive digit offsets of this pass
-    unsigned loff[RADIX];           // tile-local exclusive digit offsets
-    unsigned gbase[RADIX];          // global start of this tile's run of each digit
-    unsigned scan[S_WARPS];
+    static constexpr int TILE = tile_of<K>(), WARPS = SortCfg<K>::THREADS / 32;
+    K keys[TILE];
+    unsigned vals[TILE];
+    unsigned whist[WARPS][RADIX]; // per-warp digit counters, then per-warp exclusive offsets
+    unsigned goff[RADIX];         // global exclusive digit offsets of this pass
+    unsigned loff[RADIX];         // tile-local exclusive digit offsets
+    unsigned gbase[RADIX];        // global start of this tile's run of each digit
+    unsigned scan[WARPS];
     unsigned tile;
 };
 
 template <typename K>
-__global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ kin, const unsigned* __restrict__ vin,
+__global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k_onesweep(const K* __restrict__ kin, const unsigned* __restrict__ vin,
                                                         K* __restrict__ kout, unsigned* __restrict__ vout, int pass,
                                                         int bit0, int ballot_rank, const unsigned* __restrict__ hist,
                                                         unsigned* status,
                                                         unsigned* status_next, Counters* ctr, Sticky* sticky)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int S_THREADS = SortCfg<K>::THREADS, S_KPT = SortCfg<K>::KPT, S_TILE = tile_of<K>();
+    constexpr int S_WARPS = S_THREADS / 32;
     SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int shift = bit0 + 8 * pass;
@@ -158,10 +171,14 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
         if (tid < RADIX) S.goff[tid] = e;
     }
     const unsigned lt_mask = (1u << lane) - 1u;
+    // The first tile is claimed here; each later one is claimed, and the warp
+    // counters cleared, during the write-out of the tile before it. Five
+    // barriers per tile: after ranking (B), after the digit scan (C), after the
+    // local offsets (D), after the reorder (E) and after the write-out (A).
+    for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) (&S.whist[0][0])[j] = 0u;
+    if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
+    __syncthreads();
     while (true) {
-        if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
-        for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) (&S.whist[0][0])[j] = 0u;
-        __syncthreads();
         const long long tile = S.tile;
         if (tile >= ntiles) break;
 
@@ -177,7 +194,8 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
             v[i] = ok ? vin[e] : 0u;
         }
         // stable rank of each element among the warp's elements of the same digit
-        unsigned rank[S_KPT];
+        // (below 32 * KPT: two ranks share a register)
+        unsigned rank2[(S_KPT + 1) / 2];
 #pragma unroll
         for (int i = 0; i < S_KPT; i++) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
@@ -200,12 +218,17 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
                 S.whist[warp][d] = b + __popc(peers);
             }
             b = __shfl_sync(0xffffffffu, b, leader);
-            rank[i] = b + __popc(peers & lt_mask);
+            const unsigned r = b + __popc(peers & lt_mask);
+            if (i & 1) rank2[i >> 1] |= r << 16;
+            else rank2[i >> 1] = r;
             __syncwarp();
         }
-        __syncthreads();
-        // digit tid: tile count, per-warp exclusive offsets, publish the count
-        unsigned count = 0;
+        __syncthreads(); // B
+        // digit tid: tile count, per-warp exclusive offsets, publish the count,
+        // issue the first look-back window (consumed after barrier D), and
+        // scan the counts within the warp
+        unsigned count = 0, incl = 0;
+        unsigned sv[LB_WINDOW];
         if (tid < RADIX) {
 #pragma unroll
             for (int w = 0; w < S_WARPS; w++) {
@@ -213,31 +236,43 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
                 S.whist[w][tid] = count;
                 count += c;
             }
-            unsigned* st = status + tile * RADIX + tid;
-            *reinterpret_cast<volatile unsigned*>(st) = (tile == 0 ? SF_PRE : SF_AGG) | count;
+            *reinterpret_cast<volatile unsigned*>(status + tile * RADIX + tid) = (tile == 0 ? SF_PRE : SF_AGG) | count;
+#pragma unroll
+            for (int w = 0; w < LB_WINDOW; w++)
+                sv[w] = (tile - 1 - w >= 0)
+                            ? *reinterpret_cast<volatile unsigned*>(status + (tile - 1 - w) * RADIX + tid)
+                            : (2u << 30); // before tile 0: prefix 0
+            incl = count;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) S.scan[warp] = incl;
         }
-        // tile-local exclusive digit offsets (whole block)
-        const unsigned lo = digit_exclusive_scan(count, S.scan);
+        __syncthreads(); // C
         if (tid < RADIX) {
+            unsigned lo = incl - count;
+            for (int w = 0; w < warp; w++) lo += S.scan[w];
             S.loff[tid] = lo;
-            // windowed decoupled look-back: LB_WINDOW predecessors per round trip
+        }
+        __syncthreads(); // D
+        if (tid < RADIX) {
+            // windowed decoupled look-back: LB_WINDOW predecessors per round trip,
+            // sv[w] holding the status of tile t - w
             unsigned excl = 0;
             if (tile > 0) {
                 long long t = tile - 1;
-                bool timed_out = false, found = false;
+                bool timed_out = false;
                 unsigned spins = 0;
-                while (!found && t >= 0) {
-                    unsigned sv[LB_WINDOW];
-#pragma unroll
-                    for (int w = 0; w < LB_WINDOW; w++)
-                        sv[w] = (t - w >= 0) ? *reinterpret_cast<volatile unsigned*>(status + (t - w) * RADIX + tid)
-                                             : (2u << 30); // before tile 0: prefix 0
+                while (true) {
                     // use the window up to the first missing entry or the first prefix
                     int used = 0;
+                    bool found = false;
                     unsigned add = 0;
 #pragma unroll
                     for (int w = 0; w < LB_WINDOW; w++) {
-                        if (used == w) {
+                        if (used == w && !found) {
                             const unsigned f = sv[w] >> 30;
                             if (f != 0u) {
                                 add += sv[w] & SF_VAL;
@@ -245,10 +280,10 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
                                 if (f == 2u) found = true;
                             }
                         }
-                        if (found) break;
                     }
                     excl += add;
                     t -= used;
+                    if (found || t < 0) break;
                     if (used == 0) { // nearest predecessor not published yet
                         if (++spins > SPIN_LIMIT) {
                             timed_out = true;
@@ -256,6 +291,10 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
                         }
                         __nanosleep(32);
                     }
+#pragma unroll
+                    for (int w = 0; w < LB_WINDOW; w++)
+                        sv[w] = (t - w >= 0) ? *reinterpret_cast<volatile unsigned*>(status + (t - w) * RADIX + tid)
+                                             : (2u << 30);
                 }
                 if (timed_out) {
                     atomicOr(&ctr->error, ERR_SORT_LOOKBACK);
@@ -266,16 +305,17 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
             S.gbase[tid] = S.goff[tid] + excl;
             if (status_next) status_next[tile * RADIX + tid] = 0u;
         }
-        __syncthreads();
-        // reorder the tile by digit in shared memory
+        // reorder the tile by digit in shared memory (the other warps start while
+        // the digit threads look back)
 #pragma unroll
         for (int i = 0; i < S_KPT; i++) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-            const unsigned pos = S.loff[d] + S.whist[warp][d] + rank[i];
+            const unsigned r = (i & 1) ? (rank2[i >> 1] >> 16) : (rank2[i >> 1] & 0xffffu);
+            const unsigned pos = S.loff[d] + S.whist[warp][d] + r;
             S.keys[pos] = k[i];
             S.vals[pos] = v[i];
         }
-        __syncthreads();
+        __syncthreads(); // E
         const long long rem = n - tile * S_TILE;
         const int valid = rem < S_TILE ? (int)rem : S_TILE;
         for (int j = tid; j < valid; j += S_THREADS) {
@@ -287,7 +327,9 @@ __global__ void __launch_bounds__(S_THREADS) k_onesweep(const K* __restrict__ ki
                 vout[dst] = S.vals[j];
             }
         }
-        __syncthreads();
+        for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) (&S.whist[0][0])[j] = 0u;
+        if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
+        __syncthreads(); // A
     }
 }
 
@@ -301,7 +343,7 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
         int per_sm = 0, sms = 0, dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K>, S_THREADS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K>, SortCfg<K>::THREADS, smem);
         grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     }
     const int hist_grid = 8 * sm_count();
@@ -312,7 +354,7 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
     for (int p = 0; p < a.passes; p++) {
         const int src = p & 1, dst = src ^ 1;
         unsigned* nxt = (p + 1 < a.passes) ? a.status[(p + 1) & 1] : nullptr;
-        k_onesweep<K><<<grid, S_THREADS, smem, s>>>((const K*)a.keys[src], a.vals[src], (K*)a.keys[dst], a.vals[dst], p,
+        k_onesweep<K><<<grid, SortCfg<K>::THREADS, smem, s>>>((const K*)a.keys[src], a.vals[src], (K*)a.keys[dst], a.vals[dst], p,
                                                     a.bit0, (a.ballot_mask >> p) & 1, a.hist, a.status[p & 1], nxt,
                                                     a.ctr, a.sticky);
     }

@@ -19,7 +19,7 @@ using namespace rg;
 namespace {
 
 constexpr long long NA_MAX = 1ll << 19;     // at most 524,288 pairs per call
-constexpr long long NA_TILE = 4096;         // entries per sort tile (checked at set-up)
+constexpr long long NA_TILE = 4096;         // smallest sort tile the status arrays are sized for
 constexpr long long NA_TILES = NA_MAX / NA_TILE;
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t OFF_KEYS = 0;
@@ -74,7 +74,7 @@ extern "C" rg_status rg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, int64
     if (n > 0 && (!keys || !vals)) return na_fail(RG_ERR_INVALID_ARG, "rg_sort_pairs_noalloc: keys or vals is NULL");
     if (key_bits != 8 && key_bits != 16 && key_bits != 24 && key_bits != 32)
         return na_fail(RG_ERR_INVALID_ARG, "rg_sort_pairs_noalloc: key_bits must be 8, 16, 24 or 32");
-    if (sort_tile_items() != NA_TILE) return na_fail(RG_ERR_CUDA, "rg_sort_pairs_noalloc: sort tile size mismatch");
+    if (sort_tile_items() < NA_TILE) return na_fail(RG_ERR_CUDA, "rg_sort_pairs_noalloc: sort tile below the sized minimum");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
         return na_fail(RG_ERR_CUDA, "rg_sort_pairs_noalloc: no usable current device");
