@@ -25,9 +25,17 @@ namespace rg {
 // 4096 entries at 64 registers (16 keys of 64 bits would spill).
 template <typename K>
 struct SortCfg;
+#ifndef RG_SORT_T32
+#define RG_SORT_T32 384
+#define RG_SORT_K32 16
+#define RG_SORT_B32 2
+#endif
+#ifndef RG_SORT_VLATE
+#define RG_SORT_VLATE 0
+#endif
 template <>
 struct SortCfg<unsigned> {
-    static constexpr int THREADS = 384, KPT = 16, MIN_BLOCKS = 2;
+    static constexpr int THREADS = RG_SORT_T32, KPT = RG_SORT_K32, MIN_BLOCKS = RG_SORT_B32;
 };
 template <>
 struct SortCfg<unsigned long long> {
@@ -145,7 +153,7 @@ struct SortSmem {
     unsigned whist[WARPS][RADIX]; // per-warp digit counters, then per-warp exclusive offsets
     unsigned goff[RADIX];         // global exclusive digit offsets of this pass
     unsigned loff[RADIX];         // tile-local exclusive digit offsets
-    unsigned gbase[RADIX];        // global start of this tile's run of each digit
+    unsigned gbase[RADIX];        // global start of this tile's run of each digit minus its local start
     unsigned scan[WARPS];
     unsigned tile;
 };
@@ -163,8 +171,9 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
     SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int shift = bit0 + 8 * pass;
-    const long long n = ctr->n_entries;
-    const long long ntiles = (n + S_TILE - 1) / S_TILE;
+    // entry counts stay below 2^30 (workspace limit): 32-bit indices throughout
+    const unsigned n = ctr->n_entries;
+    const unsigned ntiles = (n + S_TILE - 1) / S_TILE;
     {
         const unsigned h = tid < RADIX ? hist[pass * RADIX + tid] : 0u;
         const unsigned e = digit_exclusive_scan(h, S.scan);
@@ -179,19 +188,19 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
     if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
     __syncthreads();
     while (true) {
-        const long long tile = S.tile;
+        const unsigned tile = S.tile;
         if (tile >= ntiles) break;
 
         // load the tile warp-striped: element = tile*TILE + warp*32*KPT + i*32 + lane
-        const long long e0 = tile * S_TILE + (long long)warp * 32 * S_KPT + lane;
+        const unsigned e0 = tile * S_TILE + warp * 32 * S_KPT + lane;
         K k[S_KPT];
         unsigned v[S_KPT];
 #pragma unroll
         for (int i = 0; i < S_KPT; i++) {
-            const long long e = e0 + 32 * i;
+            const unsigned e = e0 + 32 * i;
             const bool ok = e < n;
             k[i] = ok ? kin[e] : (K)~(K)0; // padding sorts last (digit 255, after the valid ones)
-            v[i] = ok ? vin[e] : 0u;
+            if (!RG_SORT_VLATE) v[i] = ok ? vin[e] : 0u;
         }
         // stable rank of each element among the warp's elements of the same digit
         // (below 32 * KPT: two ranks share a register)
@@ -213,10 +222,7 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             }
             const int leader = __ffs(peers) - 1;
             unsigned b = 0;
-            if (lane == leader) {
-                b = S.whist[warp][d];
-                S.whist[warp][d] = b + __popc(peers);
-            }
+            if (lane == leader) b = atomicAdd(&S.whist[warp][d], (unsigned)__popc(peers)); // one lane per digit
             b = __shfl_sync(0xffffffffu, b, leader);
             const unsigned r = b + __popc(peers & lt_mask);
             if (i & 1) rank2[i >> 1] |= r << 16;
@@ -236,11 +242,11 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
                 S.whist[w][tid] = count;
                 count += c;
             }
-            *reinterpret_cast<volatile unsigned*>(status + tile * RADIX + tid) = (tile == 0 ? SF_PRE : SF_AGG) | count;
+            *reinterpret_cast<volatile unsigned*>(status + (size_t)tile * RADIX + tid) = (tile == 0 ? SF_PRE : SF_AGG) | count;
 #pragma unroll
             for (int w = 0; w < LB_WINDOW; w++)
-                sv[w] = (tile - 1 - w >= 0)
-                            ? *reinterpret_cast<volatile unsigned*>(status + (tile - 1 - w) * RADIX + tid)
+                sv[w] = ((int)tile - 1 - w >= 0)
+                            ? *reinterpret_cast<volatile unsigned*>(status + (size_t)(tile - 1 - w) * RADIX + tid)
                             : (2u << 30); // before tile 0: prefix 0
             incl = count;
 #pragma unroll
@@ -251,18 +257,26 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             if (lane == 31) S.scan[warp] = incl;
         }
         __syncthreads(); // C
+        unsigned lo = 0;
         if (tid < RADIX) {
-            unsigned lo = incl - count;
+            lo = incl - count;
             for (int w = 0; w < warp; w++) lo += S.scan[w];
             S.loff[tid] = lo;
         }
         __syncthreads(); // D
+        if (RG_SORT_VLATE) {
+#pragma unroll
+            for (int i = 0; i < S_KPT; i++) {
+                const long long e = e0 + 32 * i;
+                v[i] = e < n ? vin[e] : 0u;
+            }
+        }
         if (tid < RADIX) {
             // windowed decoupled look-back: LB_WINDOW predecessors per round trip,
             // sv[w] holding the status of tile t - w
             unsigned excl = 0;
             if (tile > 0) {
-                long long t = tile - 1;
+                int t = (int)tile - 1;
                 bool timed_out = false;
                 unsigned spins = 0;
                 while (true) {
@@ -293,17 +307,18 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
                     }
 #pragma unroll
                     for (int w = 0; w < LB_WINDOW; w++)
-                        sv[w] = (t - w >= 0) ? *reinterpret_cast<volatile unsigned*>(status + (t - w) * RADIX + tid)
+                        sv[w] = (t - w >= 0) ? *reinterpret_cast<volatile unsigned*>(status + (size_t)(t - w) * RADIX + tid)
                                              : (2u << 30);
                 }
                 if (timed_out) {
                     atomicOr(&ctr->error, ERR_SORT_LOOKBACK);
                     atomicOr(&sticky->error, ERR_SORT_LOOKBACK);
                 }
-                *reinterpret_cast<volatile unsigned*>(status + tile * RADIX + tid) = SF_PRE | ((excl + count) & SF_VAL);
+                *reinterpret_cast<volatile unsigned*>(status + (size_t)tile * RADIX + tid) = SF_PRE | ((excl + count) & SF_VAL);
             }
-            S.gbase[tid] = S.goff[tid] + excl;
-            if (status_next) status_next[tile * RADIX + tid] = 0u;
+            // output index of tile-sorted element j of this digit = gbase[d] + j (mod 2^32)
+            S.gbase[tid] = S.goff[tid] + excl - lo;
+            if (status_next) status_next[(size_t)tile * RADIX + tid] = 0u;
         }
         // reorder the tile by digit in shared memory (the other warps start while
         // the digit threads look back)
@@ -316,15 +331,26 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             S.vals[pos] = v[i];
         }
         __syncthreads(); // E
-        const long long rem = n - tile * S_TILE;
-        const int valid = rem < S_TILE ? (int)rem : S_TILE;
-        for (int j = tid; j < valid; j += S_THREADS) {
-            const K kk = S.keys[j];
-            const unsigned d = (unsigned)(kk >> shift) & 0xffu;
-            const unsigned dst = S.gbase[d] + (unsigned)j - S.loff[d];
-            if (dst < (unsigned long long)n) { // always true unless a bounded wait gave up
-                kout[dst] = kk;
-                vout[dst] = S.vals[j];
+        const unsigned rem = n - tile * S_TILE;
+        if (rem >= (unsigned)S_TILE) {
+#pragma unroll
+            for (int u = 0; u < S_KPT; u++) {
+                const int j = tid + u * S_THREADS;
+                const K kk = S.keys[j];
+                const unsigned dst = S.gbase[(unsigned)(kk >> shift) & 0xffu] + (unsigned)j;
+                if (dst < n) { // always true unless a bounded wait gave up
+                    kout[dst] = kk;
+                    vout[dst] = S.vals[j];
+                }
+            }
+        } else {
+            for (int j = tid; j < (int)rem; j += S_THREADS) {
+                const K kk = S.keys[j];
+                const unsigned dst = S.gbase[(unsigned)(kk >> shift) & 0xffu] + (unsigned)j;
+                if (dst < n) {
+                    kout[dst] = kk;
+                    vout[dst] = S.vals[j];
+                }
             }
         }
         for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) (&S.whist[0][0])[j] = 0u;
