@@ -48,11 +48,11 @@ typedef enum {
     RG_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up (result invalid) */
     RG_ERR_BUSY = 6,
     RG_ERR_NOT_READY = 7,
-    RG_ERR_UNSUPPORTED = 8   /* entry point or option not built yet */
+    RG_ERR_UNSUPPORTED = 8   /* option not supported (e.g. rg_backward in RoofGS mode) */
 } rg_status;
 
 typedef struct rg_scene rg_scene;   /* opaque; owns every device buffer it allocates */
-typedef struct rg_server rg_server; /* opaque; request loop (not built yet) */
+typedef struct rg_server rg_server; /* opaque; request loop (rg_server_create) */
 
 /* storage flags of rg_scene_desc */
 #define RG_STORE_FP32 1u     /* keep the FP32 attributes (needed by RG_MODE_EXACT) */
