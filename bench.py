@@ -70,6 +70,7 @@ def parse():
     p.add_argument("--no-exact", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-backward", action="store_true")
+    p.add_argument("--no-ortho", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
 
@@ -249,14 +250,38 @@ def run_ours(a, rank, world, local_rank):
         poses_used = sorted({(rank + k * world) % len(cams) for k in range(steps)})
         results[mode] = {"ms": ms, "steps": steps, "stats": mean_stats(stats, poses_used),
                          "stage_ms": [x / max(frames, 1) for x in stage_ms], "frames_timed_by_events": frames}
-    # end-to-end through the public API: render + device->host read of every frame into pinned memory
-    host = torch.empty((3, a.height, a.width), dtype=torch.float32, pin_memory=True)
+    # end-to-end through the public API: every frame rendered by rg_render and read back into pinned
+    # host memory inside the timed region. Serial: render, copy, render, ... on one stream.
+    # Pipelined (the number reported): two image buffers; frame k's device->host copy runs on a
+    # copy stream while frame k+1 renders, and a buffer is rendered into again only after its
+    # previous image has reached the host.
     e2e_steps = max(5, min(a.steps, 60))
+    hosts = [torch.empty((3, a.height, a.width), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    outs = [out, torch.empty_like(out)]
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         gs.render(cams[(rank + k * world) % len(cams)], mode="roofgs", out=out)
-        host.copy_(out, non_blocking=True)
+        hosts[0].copy_(out, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_serial_s = time.perf_counter() - t0
+    rs = torch.cuda.current_stream(dev)
+    cs = torch.cuda.Stream(dev)
+    rendered = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        b = k & 1
+        if k >= 2:
+            rs.wait_event(copied[b])
+        gs.render(cams[(rank + k * world) % len(cams)], mode="roofgs", out=outs[b], stream=rs)
+        rendered[b].record(rs)
+        cs.wait_event(rendered[b])
+        with torch.cuda.stream(cs):
+            hosts[b].copy_(outs[b], non_blocking=True)
+        copied[b].record(cs)
     torch.cuda.synchronize(dev)
     barrier()
     e2e_s = time.perf_counter() - t0
@@ -264,6 +289,8 @@ def run_ours(a, rank, world, local_rank):
     extra = {}
     if rank == 0 and not a.no_batch:
         extra["batch"] = run_batch(a, sc, gs, dev)
+    if rank == 0 and not a.no_ortho:
+        extra["ortho"] = run_ortho(a, sc, cams, gs, dev)
     if rank == 0 and not a.no_backward:
         extra["backward"] = run_backward(dev)
     if rank == 0 and not a.no_serve:
@@ -285,6 +312,8 @@ def run_ours(a, rank, world, local_rank):
            "resolution": [a.width, a.height], "tile": [16, 16], "poses": a.poses, "parallelism": "replicas",
            "l2": "inputs larger than L2: 240 MB compact scene read per frame, 99.5 MB image written per frame",
            "entries_per_frame": round(r["stats"]["n_entries"]),
+           "visible_per_frame": round(r["stats"]["n_visible"]),
+           "pairs_per_frame": round(r["stats"]["n_pairs"]), "blends_per_frame": round(r["stats"]["n_blends"]),
            "stage_ms": dict(zip(STAGES, [round(x, 4) for x in r["stage_ms"]]))}
     if "exact" in results:
         ex = results["exact"]
@@ -301,7 +330,9 @@ def run_ours(a, rank, world, local_rank):
     line["gpu_launches"] = r["steps"] * (1 + 1 + gp + 1 + 1 + int(r["stats"]["sort_passes"]) + 1 + 1)
     line["e2e"] = {"value": round(world * e2e_steps / e2e_s, 2), "unit": UNIT,
                    "h2d_bytes_per_step": 100,  # the rg_camera struct, passed by value per call
-                   "d2h_bytes_per_step": 3 * a.width * a.height * 4}
+                   "d2h_bytes_per_step": 3 * a.width * a.height * 4,
+                   "mode": "pipelined: copy of frame k overlaps the render of frame k+1",
+                   "serial_value": round(world * e2e_steps / e2e_serial_s, 2)}
     line["clocks"] = {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if clocks else None
     line.update(extra)
     if world == 1 and not a.no_cpu_baseline:
@@ -398,6 +429,60 @@ def run_backward(dev):
         res[name] = {"forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3)}
         gs.close()
     res["note"] = "exact mode; backward replays front end, sort and per-pixel blend (one host sync per call)"
+    return res
+
+
+def run_ortho(a, sc, cams, gs, dev):
+    """Orthogonality with pruning (the paper's orthogonality table, synthetic analog): FPS of the exact
+    and RoofGS modes on the full scene and on the 10 % of its Gaussians with the largest footprint score
+    (synth.prune_by_footprint), at 1080p (500k clustered) and at the 4K workload."""
+    import numpy as np
+    import torch
+
+    from paper_2608_15785_gb300 import binding, synth
+
+    def fps(scene, cs, mode, frames):
+        for c in cs:
+            scene.render(c, mode=mode, stats=True)  # size the workspace for every pose
+        out = torch.empty((3, cs[0].height, cs[0].width), device=dev)
+        for k in range(3):
+            scene.render(cs[k % len(cs)], mode=mode, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(frames):
+            scene.render(cs[k % len(cs)], mode=mode, out=out)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        scene.check()
+        return frames / (e0.elapsed_time(e1) / 1e3)
+
+    def psnr(scene, cam):
+        x = scene.render(cam, mode="exact").double()
+        y = scene.render(cam, mode="roofgs").double()
+        mse = float(((x - y) ** 2).mean())
+        return 99.0 if mse == 0 else 10 * np.log10(1.0 / mse)
+
+    res = {"pruning": "keep 10 % of the Gaussians with the largest opacity x s1 x s2 (two largest axes)"}
+    sc2 = synth.clustered_scene(500_000, 1)
+    cams2 = [synth.orbit_camera(k, 1920, 1080) for k in range(10)]
+    for label, full, cs, frames, gfull in (("1080p, 500k", sc2, cams2, 100, None),
+                                            ("4K, 3M", sc, cams[:10], 40, gs)):
+        pr = synth.prune_by_footprint(full, 0.1)
+        row = {}
+        for tag, scene_np, g in (("full", full, gfull), ("pruned", pr, None)):
+            own = g is None
+            if own:
+                g = binding.Scene(scene_np, sh_scale_mode=binding.RG_SH_SCALE_BAND_GAUSS)
+            row[tag] = {"gaussians": int(scene_np.n), "exact_fps": round(fps(g, cs, "exact", max(10, frames // 4)), 1),
+                        "roofgs_fps": round(fps(g, cs, "roofgs", frames), 1),
+                        "psnr_roofgs_vs_exact_db": round(psnr(g, cs[0]), 2)}
+            if own:
+                g.close()
+        base = row["full"]["exact_fps"]
+        row["speedup_vs_exact_full"] = {"roofgs": round(row["full"]["roofgs_fps"] / base, 2),
+                                        "pruned_exact": round(row["pruned"]["exact_fps"] / base, 2),
+                                        "pruned_roofgs": round(row["pruned"]["roofgs_fps"] / base, 2)}
+        res[label] = row
     return res
 
 

@@ -152,3 +152,15 @@ def workload(name: str, n: int | None = None):
     scene = clustered_scene(n or w["n"], w["seed"])
     poses = 1 if name == "clustered_1080p" else 30
     return scene, [orbit_camera(k, w["width"], w["height"]) for k in range(poses)]
+
+
+def prune_by_footprint(scene: Scene, keep: float) -> Scene:
+    """Keep the fraction `keep` of the Gaussians with the largest o * s1 * s2
+    (opacity times the area spanned by the two largest axes), in their original
+    order: a synthetic stand-in for a learned pruning method, used to check that
+    the renderer's savings compose with pruning."""
+    s = np.sort(scene.scales, axis=1)
+    score = scene.opacities * s[:, 2] * s[:, 1]
+    k = max(1, int(round(keep * scene.n)))
+    idx = np.sort(np.argsort(-score, kind="stable")[:k])
+    return scene.subset(idx)
