@@ -175,6 +175,27 @@ def test_roofgs_ingredient_toggles(tiny, flags):
     assert_close(img, ref, diag, TOL + HALF_COLOUR, label="flags %d" % flags)
 
 
+@pytest.mark.parametrize("flags", [0, binding.RG_FLAG_SINGLE_PIXEL, binding.RG_FLAG_EXACT_EXP])
+def test_timed_launch_equals_counting_launch(flags):
+    """The counting launch of a stats call and the launch timed by the benchmark are
+    separate kernel variants: both must give the same bits, on close, far,
+    thin-Gaussian and ragged views."""
+    needles = synth.tiny_scene(4000, seed=7)
+    rng = np.random.default_rng(7)
+    needles.scales = (needles.scales * np.where(rng.random((4000, 3)) < 0.5, 0.02, 6.0)).astype(np.float32)
+    cases = [(synth.tiny_scene(10_000, seed=0), [synth.tiny_camera(256, 256), synth.tiny_camera(100, 37)]),
+             (needles, [synth.tiny_camera(320, 200), synth.tiny_camera(97, 131)]),
+             (synth.clustered_scene(200_000, seed=3), [synth.orbit_camera(k, 1280, 720, radius=r)
+                                                       for k, r in ((0, 4.0), (5, 1.6), (9, 12.0))])]
+    for sc, cams in cases:
+        gs = gpu_scene(sc)
+        for cam in cams:
+            a, _ = render(gs, cam, "roofgs", flags=flags, stats=True)
+            b = render(gs, cam, "roofgs", flags=flags)
+            assert np.array_equal(a, b), (cam.width, cam.height)
+            assert a.std() > 0
+
+
 def test_roofgs_psnr_against_exact_tiny(tiny):
     sc, cam, gs, _ = tiny
     a = render(gs, cam, "exact")
