@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-backward", action="store_true")
     p.add_argument("--no-ortho", action="store_true")
+    p.add_argument("--ppt", type=int, default=4, choices=(1, 2, 4),
+                   help="RoofGS pixels per thread in the rasterizer (2 = the paper's dual-pixel scheme)")
     p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
 
@@ -216,7 +218,7 @@ def run_ours(a, rank, world, local_rank):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(steps):
-            gs.render(cams[(rank + k * world) % len(cams)], mode=mode, flags=flags, out=out)
+            gs.render(cams[(rank + k * world) % len(cams)], mode=mode, flags=flags | rflags, out=out)
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
@@ -226,6 +228,8 @@ def run_ours(a, rank, world, local_rank):
             ms = float(t.item())
         return ms
 
+    # RoofGS ingredient flag for the rasterizer's pixels per thread (ignored in exact mode)
+    rflags = {1: binding.RG_FLAG_SINGLE_PIXEL, 2: 0, 4: binding.RG_FLAG_QUAD_PIXEL}[a.ppt]
     results = {}
     sampler = ClockSampler(bus_id) if rank == 0 else None
     modes = ["roofgs"] if a.no_exact else ["roofgs", "exact"]
@@ -233,10 +237,10 @@ def run_ours(a, rank, world, local_rank):
         # checked frames: size the workspace for every pose, collect the work counters
         stats = []
         for cam in cams:
-            _, st = gs.render(cam, mode=mode, out=out, stats=True)
+            _, st = gs.render(cam, mode=mode, flags=rflags, out=out, stats=True)
             stats.append(st)
         for k in range(a.warmup):
-            gs.render(cams[k % len(cams)], mode=mode, out=out)
+            gs.render(cams[k % len(cams)], mode=mode, flags=rflags, out=out)
         torch.cuda.synchronize(dev)
         gs.stage_times()  # discard
         steps = a.steps if mode == "roofgs" else max(10, a.steps // 2)
@@ -261,7 +265,7 @@ def run_ours(a, rank, world, local_rank):
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        gs.render(cams[(rank + k * world) % len(cams)], mode="roofgs", out=out)
+        gs.render(cams[(rank + k * world) % len(cams)], mode="roofgs", flags=rflags, out=out)
         hosts[0].copy_(out, non_blocking=True)
     torch.cuda.synchronize(dev)
     barrier()
@@ -276,7 +280,7 @@ def run_ours(a, rank, world, local_rank):
         b = k & 1
         if k >= 2:
             rs.wait_event(copied[b])
-        gs.render(cams[(rank + k * world) % len(cams)], mode="roofgs", out=outs[b], stream=rs)
+        gs.render(cams[(rank + k * world) % len(cams)], mode="roofgs", flags=rflags, out=outs[b], stream=rs)
         rendered[b].record(rs)
         cs.wait_event(rendered[b])
         with torch.cuda.stream(cs):
@@ -294,7 +298,7 @@ def run_ours(a, rank, world, local_rank):
     if rank == 0 and not a.no_backward:
         extra["backward"] = run_backward(dev)
     if rank == 0 and not a.no_serve:
-        extra["serve"] = run_serve(dev, gs)
+        extra["serve"] = run_serve(dev, gs, a.ppt)
     clocks = sampler.stop() if sampler else None
     if dist is not None:
         dist.barrier()
@@ -308,7 +312,7 @@ def run_ours(a, rank, world, local_rank):
     line = {"metric": METRIC, "value": round(fps, 2), "unit": UNIT, "n_gpus": world, "steps": r["steps"],
             "warmup": a.warmup, "ms_per_step": round(r["ms"] / r["steps"], 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
-    cfg = {"workload": workload_desc(a), "mode": "roofgs", "n_gaussians": a.gaussians,
+    cfg = {"workload": workload_desc(a), "mode": "roofgs", "pixels_per_thread": a.ppt, "n_gaussians": a.gaussians,
            "resolution": [a.width, a.height], "tile": [16, 16], "poses": a.poses, "parallelism": "replicas",
            "l2": "inputs larger than L2: 240 MB compact scene read per frame, 99.5 MB image written per frame",
            "entries_per_frame": round(r["stats"]["n_entries"]),
@@ -440,17 +444,18 @@ def run_ortho(a, sc, cams, gs, dev):
     import torch
 
     from paper_2608_15785_gb300 import binding, synth
+    rf = {1: binding.RG_FLAG_SINGLE_PIXEL, 2: 0, 4: binding.RG_FLAG_QUAD_PIXEL}[a.ppt]
 
     def fps(scene, cs, mode, frames):
         for c in cs:
-            scene.render(c, mode=mode, stats=True)  # size the workspace for every pose
+            scene.render(c, mode=mode, flags=rf, stats=True)  # size the workspace for every pose
         out = torch.empty((3, cs[0].height, cs[0].width), device=dev)
         for k in range(3):
-            scene.render(cs[k % len(cs)], mode=mode, out=out)
+            scene.render(cs[k % len(cs)], mode=mode, flags=rf, out=out)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for k in range(frames):
-            scene.render(cs[k % len(cs)], mode=mode, out=out)
+            scene.render(cs[k % len(cs)], mode=mode, flags=rf, out=out)
         e1.record()
         torch.cuda.synchronize(dev)
         scene.check()
@@ -458,7 +463,7 @@ def run_ortho(a, sc, cams, gs, dev):
 
     def psnr(scene, cam):
         x = scene.render(cam, mode="exact").double()
-        y = scene.render(cam, mode="roofgs").double()
+        y = scene.render(cam, mode="roofgs", flags=rf).double()
         mse = float(((x - y) ** 2).mean())
         return 99.0 if mse == 0 else 10 * np.log10(1.0 / mse)
 
@@ -486,7 +491,7 @@ def run_ortho(a, sc, cams, gs, dev):
     return res
 
 
-def run_serve(dev, gs3):
+def run_serve(dev, gs3, ppt=2):
     """Request loop: 4 resident scenes (0.5M, 1M, 3M, 6M), Poisson arrivals of 720p/1080p/4K requests
     with random orbit poses; p50/p99 latency (submit -> image ready) and FPS at several request rates."""
     import threading
@@ -500,7 +505,8 @@ def run_serve(dev, gs3):
     scenes = [extra[0], extra[1], gs3, extra[2]]
     sizes = [(1280, 720), (1920, 1080), (3840, 2160)]
     srv = binding.Server(scenes, 3840, 2160, mode="roofgs", max_slots=8, memory_budget=96 << 30,
-                         calibration=synth.orbit_camera(0, 3840, 2160))
+                         calibration=synth.orbit_camera(0, 3840, 2160),
+                         flags={1: binding.RG_FLAG_SINGLE_PIXEL, 2: 0, 4: binding.RG_FLAG_QUAD_PIXEL}[ppt])
     pool = [torch.empty((3, 2160, 3840), device=dev) for _ in range(16)]
     rng = np.random.default_rng(11)
     results = []

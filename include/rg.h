@@ -114,6 +114,9 @@ typedef struct {
  * paper's scheme, Sec. IV-A.2), instead of ordering the Gaussians by quantized depth
  * first and sorting only the b_t tile bits of the entries; both give the same order */
 #define RG_FLAG_SORT_FULL_KEY (1u << 2)
+/* four vertically adjacent pixels per thread (Eq. (20) applied three times) instead of
+ * two; RG_FLAG_SINGLE_PIXEL takes precedence when both are given */
+#define RG_FLAG_QUAD_PIXEL (1u << 3)
 /* flags for both modes */
 #define RG_FLAG_STAGE_EVENTS (1u << 8) /* record per-stage CUDA events (rg_stage_times) */
 #define RG_FLAG_BATCH_CHECKED (1u << 9) /* rg_render_batch: synchronise, and re-size and render again on overflow */

@@ -26,6 +26,7 @@ RG_MODE_ROOFGS = 1
 RG_FLAG_EXACT_EXP = 1 << 0
 RG_FLAG_SINGLE_PIXEL = 1 << 1
 RG_FLAG_SORT_FULL_KEY = 1 << 2
+RG_FLAG_QUAD_PIXEL = 1 << 3
 RG_FLAG_STAGE_EVENTS = 1 << 8
 RG_FLAG_BATCH_CHECKED = 1 << 9
 RG_INSPECT_KEYS = 1

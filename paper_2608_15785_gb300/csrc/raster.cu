@@ -9,9 +9,10 @@
 // memory, each Gaussian's coefficients are folded (Eqs. (13)-(15)) --
 // -1/2 and log o absorbed, C1..C6 -- in TILE-LOCAL coordinates (pixel and mean
 // shifted by the tile origin, so the FP32 terms stay small at 4K); every
-// thread owns two vertically adjacent pixels (x, y) and (x, y+1): the first
-// exponent is the FMA chain of Eq. (16) on hoisted x^2, xy, y^2, x, y, the
-// second follows from Eq. (20). Pairs with P < -ln 255 are skipped before any
+// thread owns PPT vertically adjacent pixels (x, y) ... (x, y+PPT-1), two by
+// default (the paper's dual-pixel scheme), one or four on request: the first
+// exponent is the FMA chain of Eq. (16) on hoisted x^2, xy, y^2, x, y, each
+// next one follows from Eq. (20) (two additions per extra row). Pairs with P < -ln 255 are skipped before any
 // exponential (Eq. (23)); alpha = min(0.99, exp^(P)) with the bit-level
 // exponential of Eq. (24) (Eq. (25)). A warp whose pixels are all finished
 // skips the batch (vote); the block leaves once every pixel is finished.
@@ -36,8 +37,6 @@ __global__ void k_fast_exp_eval(const float* P, float* out, long long n)
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = fast_exp(P[i]);
 }
-
-constexpr int R_THREADS = 128;  // 128 threads x 2 pixels = one 16x16 tile
 
 template <bool FAST, bool COUNT>
 __device__ __forceinline__ void blend(float P, float r, float g, float b, float& T, float& c0, float& c1, float& c2,
@@ -78,32 +77,40 @@ __device__ __forceinline__ void flush_counts(Counters* c, unsigned n_eval, unsig
     }
 }
 
-template <bool FAST, bool DUAL, bool COUNT>
-__global__ void __launch_bounds__(DUAL ? R_THREADS : 256) k_raster_roofgs(RasterArgs a)
+template <bool FAST, int PPT, bool COUNT>
+__global__ void __launch_bounds__(256 / PPT) k_raster_roofgs(RasterArgs a)
 {
-    constexpr int NT = DUAL ? R_THREADS : 256;
+    constexpr int NT = 256 / PPT; // threads per 16x16 tile
     __shared__ float4 s_c0[NT];
     __shared__ float4 s_c1[NT];
-    __shared__ float4 s_c2[NT];
+    __shared__ float s_cb[NT];
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int x0 = tx * TILE, y0 = ty * TILE;
     const int t = threadIdx.x;
+    // the thread's pixels: (x, y), (x, y+1), ..., (x, y+PPT-1)
     const int lx = t & 15;
-    const int ly = DUAL ? (t >> 4) * 2 : (t >> 4);
+    const int ly = (t >> 4) * PPT;
     const int px = x0 + lx, py = y0 + ly;
     const int W = a.cam.W, H = a.cam.H;
-    bool done1 = !(px < W && py < H);
-    bool done2 = DUAL ? !(px < W && py + 1 < H) : true;
+    bool done[PPT];
+    float T[PPT], cr[PPT], cg[PPT], cb[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; i++) {
+        done[i] = !(px < W && py + i < H);
+        T[i] = 1.0f;
+        cr[i] = cg[i] = cb[i] = 0.0f;
+    }
     // hoisted pixel terms (tile-local)
     const float x = (float)lx, y = (float)ly;
     const float xx = x * x, xy = x * y, yy = y * y, y2p1 = 2.0f * y + 1.0f;
-    float T1 = 1.0f, T2 = 1.0f;
-    float r1 = 0.f, g1 = 0.f, b1 = 0.f, r2 = 0.f, g2 = 0.f, b2 = 0.f;
     unsigned n_eval = 0, n_blend = 0;
     const uint2 range = a.ranges[tile];
     for (unsigned start = range.x; start < range.y; start += NT) {
-        if (__syncthreads_count(!(done1 && done2)) == 0) break;
+        bool all_done = true;
+#pragma unroll
+        for (int i = 0; i < PPT; i++) all_done = all_done && done[i];
+        if (__syncthreads_count(!all_done) == 0) break;
         const unsigned j = start + t;
         if (j < range.y) {
             unsigned id = a.vals[j];
@@ -111,52 +118,55 @@ __global__ void __launch_bounds__(DUAL ? R_THREADS : 256) k_raster_roofgs(Raster
             const float4 q0 = __ldg(&a.rec[2 * id]);
             const float4 q1 = __ldg(&a.rec[2 * id + 1]);
             const float u = q0.x - (float)x0, v = q0.y - (float)y0;
-            const float ca = q0.z, cb = q0.w, cc = q1.x, logo = q1.y;
+            const float ca = q0.z, cbq = q0.w, cc = q1.x, logo = q1.y;
             // Eq. (15): folded coefficients
-            const float C1 = -0.5f * ca, C2 = -0.5f * cb, C3 = -0.5f * cc;
-            const float C4 = fmaf(ca, u, 0.5f * cb * v);
-            const float C5 = fmaf(cc, v, 0.5f * cb * u);
-            const float C0 = fmaf(ca * u, u, fmaf(cb * u, v, cc * v * v)); // Eq. (14)
+            const float C1 = -0.5f * ca, C2 = -0.5f * cbq, C3 = -0.5f * cc;
+            const float C4 = fmaf(ca, u, 0.5f * cbq * v);
+            const float C5 = fmaf(cc, v, 0.5f * cbq * u);
+            const float C0 = fmaf(ca * u, u, fmaf(cbq * u, v, cc * v * v)); // Eq. (14)
             const float C6 = fmaf(-0.5f, C0, logo);
             const unsigned rg = __float_as_uint(q1.z), bb = __float_as_uint(q1.w);
-            const float cr = __half2float(__ushort_as_half((unsigned short)(rg & 0xffffu)));
-            const float cg = __half2float(__ushort_as_half((unsigned short)(rg >> 16)));
-            const float cbl = __half2float(__ushort_as_half((unsigned short)(bb & 0xffffu)));
+            const float fr = __half2float(__ushort_as_half((unsigned short)(rg & 0xffffu)));
+            const float fg = __half2float(__ushort_as_half((unsigned short)(rg >> 16)));
+            const float fb = __half2float(__ushort_as_half((unsigned short)(bb & 0xffffu)));
             s_c0[t] = make_float4(C1, C2, C3, C4);
-            s_c1[t] = make_float4(C5, C6, cr, cg);
-            s_c2[t] = make_float4(cbl, 0.f, 0.f, 0.f);
+            s_c1[t] = make_float4(C5, C6, fr, fg);
+            s_cb[t] = fb;
         }
         __syncthreads();
         const int cnt = min((unsigned)NT, range.y - start);
-        if (!__all_sync(0xffffffffu, done1 && done2)) {
+        if (!__all_sync(0xffffffffu, all_done)) {
             for (int k = 0; k < cnt; k++) {
                 const float4 c0 = s_c0[k];
                 const float4 c1 = s_c1[k];
-                const float cbl = s_c2[k].x;
+                const float fb = s_cb[k];
                 // Eq. (16): P(x, y) = C1 x^2 + C2 xy + C3 y^2 + C4 x + C5 y + C6
-                const float P1 = fmaf(c0.x, xx, fmaf(c0.y, xy, fmaf(c0.z, yy, fmaf(c0.w, x, fmaf(c1.x, y, c1.y)))));
-                blend<FAST, COUNT>(P1, c1.z, c1.w, cbl, T1, r1, g1, b1, done1, n_eval, n_blend);
-                if (DUAL) {
-                    // Eq. (20): P(x, y+1) = P(x, y) + C2 x + C3 (2y + 1) + C5
-                    const float P2 = P1 + fmaf(c0.y, x, fmaf(c0.z, y2p1, c1.x));
-                    blend<FAST, COUNT>(P2, c1.z, c1.w, cbl, T2, r2, g2, b2, done2, n_eval, n_blend);
+                float P = fmaf(c0.x, xx, fmaf(c0.y, xy, fmaf(c0.z, yy, fmaf(c0.w, x, fmaf(c1.x, y, c1.y)))));
+                blend<FAST, COUNT>(P, c1.z, c1.w, fb, T[0], cr[0], cg[0], cb[0], done[0], n_eval, n_blend);
+                if (PPT >= 2) {
+                    // Eq. (20): P(x, y+1) = P(x, y) + C2 x + C3 (2y + 1) + C5; the step to the next
+                    // row grows by 2 C3 per row
+                    float d = fmaf(c0.y, x, fmaf(c0.z, y2p1, c1.x));
+#pragma unroll
+                    for (int i = 1; i < PPT; i++) {
+                        if (i > 1) d = fmaf(2.0f, c0.z, d);
+                        P = P + d;
+                        blend<FAST, COUNT>(P, c1.z, c1.w, fb, T[i], cr[i], cg[i], cb[i], done[i], n_eval, n_blend);
+                    }
                 }
             }
         }
     }
     if (COUNT) flush_counts(a.count, n_eval, n_blend);
     const size_t plane = (size_t)W * H;
-    if (px < W && py < H) {
-        const size_t o = (size_t)py * W + px;
-        a.out[o] = r1 + T1 * a.cam.bg[0];
-        a.out[plane + o] = g1 + T1 * a.cam.bg[1];
-        a.out[2 * plane + o] = b1 + T1 * a.cam.bg[2];
-    }
-    if (DUAL && px < W && py + 1 < H) {
-        const size_t o = (size_t)(py + 1) * W + px;
-        a.out[o] = r2 + T2 * a.cam.bg[0];
-        a.out[plane + o] = g2 + T2 * a.cam.bg[1];
-        a.out[2 * plane + o] = b2 + T2 * a.cam.bg[2];
+#pragma unroll
+    for (int i = 0; i < PPT; i++) {
+        if (px < W && py + i < H) {
+            const size_t o = (size_t)(py + i) * W + px;
+            a.out[o] = cr[i] + T[i] * a.cam.bg[0];
+            a.out[plane + o] = cg[i] + T[i] * a.cam.bg[1];
+            a.out[2 * plane + o] = cb[i] + T[i] * a.cam.bg[2];
+        }
     }
 }
 
@@ -164,12 +174,14 @@ template <bool COUNT>
 static void raster_roofgs_variant(const RasterArgs& a, cudaStream_t s)
 {
     const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
-    if (a.dual_pixel) {
-        if (a.fast_exp) k_raster_roofgs<true, true, COUNT><<<tiles, R_THREADS, 0, s>>>(a);
-        else k_raster_roofgs<false, true, COUNT><<<tiles, R_THREADS, 0, s>>>(a);
+    if (a.fast_exp) {
+        if (a.ppt == 1) k_raster_roofgs<true, 1, COUNT><<<tiles, 256, 0, s>>>(a);
+        else if (a.ppt == 4) k_raster_roofgs<true, 4, COUNT><<<tiles, 64, 0, s>>>(a);
+        else k_raster_roofgs<true, 2, COUNT><<<tiles, 128, 0, s>>>(a);
     } else {
-        if (a.fast_exp) k_raster_roofgs<true, false, COUNT><<<tiles, 256, 0, s>>>(a);
-        else k_raster_roofgs<false, false, COUNT><<<tiles, 256, 0, s>>>(a);
+        if (a.ppt == 1) k_raster_roofgs<false, 1, COUNT><<<tiles, 256, 0, s>>>(a);
+        else if (a.ppt == 4) k_raster_roofgs<false, 4, COUNT><<<tiles, 64, 0, s>>>(a);
+        else k_raster_roofgs<false, 2, COUNT><<<tiles, 128, 0, s>>>(a);
     }
 }
 

@@ -396,7 +396,7 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     } else {
         r.rec = w.rec.as<float4>();
         r.fast_exp = (flags & RG_FLAG_EXACT_EXP) ? 0 : 1;
-        r.dual_pixel = (flags & RG_FLAG_SINGLE_PIXEL) ? 0 : 1;
+        r.ppt = (flags & RG_FLAG_SINGLE_PIXEL) ? 1 : ((flags & RG_FLAG_QUAD_PIXEL) ? 4 : 2);
         launch_raster_roofgs(r, st);
     }
     if (ev) RG_CK(cudaEventRecord(E[6], st));
@@ -438,7 +438,7 @@ struct BatchPlan {
     int mode = 0;
     uint32_t flags = 0;
     int lanes = 1;
-    uint32_t raster_flags = 0; // autotuned: 0 (two pixels per thread) or RG_FLAG_SINGLE_PIXEL
+    uint32_t raster_flags = 0; // autotuned: 0 (two pixels per thread), RG_FLAG_SINGLE_PIXEL or RG_FLAG_QUAD_PIXEL
     bool tuned = false;
     std::unique_ptr<Workspace[]> ws{new Workspace[BATCH_MAX_LANES]};
     cudaStream_t streams[BATCH_MAX_LANES] = {nullptr};
@@ -535,7 +535,7 @@ rg_status plan_capture(BatchPlan& P, const std::vector<FrameLayout>& F, float* c
     rg_status err = RG_OK;
     cudaError_t ce = cudaEventRecord(P.fork, P.cap);
     for (int l = 0; l < lanes && ce == cudaSuccess; l++) ce = cudaStreamWaitEvent(P.streams[l], P.fork, 0);
-    const uint32_t fl = (P.flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL)) | raster_flags;
+    const uint32_t fl = (P.flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL)) | raster_flags;
     for (size_t v = 0; v < F.size() && ce == cudaSuccess && err == RG_OK; v++)
         err = render_once(P.scenes[v], P.ws[v % lanes], F[v], P.mode, fl, outs[v], P.streams[v % lanes]);
     for (int l = 0; l < lanes && ce == cudaSuccess; l++) {
@@ -590,7 +590,7 @@ rg_status plan_tune(BatchPlan& P, const std::vector<FrameLayout>& F, float* cons
     RG_CK(cudaEventCreate(&e1));
     for (int lanes : {1, 2, 4}) {
         if (lanes > V && lanes > 1) continue;
-        for (uint32_t r : {0u, (uint32_t)RG_FLAG_SINGLE_PIXEL}) {
+        for (uint32_t r : {0u, (uint32_t)RG_FLAG_SINGLE_PIXEL, (uint32_t)RG_FLAG_QUAD_PIXEL}) {
             if (P.mode != RG_MODE_ROOFGS && r) continue;
             rg_status e = plan_capture(P, F, outs, lanes, r);
             if (e != RG_OK) {
@@ -1122,7 +1122,7 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lock(g_batch_mu);
     BatchPlan* P = nullptr;
-    const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_BATCH_CHECKED);
+    const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL | RG_FLAG_BATCH_CHECKED);
     for (auto& p : g_plans) {
         if (p->device != dev || p->mode != mode || p->flags != key_flags || p->scenes != vs) continue;
         bool same = true;
@@ -1184,7 +1184,7 @@ rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, 
     int dev = 0;
     RG_CK(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(g_batch_mu);
-    const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_BATCH_CHECKED);
+    const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL | RG_FLAG_BATCH_CHECKED);
     for (auto& p : g_plans) {
         if (p->device != dev || p->mode != opts->mode || p->flags != key_flags || (int)p->scenes.size() != n) continue;
         bool same = true;
@@ -1192,7 +1192,7 @@ rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, 
             same = p->scenes[v] == scenes[scene_idx[v]] && p->widths[v] == cams[v].width && p->heights[v] == cams[v].height;
         if (same) {
             *lanes = p->lanes;
-            *pixels_per_thread = (p->raster_flags & RG_FLAG_SINGLE_PIXEL) ? 1 : 2;
+            *pixels_per_thread = (p->raster_flags & RG_FLAG_SINGLE_PIXEL) ? 1 : ((p->raster_flags & RG_FLAG_QUAD_PIXEL) ? 4 : 2);
             return RG_OK;
         }
     }

@@ -435,7 +435,7 @@ struct RasterArgs {
     // RoofGS
     const float4* rec;
     int fast_exp;
-    int dual_pixel;
+    int ppt;              // pixels per thread: 1, 2 (Eq. (20)) or 4
     // exact
     const float2* xy;
     const float4* conic_op;

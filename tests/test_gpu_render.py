@@ -166,6 +166,7 @@ def test_roofgs_mode_within_fast_exp_bound_tiny(tiny):
 
 @pytest.mark.parametrize("flags", [binding.RG_FLAG_EXACT_EXP, binding.RG_FLAG_SINGLE_PIXEL,
                                    binding.RG_FLAG_EXACT_EXP | binding.RG_FLAG_SINGLE_PIXEL,
+                                   binding.RG_FLAG_QUAD_PIXEL, binding.RG_FLAG_EXACT_EXP | binding.RG_FLAG_QUAD_PIXEL,
                                    binding.RG_FLAG_SORT_FULL_KEY])
 def test_roofgs_ingredient_toggles(tiny, flags):
     sc, cam, gs, comp = tiny
@@ -175,7 +176,7 @@ def test_roofgs_ingredient_toggles(tiny, flags):
     assert_close(img, ref, diag, TOL + HALF_COLOUR, label="flags %d" % flags)
 
 
-@pytest.mark.parametrize("flags", [0, binding.RG_FLAG_SINGLE_PIXEL, binding.RG_FLAG_EXACT_EXP])
+@pytest.mark.parametrize("flags", [0, binding.RG_FLAG_SINGLE_PIXEL, binding.RG_FLAG_QUAD_PIXEL, binding.RG_FLAG_EXACT_EXP])
 def test_timed_launch_equals_counting_launch(flags):
     """The counting launch of a stats call and the launch timed by the benchmark are
     separate kernel variants: both must give the same bits, on close, far,
@@ -359,12 +360,19 @@ def test_full_size_parity(name, per_gauss):
         ref, diag, _ = oracle.render(sc, cam, om, comp=comp if mode == "roofgs" else None, exp_kind=kind, tiles=tiles)
         base = TOL if mode == "exact" else TOL + HALF_COLOUR
         tol = base + allowance(diag)
-        err = np.abs(img - ref)[:, mask]
-        over = float(np.mean((err > base).any(axis=0)))
-        print("%s %s: max |err| %.3g over %d sampled tiles, pixels over the strict %.3g: %.5f" % (
-            name, mode, float(err.max()), len(tiles), base, over))
-        assert (err <= tol[mask][None]).all(), "%s %s: worst excess %.3g" % (name, mode, (err - tol[mask][None]).max())
-        assert over <= 0.02
+        # RoofGS: the default two pixels per thread, and the four of the benchmark's timed frames
+        variants = [("", img)] if mode == "exact" else [
+            (" ppt2", img), (" ppt4", render(gs, cam, mode, flags=binding.RG_FLAG_QUAD_PIXEL))]
+        for label, im in variants:
+            err = np.abs(im - ref)[:, mask]
+            over = float(np.mean((err > base).any(axis=0)))
+            print("%s %s%s: max |err| %.3g over %d sampled tiles, pixels over the strict %.3g: %.5f" % (
+                name, mode, label, float(err.max()), len(tiles), base, over))
+            assert (err <= tol[mask][None]).all(), "%s %s%s: worst excess %.3g" % (
+                name, mode, label, (err - tol[mask][None]).max())
+            assert over <= 0.02
     a = render(gs, cam, "exact")
     b = render(gs, cam, "roofgs")
     assert psnr(a, b) >= 46.4, psnr(a, b)
+    b4 = render(gs, cam, "roofgs", flags=binding.RG_FLAG_QUAD_PIXEL)
+    assert psnr(a, b4) >= 46.4, psnr(a, b4)
