@@ -50,9 +50,9 @@ REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_powe
 OPS = {"roofgs": (5, 11), "exact": (10, 20)}
 STAGES = ["depth_order", "front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"]
 # DRAM bytes per entry of one tile-bit one-sweep pass: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the first tile-bit pass on the 1M-Gaussian 4K case
-# (218.6 MB + 178.7 MB for 27.03 M entries), scaled by the entries of the launch
-SORT_PASS_TRAFFIC_PER_ENTRY = 14.7
+# dram__bytes_write.sum of the tile-bit passes on the 1M-Gaussian 4K case
+# (220.2 + 173.2 MB and 220.0 + 169.0 MB for 27.03 M entries), scaled by the entries of the launch
+SORT_PASS_TRAFFIC_PER_ENTRY = 14.5
 
 
 def parse():
@@ -314,7 +314,8 @@ def run_ours(a, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
     cfg = {"workload": workload_desc(a), "mode": "roofgs", "pixels_per_thread": a.ppt, "n_gaussians": a.gaussians,
            "resolution": [a.width, a.height], "tile": [16, 16], "poses": a.poses, "parallelism": "replicas",
-           "l2": "inputs larger than L2: 240 MB compact scene read per frame, 99.5 MB image written per frame",
+           "l2": "inputs larger than L2: %.0f MB compact scene read per frame, %.1f MB image written per frame" % (
+               80e-6 * a.gaussians, 12e-6 * a.width * a.height),
            "entries_per_frame": round(r["stats"]["n_entries"]),
            "visible_per_frame": round(r["stats"]["n_visible"]),
            "pairs_per_frame": round(r["stats"]["n_pairs"]), "blends_per_frame": round(r["stats"]["n_blends"]),
@@ -603,7 +604,8 @@ def rooflines(r, a, props, clocks):
     traffic = None
     if dom == "sort_pass" and SORT_PASS_TRAFFIC_PER_ENTRY:
         traffic = round(SORT_PASS_TRAFFIC_PER_ENTRY * st["n_entries"])
-    names = {"sort_pass": "k_onesweep<uint32> (one tile-bit pass)", "raster": "k_raster_roofgs<fast, dual>",
+    names = {"sort_pass": "k_onesweep<uint32> (one tile-bit pass)",
+             "raster": "k_raster_roofgs<fast exp, %d pixels per thread>" % a.ppt,
              "front_end": "k_frontend_fused", "depth_order": "k_depth_keys + per-Gaussian sort",
              "sort_hist": "k_sort_hist<uint32>", "ranges": "k_ranges<uint32>"}
     roof = {"kernel": names[dom], "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
