@@ -161,7 +161,7 @@ def stage_work(mode, st, W, H):
         front = 20 * N + 16 * nf + 80 * nv + 8 * nd
         sort_pass = 16 * nd  # one pass: each (key, value) entry read once and written once
         hist = 4 * nd
-        ranges = 4 * nd + 8 * tiles
+        ranges = 0  # no ranges pass: every rasterizer block searches its tile's range in the sorted keys
     else:
         depth = 0
         # preprocess: 44 B geometry per Gaussian, 192 B FP32 SH + 56 B outputs if visible, 4 B count;
@@ -330,9 +330,9 @@ def run_ours(a, rank, world, local_rank):
     line["config"] = cfg
     line["roofline"], line["stages"] = rooflines(r, a, props, clocks)
     # per frame: depth keys, depth-sort histogram + passes, fused front end, entry histogram +
-    # tile-bit passes, ranges, rasterizer
+    # tile-bit passes, rasterizer (which finds the tile ranges itself)
     gp = (int(r["stats"]["b_d"]) + 7) // 8
-    line["gpu_launches"] = r["steps"] * (1 + 1 + gp + 1 + 1 + int(r["stats"]["sort_passes"]) + 1 + 1)
+    line["gpu_launches"] = r["steps"] * (1 + 1 + gp + 1 + 1 + int(r["stats"]["sort_passes"]) + 1)
     line["e2e"] = {"value": round(world * e2e_steps / e2e_s, 2), "unit": UNIT,
                    "h2d_bytes_per_step": 100,  # the rg_camera struct, passed by value per call
                    "d2h_bytes_per_step": 3 * a.width * a.height * 4,
@@ -587,11 +587,12 @@ def rooflines(r, a, props, clocks):
         "front_end": hbm_stage(work["front"], ms["front_end"]),
         "sort_hist": hbm_stage(work["hist"], ms["sort_hist"]),
         "sort_pass": hbm_stage(work["sort_pass"], ms["sort_passes"] / passes),
-        "ranges": hbm_stage(work["ranges"], ms["ranges"]),
+        "ranges": hbm_stage(work["ranges"], ms["ranges"]) if work["ranges"] else None,
         "raster": {"bound": "alu", "achieved": work["raster_ops"] / (ms["raster"] * 1e-3) / 1e9, "peak": alu_peak,
                    "unit": "Gop/s", "ms": ms["raster"], "ops": work["raster_ops"]},
     }
     stages["sort_pass"]["launches_per_frame"] = work["passes"]
+    stages = {k: v for k, v in stages.items() if v is not None}
     for v in stages.values():
         v["frac"] = round(v["achieved"] / v["peak"], 4)
         v["achieved"] = round(v["achieved"], 1)

@@ -77,6 +77,28 @@ __device__ __forceinline__ void flush_counts(Counters* c, unsigned n_eval, unsig
     }
 }
 
+// First index i in [0, n) with (keys[i] >> shift) >= t, n if none (keys sorted): a
+// 33-ary search by one warp, each round 32 lanes probe and one ballot keeps the part
+// that holds the boundary (six dependent loads for 68 M keys). Warp-uniform result.
+__device__ __forceinline__ unsigned warp_lower_bound(const unsigned* __restrict__ keys, unsigned n, int shift,
+                                                     unsigned t)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned lo = 0, hi = n; // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const unsigned probe = lo + (unsigned)(((unsigned long long)(hi - lo) * (unsigned)(lane + 1)) / 33u);
+        const bool less = (unsigned)((unsigned long long)__ldg(&keys[probe]) >> shift) < t;
+        const int c = __popc(__ballot_sync(0xffffffffu, less)); // lanes 0..c-1 probe below the boundary
+        const unsigned plo = __shfl_sync(0xffffffffu, probe, c > 0 ? c - 1 : 0);
+        const unsigned phi = __shfl_sync(0xffffffffu, probe, c < 32 ? c : 31);
+        if (c > 0) lo = plo + 1;
+        if (c < 32) hi = phi;
+    }
+    const unsigned i = lo + (unsigned)lane;
+    const bool less = i < hi && (unsigned)((unsigned long long)__ldg(&keys[i]) >> shift) < t;
+    return lo + (unsigned)__popc(__ballot_sync(0xffffffffu, less));
+}
+
 template <bool FAST, int PPT, bool COUNT>
 __global__ void __launch_bounds__(256 / PPT) k_raster_roofgs(RasterArgs a)
 {
@@ -105,7 +127,20 @@ __global__ void __launch_bounds__(256 / PPT) k_raster_roofgs(RasterArgs a)
     const float x = (float)lx, y = (float)ly;
     const float xx = x * x, xy = x * y, yy = y * y, y2p1 = 2.0f * y + 1.0f;
     unsigned n_eval = 0, n_blend = 0;
-    const uint2 range = a.ranges[tile];
+    uint2 range;
+    if (a.skeys) { // warps 0 and 1 search the first entries of tiles `tile` and `tile + 1`
+        __shared__ unsigned s_bound[2];
+        const int warp = t >> 5;
+        if (warp < 2) {
+            const unsigned b = warp_lower_bound(a.skeys, a.ctr->n_entries, a.tile_shift, (unsigned)(tile + warp));
+            if ((t & 31) == 0) s_bound[warp] = b;
+        }
+        __syncthreads();
+        range = s_bound[1] > s_bound[0] ? make_uint2(s_bound[0], s_bound[1]) : make_uint2(0u, 0u);
+        if (t == 0) a.ranges_out[tile] = range;
+    } else {
+        range = a.ranges[tile];
+    }
     for (unsigned start = range.x; start < range.y; start += NT) {
         bool all_done = true;
 #pragma unroll

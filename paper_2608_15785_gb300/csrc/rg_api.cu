@@ -248,8 +248,11 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         if (w.ev_pending < EV_RING) w.ev_pending++;
         RG_CK(cudaEventRecord(E[0], st));
     }
+    // RoofGS frames that rasterize find each tile's range inside the rasterizer (a search of
+    // the sorted keys per tile block); the others run the ranges pass
+    const bool search_ranges = mode == RG_MODE_ROOFGS && out != nullptr;
     RG_CK(cudaMemsetAsync(w.ctrl.p, 0, CTRL_ALLOC, st));
-    RG_CK(cudaMemsetAsync(w.ranges.p, 0, (size_t)F.tiles * sizeof(uint2), st));
+    if (!search_ranges) RG_CK(cudaMemsetAsync(w.ranges.p, 0, (size_t)F.tiles * sizeof(uint2), st));
     const long long n = s->n;
     SortArgs sa;
     memset(&sa, 0, sizeof(sa));
@@ -361,14 +364,16 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     launch_sort(sa, st, ev ? E[3] : nullptr);
     if (ev) RG_CK(cudaEventRecord(E[4], st));
     const int fin = sa.passes & 1;
-    RangeArgs ra;
-    ra.keys = w.keys[fin].p;
-    ra.key_bytes = sa.key_bytes;
-    ra.tile_shift = tile_shift;
-    ra.ntiles = F.tiles;
-    ra.ranges = w.ranges.as<uint2>();
-    ra.ctr = ctr;
-    launch_ranges(ra, st);
+    if (!search_ranges) {
+        RangeArgs ra;
+        ra.keys = w.keys[fin].p;
+        ra.key_bytes = sa.key_bytes;
+        ra.tile_shift = tile_shift;
+        ra.ntiles = F.tiles;
+        ra.ranges = w.ranges.as<uint2>();
+        ra.ctr = ctr;
+        launch_ranges(ra, st);
+    }
     if (ev) RG_CK(cudaEventRecord(E[5], st));
     w.last_mode = mode;
     w.last_passes = sa.passes;
@@ -395,6 +400,10 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         launch_raster_exact(r, st);
     } else {
         r.rec = w.rec.as<float4>();
+        r.skeys = w.keys[fin].as<unsigned>();
+        r.tile_shift = tile_shift;
+        r.ranges_out = w.ranges.as<uint2>();
+        r.ctr = ctr;
         r.fast_exp = (flags & RG_FLAG_EXACT_EXP) ? 0 : 1;
         r.ppt = (flags & RG_FLAG_SINGLE_PIXEL) ? 1 : ((flags & RG_FLAG_QUAD_PIXEL) ? 4 : 2);
         launch_raster_roofgs(r, st);

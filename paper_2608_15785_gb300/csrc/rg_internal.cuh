@@ -427,6 +427,13 @@ void launch_ranges(const RangeArgs& a, cudaStream_t s);
 
 struct RasterArgs {
     const uint2* ranges;
+    // RoofGS: when set, every tile block finds its own [start, end) in the sorted keys
+    // (tile id = key >> tile_shift, n_entries from the counters) and writes it to
+    // ranges_out; `ranges` is then unused
+    const unsigned* skeys;
+    int tile_shift;
+    uint2* ranges_out;
+    const Counters* ctr;  // frame counters (n_entries) for the search
     const unsigned* vals;
     long long n;          // Gaussians (values are indices below n)
     int tiles_x, tiles_y;
