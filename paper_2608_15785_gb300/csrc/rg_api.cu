@@ -342,6 +342,9 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
             ga.key_bytes = 4;
             ga.passes = (F.lay.b_d + 7) / 8;
             ga.bit0 = 0;
+            // Gaussians in index order carry scattered low depth digits: rank the first pass
+            // with ballots (measured 8 % faster on the 3 M-Gaussian depth keys)
+            ga.ballot_mask = 1;
             ga.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + CTRL_BYTES + sizeof(Counters));
             ga.max_tiles = (n + sort_tile_items() - 1) / sort_tile_items();
             ga.ctr = gctr;

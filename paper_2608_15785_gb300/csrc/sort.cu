@@ -30,9 +30,6 @@ struct SortCfg;
 #define RG_SORT_K32 16
 #define RG_SORT_B32 2
 #endif
-#ifndef RG_SORT_VLATE
-#define RG_SORT_VLATE 0
-#endif
 template <>
 struct SortCfg<unsigned> {
     static constexpr int THREADS = RG_SORT_T32, KPT = RG_SORT_K32, MIN_BLOCKS = RG_SORT_B32;
@@ -200,7 +197,7 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             const unsigned e = e0 + 32 * i;
             const bool ok = e < n;
             k[i] = ok ? kin[e] : (K)~(K)0; // padding sorts last (digit 255, after the valid ones)
-            if (!RG_SORT_VLATE) v[i] = ok ? vin[e] : 0u;
+            v[i] = ok ? vin[e] : 0u;
         }
         // stable rank of each element among the warp's elements of the same digit
         // (below 32 * KPT: two ranks share a register)
@@ -264,13 +261,6 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             S.loff[tid] = lo;
         }
         __syncthreads(); // D
-        if (RG_SORT_VLATE) {
-#pragma unroll
-            for (int i = 0; i < S_KPT; i++) {
-                const long long e = e0 + 32 * i;
-                v[i] = e < n ? vin[e] : 0u;
-            }
-        }
         if (tid < RADIX) {
             // windowed decoupled look-back: LB_WINDOW predecessors per round trip,
             // sv[w] holding the status of tile t - w
