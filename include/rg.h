@@ -120,6 +120,11 @@ typedef struct {
 /* flags for both modes */
 #define RG_FLAG_STAGE_EVENTS (1u << 8) /* record per-stage CUDA events (rg_stage_times) */
 #define RG_FLAG_BATCH_CHECKED (1u << 9) /* rg_render_batch: synchronise, and re-size and render again on overflow */
+/* test hook for the failure path: the first radix pass of the entry sort never processes its
+ * first tile, so the next tile's bounded look-back wait runs out (about a second); the frame
+ * is invalid, kernels finish with in-bounds writes only, and the next rg_scene_check (or this
+ * call, given stats) returns RG_ERR_TIMEOUT. The scene renders normally afterwards. */
+#define RG_FLAG_TEST_STALL_SORT (1u << 10)
 
 typedef struct {
     int32_t mode;   /* RG_MODE_EXACT or RG_MODE_ROOFGS */

@@ -29,6 +29,7 @@ RG_FLAG_SORT_FULL_KEY = 1 << 2
 RG_FLAG_QUAD_PIXEL = 1 << 3
 RG_FLAG_STAGE_EVENTS = 1 << 8
 RG_FLAG_BATCH_CHECKED = 1 << 9
+RG_FLAG_TEST_STALL_SORT = 1 << 10
 RG_INSPECT_KEYS = 1
 RG_INSPECT_VALUES = 2
 RG_INSPECT_RANGES = 3

@@ -188,6 +188,9 @@ rg_status make_layout(const rg_camera* c, FrameLayout& f)
     return RG_OK;
 }
 
+// one device word set from the stream (test hook of RG_FLAG_TEST_STALL_SORT)
+__global__ void k_set_word(unsigned* p, unsigned v) { *p = v; }
+
 rg_status ensure_workspace(Workspace& w, int64_t n_gauss, int mode, int tiles, int64_t cap)
 {
     const int64_t n = n_gauss > 0 ? n_gauss : 1;
@@ -252,6 +255,10 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     // the sorted keys per tile block); the others run the ranges pass
     const bool search_ranges = mode == RG_MODE_ROOFGS && out != nullptr;
     RG_CK(cudaMemsetAsync(w.ctrl.p, 0, CTRL_ALLOC, st));
+    if (flags & RG_FLAG_TEST_STALL_SORT) { // tile 0 of the first entry-sort pass is never claimed
+        k_set_word<<<1, 1, 0, st>>>(&ctr->sort_tile_ctr[0], 1u);
+        RG_CK(cudaGetLastError());
+    }
     if (!search_ranges) RG_CK(cudaMemsetAsync(w.ranges.p, 0, (size_t)F.tiles * sizeof(uint2), st));
     const long long n = s->n;
     SortArgs sa;

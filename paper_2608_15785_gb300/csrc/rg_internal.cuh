@@ -9,7 +9,7 @@ namespace rg {
 
 constexpr int TILE = 16;                       // tile edge in pixels (16 x 16 tiles)
 constexpr float LN255F = 5.541263545158426f;   // ln 255: alpha = 1/255 in log space, Eq. (23)
-constexpr unsigned SPIN_LIMIT = 1u << 22;      // bounded device waits (x ~64 ns sleep)
+constexpr unsigned SPIN_LIMIT = 1u << 20;      // bounded device waits: ~1 s of polls with a short sleep
 
 // Error bits of Counters::error / Sticky::error
 constexpr unsigned ERR_FE_LOOKBACK = 1u;

@@ -197,6 +197,23 @@ def test_timed_launch_equals_counting_launch(flags):
             assert a.std() > 0
 
 
+def test_outputs_are_finite_and_in_range():
+    """NaN/Inf scan of the images of every mode and ingredient, on close, far and thin views."""
+    sc = synth.clustered_scene(200_000, seed=3)
+    gs = gpu_scene(sc)
+    cams = [synth.orbit_camera(k, 640, 360, radius=r) for k, r in ((0, 4.0), (5, 1.2), (9, 30.0))]
+    flag_sets = [0, binding.RG_FLAG_EXACT_EXP, binding.RG_FLAG_SINGLE_PIXEL, binding.RG_FLAG_QUAD_PIXEL,
+                 binding.RG_FLAG_SORT_FULL_KEY]
+    for cam in cams:
+        for mode in ("exact", "roofgs"):
+            for fl in (flag_sets if mode == "roofgs" else [0]):
+                img = render(gs, cam, mode, flags=fl)
+                assert np.isfinite(img).all(), (mode, fl)
+                # colours in [0, 1] blended with weights summing to 1 - T, plus T bg
+                assert img.min() >= -1e-6 and img.max() <= 1.0 + 1e-5, (mode, fl, img.min(), img.max())
+    gs.check()
+
+
 def test_roofgs_psnr_against_exact_tiny(tiny):
     sc, cam, gs, _ = tiny
     a = render(gs, cam, "exact")
