@@ -161,6 +161,18 @@ rg_status rg_scene_create(const rg_scene_desc* desc, void* stream, rg_scene** ou
 /* Free every device buffer of the scene (synchronises the device). NULL is a no-op. */
 rg_status rg_scene_destroy(rg_scene* scene);
 
+/*
+ * Scene files (checkpoint / resume of a resident scene; the paper has no counterpart):
+ * rg_scene_save writes the scene's stored buffers (the FP32 attributes and/or the compact
+ * attributes with their 12 band scales) to `path` after a fixed header, raw little-endian;
+ * rg_scene_load creates a scene from such a file on the current device without re-encoding,
+ * so it renders bit-identically to the saved one. Both synchronise (the device / `stream`).
+ * Errors: RG_ERR_INVALID_ARG (NULL argument, a file that cannot be opened, written or read,
+ * or whose magic, version, fields or size do not match), RG_ERR_OOM, RG_ERR_CUDA.
+ */
+rg_status rg_scene_save(rg_scene* scene, const char* path);
+rg_status rg_scene_load(const char* path, void* stream, rg_scene** out);
+
 /* Grow the frame workspace to hold at least n_entries (tile, Gaussian) entries. Synchronous. */
 rg_status rg_scene_reserve(rg_scene* scene, int64_t n_entries);
 

@@ -43,7 +43,8 @@ RG_INSPECT_LOG_OPACITY = 8
 EXPORTS = ["rg_scene_create", "rg_scene_destroy", "rg_scene_reserve", "rg_render", "rg_scene_check",
            "rg_stage_times", "rg_inspect", "rg_eval_fast_exp", "rg_render_batch", "rg_backward", "rg_submit",
            "rg_poll", "rg_last_error", "rg_version", "rg_sort_pairs_noalloc", "rg_batch_plan_info",
-           "rg_server_create", "rg_server_destroy", "rg_server_stats", "rg_server_reset_stats"]
+           "rg_server_create", "rg_server_destroy", "rg_server_stats", "rg_server_reset_stats", "rg_scene_save",
+           "rg_scene_load"]
 
 
 class RgError(RuntimeError):
@@ -198,6 +199,21 @@ class Scene:
     @property
     def handle(self):
         return self._h
+
+    def save(self, path: str):
+        """Write the scene's stored buffers to a file (rg_scene_save)."""
+        check(lib().rg_scene_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Scene":
+        """A resident scene from a file written by save() (rg_scene_load), no re-encoding."""
+        h = C.c_void_p()
+        check(lib().rg_scene_load(os.fsencode(path), _stream_ptr(stream), C.byref(h)))
+        obj = cls.__new__(cls)
+        obj._h = h
+        with open(path, "rb") as f:  # header: magic[8], version u32, storage u32, n i64, ...
+            obj.n = int(np.frombuffer(f.read(24)[16:24], dtype="<i8")[0])
+        return obj
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

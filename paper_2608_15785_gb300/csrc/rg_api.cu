@@ -925,6 +925,150 @@ rg_status rg_scene_reserve(rg_scene* scene, int64_t n_entries)
     return RG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Scene files: a fixed header, then the stored buffers in a fixed order (FP32 means,
+// scales, quats, opacities, SH if RG_STORE_FP32; compact geoA, geoB, SH codes if
+// RG_STORE_COMPACT), raw little-endian, so a load needs no re-encoding.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SceneFileHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t storage;
+    int64_t n;
+    int32_t sh_degree;
+    int32_t sh_scale_mode;
+    float band_scale[12];
+    uint64_t reserved[4];
+};
+constexpr char SCENE_MAGIC[8] = {'R', 'G', 'S', 'C', 'E', 'N', 'E', '1'};
+constexpr uint32_t SCENE_VERSION = 1;
+
+// (buffer, bytes) of a scene in file order
+std::vector<std::pair<DevBuf*, size_t>> scene_buffers(rg_scene* s)
+{
+    std::vector<std::pair<DevBuf*, size_t>> v;
+    const size_t n = (size_t)s->n;
+    if (s->storage & RG_STORE_FP32) {
+        v.push_back({&s->means, n * 12});
+        v.push_back({&s->scales, n * 12});
+        v.push_back({&s->quats, n * 16});
+        v.push_back({&s->opac, n * 4});
+        v.push_back({&s->sh, n * 192});
+    }
+    if (s->storage & RG_STORE_COMPACT) {
+        v.push_back({&s->geoA, n * 16});
+        v.push_back({&s->geoB, n * 16});
+        v.push_back({&s->shq, n * 48});
+    }
+    return v;
+}
+
+constexpr size_t IO_CHUNK = 64u << 20;
+
+} // namespace
+
+rg_status rg_scene_save(rg_scene* s, const char* path)
+{
+    if (!s || !path) return fail(RG_ERR_INVALID_ARG, "NULL argument");
+    RG_CK(cudaDeviceSynchronize());
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(RG_ERR_INVALID_ARG, std::string("cannot open for writing: ") + path);
+    SceneFileHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, SCENE_MAGIC, 8);
+    h.version = SCENE_VERSION;
+    h.storage = s->storage;
+    h.n = s->n;
+    h.sh_degree = s->sh_degree;
+    h.sh_scale_mode = s->sh_scale_mode;
+    memcpy(h.band_scale, s->band_scale, sizeof(h.band_scale));
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+    std::vector<unsigned char> buf;
+    for (auto& b : scene_buffers(s)) {
+        for (size_t off = 0; ok && off < b.second; off += IO_CHUNK) {
+            const size_t len = std::min(IO_CHUNK, b.second - off);
+            buf.resize(len);
+            if (cudaMemcpy(buf.data(), b.first->as<unsigned char>() + off, len, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                std::fclose(f);
+                return fail(RG_ERR_CUDA, "copy of scene buffer to host failed");
+            }
+            ok = std::fwrite(buf.data(), 1, len, f) == len;
+        }
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(RG_ERR_INVALID_ARG, std::string("write failed: ") + path);
+    return RG_OK;
+}
+
+rg_status rg_scene_load(const char* path, void* stream, rg_scene** out)
+{
+    if (!out) return fail(RG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!path) return fail(RG_ERR_INVALID_ARG, "path is NULL");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(RG_ERR_INVALID_ARG, std::string("cannot open: ") + path);
+    SceneFileHeader h;
+    auto bad = [&](const char* why) {
+        std::fclose(f);
+        return fail(RG_ERR_INVALID_ARG, std::string("not a valid scene file (") + why + "): " + path);
+    };
+    if (std::fread(&h, sizeof(h), 1, f) != 1) return bad("short header");
+    if (memcmp(h.magic, SCENE_MAGIC, 8) != 0) return bad("magic");
+    if (h.version != SCENE_VERSION) return bad("version");
+    if (h.n < 0 || h.n > (1ll << 31)) return bad("n");
+    if (h.sh_degree < 0 || h.sh_degree > 3) return bad("sh_degree");
+    if (h.sh_scale_mode != RG_SH_SCALE_BAND && h.sh_scale_mode != RG_SH_SCALE_BAND_GAUSS) return bad("sh_scale_mode");
+    if (h.storage == 0 || (h.storage & ~(RG_STORE_FP32 | RG_STORE_COMPACT))) return bad("storage");
+    for (int k = 0; k < 12; k++)
+        if (!std::isfinite(h.band_scale[k])) return bad("band scales");
+    {
+        const size_t n = (size_t)h.n;
+        size_t want = sizeof(h);
+        if (h.storage & RG_STORE_FP32) want += n * (12 + 12 + 16 + 4 + 192);
+        if (h.storage & RG_STORE_COMPACT) want += n * (16 + 16 + 48);
+        if (std::fseek(f, 0, SEEK_END) != 0 || (size_t)std::ftell(f) != want) return bad("size");
+        std::fseek(f, (long)sizeof(h), SEEK_SET);
+    }
+    rg_scene* s = new rg_scene();
+    cudaGetDevice(&s->device);
+    s->n = h.n;
+    s->sh_degree = h.sh_degree;
+    s->storage = h.storage;
+    s->sh_scale_mode = h.sh_scale_mode;
+    memcpy(s->band_scale, h.band_scale, sizeof(h.band_scale));
+    auto bufs = scene_buffers(s);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<unsigned char> buf;
+    rg_status e = ensure(s->sticky, sizeof(Sticky), "sticky");
+    if (e == RG_OK && cudaMemsetAsync(s->sticky.p, 0, sizeof(Sticky), st) != cudaSuccess) e = fail(RG_ERR_CUDA, "memset");
+    for (auto& b : bufs) {
+        if (e != RG_OK) break;
+        e = ensure(*b.first, b.second ? b.second : 16, "scene buffer");
+        for (size_t off = 0; e == RG_OK && off < b.second; off += IO_CHUNK) {
+            const size_t len = std::min(IO_CHUNK, b.second - off);
+            buf.resize(len);
+            if (std::fread(buf.data(), 1, len, f) != len) {
+                e = fail(RG_ERR_INVALID_ARG, std::string("short read: ") + path);
+                break;
+            }
+            if (cudaMemcpyAsync(b.first->as<unsigned char>() + off, buf.data(), len, cudaMemcpyHostToDevice, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                e = fail(RG_ERR_CUDA, "copy of scene buffer to the device failed");
+        }
+    }
+    std::fclose(f);
+    if (e != RG_OK) {
+        cudaStreamSynchronize(st);
+        destroy_scene(s);
+        return e;
+    }
+    *out = s;
+    return RG_OK;
+}
+
 rg_status rg_render(rg_scene* s, const rg_camera* cam, const rg_render_opts* opts, float* out_chw, rg_stats* stats,
                     void* stream)
 {

@@ -70,6 +70,25 @@ def test_bad_arguments_are_rejected_without_a_gpu(L):
     assert L.rg_scene_destroy(None) == 0
 
 
+def test_scene_files_are_validated_before_touching_a_gpu(L, tmp_path):
+    import struct
+    out = C.c_void_p()
+    assert L.rg_scene_save(None, b"x") == 1
+    assert L.rg_scene_load(None, None, C.byref(out)) == 1
+    assert L.rg_scene_load(str(tmp_path / "missing.rgs").encode(), None, C.byref(out)) == 1
+    junk = tmp_path / "junk.rgs"
+    junk.write_bytes(b"not a scene file at all" * 10)
+    assert L.rg_scene_load(str(junk).encode(), None, C.byref(out)) == 1
+    assert b"magic" in L.rg_last_error()
+    # a valid header (n = 10, compact storage) whose buffers are missing
+    hdr = b"RGSCENE1" + struct.pack("<IIqii", 1, 2, 10, 3, 0) + struct.pack("<12f", *([0.1] * 12)) + bytes(32)
+    short = tmp_path / "short.rgs"
+    short.write_bytes(hdr + bytes(100))
+    assert L.rg_scene_load(str(short).encode(), None, C.byref(out)) == 1
+    assert b"size" in L.rg_last_error()
+    assert not out.value
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """ctypes mirrors of the public structs have the C compiler's sizes and offsets."""
     import subprocess
