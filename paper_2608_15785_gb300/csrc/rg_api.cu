@@ -10,6 +10,8 @@
 #include <thread>
 #include <cstdio>
 #include <cstring>
+
+#include <nvtx3/nvToolsExt.h>
 #include <string>
 #include <vector>
 
@@ -235,6 +237,15 @@ void init_events(Workspace& w)
     w.ev_init = true;
 }
 
+// NVTX range around a stage's launches (host side; costs nothing without a tool attached),
+// e.g. for `ncu --nvtx --nvtx-include "rg raster/"`
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
 // One frame on `st`; the caller has checked arguments and the workspace.
 rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode, uint32_t flags, float* out,
                       cudaStream_t st, bool count = false)
@@ -301,9 +312,12 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         a.sticky = sticky;
         RG_CK(cudaMemsetAsync(w.lb_status.p, 0, (size_t)((n + 2047) / 2048 + 1) * 8, st));
         if (ev) RG_CK(cudaEventRecord(E[1], st));
-        launch_exact_preprocess(a, st);
-        launch_exact_scan(a, st);
-        launch_exact_duplicate(a, st);
+        {
+            NvtxScope r_("rg front end");
+            launch_exact_preprocess(a, st);
+            launch_exact_scan(a, st);
+            launch_exact_duplicate(a, st);
+        }
         sa.key_bytes = 8;
         sa.passes = (32 + F.lay.b_t + 7) / 8; // only the bits that can be non-zero
         tile_shift = 32;
@@ -356,8 +370,11 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
             ga.max_tiles = (n + sort_tile_items() - 1) / sort_tile_items();
             ga.ctr = gctr;
             ga.sticky = sticky;
-            launch_depth_keys(a, w.gkeys[0].as<unsigned>(), w.gvals[0].as<unsigned>(), gctr, st);
-            launch_sort(ga, st, nullptr);
+            {
+                NvtxScope r_("rg depth order");
+                launch_depth_keys(a, w.gkeys[0].as<unsigned>(), w.gvals[0].as<unsigned>(), gctr, st);
+                launch_sort(ga, st, nullptr);
+            }
             a.order = w.gvals[ga.passes & 1].as<unsigned>();
             if (ev) RG_CK(cudaEventRecord(E[1], st));
             sa.passes = (F.lay.b_t + 7) / 8;
@@ -366,12 +383,18 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
             // holds many distinct low tile digits: rank that pass with ballots
             sa.ballot_mask = 1;
         }
-        launch_frontend_fused(a, st);
+        {
+            NvtxScope r_("rg front end");
+            launch_frontend_fused(a, st);
+        }
         tile_shift = F.lay.b_d;
     }
     if (ev) RG_CK(cudaEventRecord(E[2], st));
     if (ev && sa.passes <= 0) RG_CK(cudaEventRecord(E[3], st));
-    launch_sort(sa, st, ev ? E[3] : nullptr);
+    {
+        NvtxScope r_("rg sort");
+        launch_sort(sa, st, ev ? E[3] : nullptr);
+    }
     if (ev) RG_CK(cudaEventRecord(E[4], st));
     const int fin = sa.passes & 1;
     if (!search_ranges) {
@@ -382,6 +405,7 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         ra.ntiles = F.tiles;
         ra.ranges = w.ranges.as<uint2>();
         ra.ctr = ctr;
+        NvtxScope r_("rg ranges");
         launch_ranges(ra, st);
     }
     if (ev) RG_CK(cudaEventRecord(E[5], st));
@@ -407,6 +431,7 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         r.xy = w.xy.as<float2>();
         r.conic_op = w.conic.as<float4>();
         r.rgb = w.rgb.as<float>();
+        NvtxScope r_("rg raster");
         launch_raster_exact(r, st);
     } else {
         r.rec = w.rec.as<float4>();
@@ -416,6 +441,7 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         r.ctr = ctr;
         r.fast_exp = (flags & RG_FLAG_EXACT_EXP) ? 0 : 1;
         r.ppt = (flags & RG_FLAG_SINGLE_PIXEL) ? 1 : ((flags & RG_FLAG_QUAD_PIXEL) ? 4 : 2);
+        NvtxScope r_("rg raster");
         launch_raster_roofgs(r, st);
     }
     if (ev) RG_CK(cudaEventRecord(E[6], st));
