@@ -393,3 +393,30 @@ def test_full_size_parity(name, per_gauss):
     assert psnr(a, b) >= 46.4, psnr(a, b)
     b4 = render(gs, cam, "roofgs", flags=binding.RG_FLAG_QUAD_PIXEL)
     assert psnr(a, b4) >= 46.4, psnr(a, b4)
+
+
+def test_8k_three_tile_bit_passes_and_seven_exact_passes():
+    """7680x4320: 129,600 tiles, so b_t = 17 and b_d = 15 (Eq. (9)); the RoofGS tile-bit sort
+    takes 3 passes and the exact 64-bit sort 7. Keys bit-exact, sampled tiles against the oracle."""
+    cam = synth.orbit_camera(4, 7680, 4320)
+    lay = oracle.layout(cam)
+    assert (lay["b_t"], lay["b_d"]) == (17, 15)
+    tiles = _sample_tiles(lay, 32, seed=3)
+    mask = _tile_mask(cam, tiles)
+    for mode, om, n in (("roofgs", oracle.ROOFGS, 300_000), ("exact", oracle.EXACT, 100_000)):
+        sc = synth.clustered_scene(n, seed=6)
+        gs = gpu_scene(sc, per_gauss=True)
+        comp = oracle.compact(sc, True) if mode == "roofgs" else None
+        img, st = render(gs, cam, mode, stats=True)
+        assert st["sort_passes"] == (3 if mode == "roofgs" else 7)
+        assert st["n_entries"] == _keys_equal(gs, sc, cam, om, comp)
+        kind = oracle.EXP_FAST32 if mode == "roofgs" else oracle.EXP_EXACT
+        ref, diag, _ = oracle.render(sc, cam, om, comp=comp, exp_kind=kind, tiles=tiles)
+        base = TOL + (HALF_COLOUR if mode == "roofgs" else 0.0)
+        tol = base + allowance(diag)
+        images = [img] if mode == "exact" else [img, render(gs, cam, mode, flags=binding.RG_FLAG_QUAD_PIXEL)]
+        for im in images:
+            err = np.abs(im - ref)[:, mask]
+            assert (err <= tol[mask][None]).all(), (mode, float((err - tol[mask][None]).max()))
+            assert float(np.mean((err > base).any(axis=0))) <= 0.02
+        gs.check()

@@ -33,7 +33,8 @@ def test_layout_worked_example():
     assert lay["qmax"] + 1 == g["levels"]
 
 
-@pytest.mark.parametrize("w,h,tiles", [(16, 16, 1), (17, 16, 2), (32, 32, 4), (48, 16, 3), (3840, 2160, 32400)])
+@pytest.mark.parametrize("w,h,tiles", [(16, 16, 1), (17, 16, 2), (32, 32, 4), (48, 16, 3), (3840, 2160, 32400),
+                                       (7680, 4320, 129600)])
 def test_layout_bit_split_is_ceil_log2(w, h, tiles):
     cam = synth.look_at_camera((0, 0, -4), w, h)
     lay = oracle.layout(cam)
