@@ -374,7 +374,7 @@ def run_batch(a, sc3, gs3, dev):
         for v, c in enumerate(cams(r)):
             scenes[idx[v]].render(c, mode="roofgs", stats=True)
     torch.cuda.synchronize(dev)
-    lanes, ppt = binding.batch_plan_info(scenes, idx, cams(0), mode="roofgs")
+    lanes, ppt, tw, th = binding.batch_plan_info(scenes, idx, cams(0), mode="roofgs")
     outs = [torch.empty((3, h, w), device=dev) for (w, h) in [sizes[v % 4] for v in range(32)]]
     reps = 6
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -400,7 +400,7 @@ def run_batch(a, sc3, gs3, dev):
                         "8 each of 1280x720, 1920x1080, 2560x1440, 3840x2160; RoofGS mode",
             "views_per_s": round(32 / (batch_ms * 1e-3), 1), "ms_per_batch": round(batch_ms, 3),
             "sequential_views_per_s": round(32 / (seq_ms * 1e-3), 1), "speedup_vs_sequential": round(seq_ms / batch_ms, 3),
-            "autotuned": {"lanes": lanes, "pixels_per_thread": ppt}, "plan_seconds": round(plan_s, 2)}
+            "autotuned": {"lanes": lanes, "pixels_per_thread": ppt, "tile": [tw, th]}, "plan_seconds": round(plan_s, 2)}
 
 
 def run_backward(dev):

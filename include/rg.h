@@ -129,8 +129,8 @@ typedef struct {
 typedef struct {
     int32_t mode;   /* RG_MODE_EXACT or RG_MODE_ROOFGS */
     uint32_t flags; /* RG_FLAG_* */
-    int32_t tile_w; /* tile shape; 16 x 16 (0 = default 16) */
-    int32_t tile_h;
+    int32_t tile_w; /* tile shape in pixels: 16 x 16 (0 x 0 = default), 32 x 8 or 8 x 32; others */
+    int32_t tile_h; /* return RG_ERR_UNSUPPORTED. rg_render_batch: 0 x 0 = autotuned */
 } rg_render_opts;
 
 /* Frame statistics (filled only when rg_render is given a non-NULL stats pointer). */
@@ -295,8 +295,9 @@ rg_status rg_backward(rg_scene* scene, const rg_camera* cam, const rg_render_opt
  * rendered from scenes[scene_idx[v]] with cams[v] (any resolution) into outs[v]
  * (device [3][H][W], caller-owned), all in opts->mode. The first call for a set of
  * (scenes, resolutions, mode, flags) creates a plan: lanes of stream + workspace,
- * sized by rendering every view once (synchronous), then an autotuner times the
- * captured batch with 1, 2 and 4 lanes and with 1 or 2 pixels per thread (RoofGS)
+ * sized by rendering every view once per candidate tile shape (synchronous), then an
+ * autotuner times the captured batch with every tile shape (16 x 16, 32 x 8, 8 x 32,
+ * unless opts gives one), 1, 2 and 4 lanes and 1, 2 and 4 pixels per thread (RoofGS)
  * and keeps the fastest. Every call captures each view's pipeline on its lane
  * (view v on lane v mod lanes) into one CUDA graph, updates the plan's instantiated
  * graph in place (cameras are kernel parameters) and launches it once on `stream`:
@@ -305,14 +306,16 @@ rg_status rg_backward(rg_scene* scene, const rg_camera* cam, const rg_render_opt
  * (rg_scene_check), as for rg_render without stats. Views of one lane run in
  * order; lanes run concurrently, so scenes may repeat across views freely.
  * A plan keeps its workspaces until one of its scenes is destroyed (at most 8
- * plans are kept). Tile shape is fixed (16x16).
+ * plans are kept).
  */
 rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
                           const rg_render_opts* opts, float* const* outs, void* stream);
 
-/* The autotuned lane count and pixels per thread of the plan for these views (0, 0 if none). */
+/* The autotuned lane count, pixels per thread and tile shape of the plan for these views
+ * (lanes 0 if no plan exists yet); tile_w and tile_h may be NULL. */
 rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
-                             const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread);
+                             const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread, int32_t* tile_w,
+                             int32_t* tile_h);
 
 /*
  * Request loop (serving; not in the paper). A server keeps its scenes resident and

@@ -226,19 +226,20 @@ class Scene:
         except Exception:
             pass
 
-    def render(self, cam, mode="roofgs", flags: int = 0, out=None, stats: bool = False, stream=None):
-        """Render one view; returns a [3, H, W] float32 CUDA tensor (and stats if asked)."""
+    def render(self, cam, mode="roofgs", flags: int = 0, out=None, stats: bool = False, stream=None, tile=(16, 16)):
+        """Render one view; returns a [3, H, W] float32 CUDA tensor (and stats if asked).
+        tile: (16, 16), (32, 8) or (8, 32) pixels."""
         import torch
         c = camera_struct(cam)
         if out is None:
             out = torch.empty((3, c.height, c.width), dtype=torch.float32, device="cuda")
-        o = RgOpts(_mode(mode), int(flags), 16, 16)
+        o = RgOpts(_mode(mode), int(flags), int(tile[0]), int(tile[1]))
         st = RgStats() if stats else None
         check(lib().rg_render(self._h, C.byref(c), C.byref(o), C.c_void_p(out.data_ptr()),
                               C.byref(st) if st is not None else None, _stream_ptr(stream)))
         return (out, st.as_dict()) if stats else out
 
-    def backward(self, cam, dL_dimg, stream=None) -> dict:
+    def backward(self, cam, dL_dimg, stream=None, tile=(16, 16)) -> dict:
         """Gradients of L w.r.t. the FP32 attributes, given dL/dimage of the exact-mode render."""
         import torch
         g = {"means": torch.empty((self.n, 3), device="cuda"), "scales": torch.empty((self.n, 3), device="cuda"),
@@ -246,7 +247,7 @@ class Scene:
              "sh": torch.empty((self.n, 16, 3), device="cuda")}
         gg = RgGrads(*(g[k].data_ptr() for k in ("means", "scales", "quats", "opacities", "sh")))
         c = camera_struct(cam)
-        o = RgOpts(RG_MODE_EXACT, 0, 16, 16)
+        o = RgOpts(RG_MODE_EXACT, 0, int(tile[0]), int(tile[1]))
         d = dL_dimg.contiguous().float()
         check(lib().rg_backward(self._h, C.byref(c), C.byref(o), C.c_void_p(d.data_ptr()), C.byref(gg),
                                 _stream_ptr(stream)))
@@ -275,8 +276,9 @@ class Scene:
         return buf.view(dtype)
 
 
-def render_batch(scenes, scene_idx, cams, mode="roofgs", flags: int = 0, outs=None, stream=None):
-    """Render many views in one captured graph (rg_render_batch); returns the list of [3, H, W] tensors."""
+def render_batch(scenes, scene_idx, cams, mode="roofgs", flags: int = 0, outs=None, stream=None, tile=(0, 0)):
+    """Render many views in one captured graph (rg_render_batch); returns the list of [3, H, W] tensors.
+    tile (0, 0): the plan's autotuner picks the tile shape."""
     import torch
     n = len(cams)
     if outs is None:
@@ -285,20 +287,21 @@ def render_batch(scenes, scene_idx, cams, mode="roofgs", flags: int = 0, outs=No
     idx = (C.c_int32 * n)(*[int(i) for i in scene_idx])
     cs = (RgCamera * n)(*[camera_struct(c) for c in cams])
     ptrs = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
-    o = RgOpts(_mode(mode), int(flags), 16, 16)
+    o = RgOpts(_mode(mode), int(flags), int(tile[0]), int(tile[1]))
     check(lib().rg_render_batch(hs, idx, cs, n, C.byref(o), ptrs, _stream_ptr(stream)))
     return outs
 
 
-def batch_plan_info(scenes, scene_idx, cams, mode="roofgs", flags: int = 0):
+def batch_plan_info(scenes, scene_idx, cams, mode="roofgs", flags: int = 0, tile=(0, 0)):
+    """(lanes, pixels per thread, tile width, tile height) the plan of these views uses."""
     n = len(cams)
     hs = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
     idx = (C.c_int32 * n)(*[int(i) for i in scene_idx])
     cs = (RgCamera * n)(*[camera_struct(c) for c in cams])
-    o = RgOpts(_mode(mode), int(flags), 16, 16)
-    lanes, ppt = C.c_int32(), C.c_int32()
-    check(lib().rg_batch_plan_info(hs, idx, cs, n, C.byref(o), C.byref(lanes), C.byref(ppt)))
-    return lanes.value, ppt.value
+    o = RgOpts(_mode(mode), int(flags), int(tile[0]), int(tile[1]))
+    lanes, ppt, tw, th = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    check(lib().rg_batch_plan_info(hs, idx, cs, n, C.byref(o), C.byref(lanes), C.byref(ppt), C.byref(tw), C.byref(th)))
+    return lanes.value, ppt.value, tw.value, th.value
 
 
 class Server:

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(B_THREADS) k_raster_backward(BackwardArgs a)
     __shared__ int s_last;
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * TILE + (threadIdx.x & 15), py = ty * TILE + (threadIdx.x >> 4);
+    const int px = tx * a.cam.tw + (threadIdx.x & (a.cam.tw - 1)), py = ty * a.cam.th + (threadIdx.x >> a.cam.tw_log2);
     const int W = a.cam.W, H = a.cam.H;
     const bool inside = px < W && py < H;
     const float fx = (float)px, fy = (float)py;

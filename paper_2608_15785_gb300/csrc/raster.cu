@@ -102,17 +102,17 @@ __device__ __forceinline__ unsigned warp_lower_bound(const unsigned* __restrict_
 template <bool FAST, int PPT, bool COUNT>
 __global__ void __launch_bounds__(256 / PPT) k_raster_roofgs(RasterArgs a)
 {
-    constexpr int NT = 256 / PPT; // threads per 16x16 tile
+    constexpr int NT = 256 / PPT; // threads per tile of 256 pixels (16 x 16, 32 x 8 or 8 x 32)
     __shared__ float4 s_c0[NT];
     __shared__ float4 s_c1[NT];
     __shared__ float s_cb[NT];
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int x0 = tx * TILE, y0 = ty * TILE;
+    const int x0 = tx * a.cam.tw, y0 = ty * a.cam.th;
     const int t = threadIdx.x;
     // the thread's pixels: (x, y), (x, y+1), ..., (x, y+PPT-1)
-    const int lx = t & 15;
-    const int ly = (t >> 4) * PPT;
+    const int lx = t & (a.cam.tw - 1);
+    const int ly = (t >> a.cam.tw_log2) * PPT;
     const int px = x0 + lx, py = y0 + ly;
     const int W = a.cam.W, H = a.cam.H;
     bool done[PPT];
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(E_THREADS) k_raster_exact(RasterArgs a)
     __shared__ float4 s_rgb[E_THREADS];
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * TILE + (threadIdx.x & 15), py = ty * TILE + (threadIdx.x >> 4);
+    const int px = tx * a.cam.tw + (threadIdx.x & (a.cam.tw - 1)), py = ty * a.cam.th + (threadIdx.x >> a.cam.tw_log2);
     const int W = a.cam.W, H = a.cam.H;
     const bool inside = px < W && py < H;
     bool done = !inside;

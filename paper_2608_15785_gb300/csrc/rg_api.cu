@@ -142,8 +142,21 @@ struct FrameLayout {
     int tiles;
 };
 
-rg_status make_layout(const rg_camera* c, FrameLayout& f)
+// Tile shapes with kernels: 256 pixels each, width a power of two.
+bool tile_shape_ok(int tw, int th) { return (tw == 16 && th == 16) || (tw == 32 && th == 8) || (tw == 8 && th == 32); }
+
+// tile shape of a render option block (0 = the default 16 x 16)
+rg_status tile_shape(const rg_render_opts* o, int& tw, int& th)
 {
+    tw = o->tile_w ? o->tile_w : TILE;
+    th = o->tile_h ? o->tile_h : TILE;
+    if (!tile_shape_ok(tw, th)) return fail(RG_ERR_UNSUPPORTED, "tile shapes built: 16x16, 32x8, 8x32");
+    return RG_OK;
+}
+
+rg_status make_layout(const rg_camera* c, FrameLayout& f, int tw = TILE, int th = TILE)
+{
+    if (!tile_shape_ok(tw, th)) return fail(RG_ERR_UNSUPPORTED, "tile shapes built: 16x16, 32x8, 8x32");
     if (!c) return fail(RG_ERR_INVALID_ARG, "camera is NULL");
     if (c->width <= 0 || c->height <= 0) return fail(RG_ERR_INVALID_ARG, "camera width/height must be positive");
     if (!(c->znear > 0.0f) || !(c->zfar > c->znear) || !std::isfinite(c->zfar))
@@ -157,8 +170,8 @@ rg_status make_layout(const rg_camera* c, FrameLayout& f)
         !std::isfinite(c->cx) || !std::isfinite(c->cy))
         return fail(RG_ERR_INVALID_ARG, "camera intrinsics must be finite with fx, fy > 0");
     Layout& L = f.lay;
-    L.tiles_x = (c->width + TILE - 1) / TILE;
-    L.tiles_y = (c->height + TILE - 1) / TILE;
+    L.tiles_x = (c->width + tw - 1) / tw;
+    L.tiles_y = (c->height + th - 1) / th;
     const long long nt = (long long)L.tiles_x * L.tiles_y;
     if (nt > (1ll << 26)) return fail(RG_ERR_INVALID_ARG, "image too large");
     int b = 0;
@@ -187,6 +200,9 @@ rg_status make_layout(const rg_camera* c, FrameLayout& f)
     volatile float tx = halfw / c->fx, ty = halfh / c->fy;
     d.limx = 1.3f * tx;
     d.limy = 1.3f * ty;
+    d.tw = tw;
+    d.th = th;
+    d.tw_log2 = tw == 32 ? 5 : (tw == 16 ? 4 : 3);
     return RG_OK;
 }
 
@@ -484,6 +500,8 @@ struct BatchPlan {
     uint32_t flags = 0;
     int lanes = 1;
     uint32_t raster_flags = 0; // autotuned: 0 (two pixels per thread), RG_FLAG_SINGLE_PIXEL or RG_FLAG_QUAD_PIXEL
+    int req_tw = 0, req_th = 0; // requested tile shape (0 x 0: autotuned)
+    int tw = TILE, th = TILE;   // tile shape in use
     bool tuned = false;
     std::unique_ptr<Workspace[]> ws{new Workspace[BATCH_MAX_LANES]};
     cudaStream_t streams[BATCH_MAX_LANES] = {nullptr};
@@ -493,6 +511,7 @@ struct BatchPlan {
     cudaGraphExec_t exec = nullptr;
     int exec_lanes = 0;
     uint32_t exec_raster = 0;
+    int exec_tw = 0;
 
     ~BatchPlan()
     {
@@ -599,7 +618,7 @@ rg_status plan_capture(BatchPlan& P, const std::vector<FrameLayout>& F, float* c
         return fail(RG_ERR_CUDA, std::string("batch capture failed: ") +
                                      cudaGetErrorString(ce != cudaSuccess ? ce : ee));
     }
-    bool fresh = !P.exec || P.exec_lanes != lanes || P.exec_raster != raster_flags;
+    bool fresh = !P.exec || P.exec_lanes != lanes || P.exec_raster != raster_flags || (!F.empty() && P.exec_tw != F[0].cam.tw);
     if (!fresh) {
         cudaGraphExecUpdateResultInfo info;
         if (cudaGraphExecUpdate(P.exec, g, &info) != cudaSuccess) {
@@ -618,49 +637,73 @@ rg_status plan_capture(BatchPlan& P, const std::vector<FrameLayout>& F, float* c
         }
         P.exec_lanes = lanes;
         P.exec_raster = raster_flags;
+        P.exec_tw = F.empty() ? 0 : F[0].cam.tw;
     }
     cudaGraphDestroy(g);
     return RG_OK;
 }
 
-// Pick the lane count and pixels per thread by timing the captured batch.
-rg_status plan_tune(BatchPlan& P, const std::vector<FrameLayout>& F, float* const* outs, cudaStream_t st)
+// layouts of all views for one tile shape
+rg_status layouts_for(const rg_camera* cams, int n, int tw, int th, std::vector<FrameLayout>& F)
 {
-    const int V = (int)F.size();
+    F.resize((size_t)n);
+    for (int v = 0; v < n; v++) RG_TRY(make_layout(&cams[v], F[v], tw, th));
+    return RG_OK;
+}
+
+// candidate tile shapes of a plan
+std::vector<std::pair<int, int>> plan_shapes(const BatchPlan& P)
+{
+    if (P.req_tw) return {{P.req_tw, P.req_th}};
+    return {{16, 16}, {32, 8}, {8, 32}};
+}
+
+// Pick the tile shape, the lane count and the pixels per thread by timing the captured batch.
+rg_status plan_tune(BatchPlan& P, const rg_camera* cams, float* const* outs, cudaStream_t st)
+{
+    const int V = (int)P.scenes.size();
     float best = 1e30f;
-    int best_l = 1;
+    int best_l = 1, best_tw = TILE, best_th = TILE;
     uint32_t best_r = 0;
     cudaEvent_t e0, e1;
     RG_CK(cudaEventCreate(&e0));
     RG_CK(cudaEventCreate(&e1));
-    for (int lanes : {1, 2, 4}) {
-        if (lanes > V && lanes > 1) continue;
-        for (uint32_t r : {0u, (uint32_t)RG_FLAG_SINGLE_PIXEL, (uint32_t)RG_FLAG_QUAD_PIXEL}) {
-            if (P.mode != RG_MODE_ROOFGS && r) continue;
-            rg_status e = plan_capture(P, F, outs, lanes, r);
-            if (e != RG_OK) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return e;
-            }
-            RG_CK(cudaGraphLaunch(P.exec, st)); // warm
-            RG_CK(cudaEventRecord(e0, st));
-            RG_CK(cudaGraphLaunch(P.exec, st));
-            RG_CK(cudaEventRecord(e1, st));
-            RG_CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            RG_CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
-                best_l = lanes;
-                best_r = r;
+    std::vector<FrameLayout> F;
+    rg_status e = RG_OK;
+    for (auto shape : plan_shapes(P)) {
+        e = layouts_for(cams, V, shape.first, shape.second, F);
+        for (int lanes : {1, 2, 4}) {
+            if (e != RG_OK) break;
+            if (lanes > V && lanes > 1) continue;
+            for (uint32_t r : {0u, (uint32_t)RG_FLAG_SINGLE_PIXEL, (uint32_t)RG_FLAG_QUAD_PIXEL}) {
+                if (P.mode != RG_MODE_ROOFGS && r) continue;
+                e = plan_capture(P, F, outs, lanes, r);
+                if (e != RG_OK) break;
+                float ms = 0.f;
+                if (cudaGraphLaunch(P.exec, st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess ||
+                    cudaGraphLaunch(P.exec, st) != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
+                    cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    e = fail(RG_ERR_CUDA, "timing the captured batch failed");
+                    break;
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_l = lanes;
+                    best_r = r;
+                    best_tw = shape.first;
+                    best_th = shape.second;
+                }
             }
         }
+        if (e != RG_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (e != RG_OK) return e;
     P.lanes = best_l;
     P.raster_flags = best_r;
+    P.tw = best_tw;
+    P.th = best_th;
     P.tuned = true;
     return RG_OK;
 }
@@ -1103,14 +1146,14 @@ rg_status rg_render(rg_scene* s, const rg_camera* cam, const rg_render_opts* opt
     if (!out_chw) return fail(RG_ERR_INVALID_ARG, "out is NULL");
     const int mode = opts->mode;
     if (mode != RG_MODE_EXACT && mode != RG_MODE_ROOFGS) return fail(RG_ERR_INVALID_ARG, "unknown mode");
-    const int tw = opts->tile_w ? opts->tile_w : TILE, th = opts->tile_h ? opts->tile_h : TILE;
-    if (tw != TILE || th != TILE) return fail(RG_ERR_UNSUPPORTED, "only 16x16 tiles are built");
+    int tw, th;
+    RG_TRY(tile_shape(opts, tw, th));
     if (mode == RG_MODE_EXACT && !(s->storage & RG_STORE_FP32))
         return fail(RG_ERR_INVALID_ARG, "exact mode needs RG_STORE_FP32");
     if (mode == RG_MODE_ROOFGS && !(s->storage & RG_STORE_COMPACT))
         return fail(RG_ERR_INVALID_ARG, "RoofGS mode needs RG_STORE_COMPACT");
     FrameLayout F;
-    RG_TRY(make_layout(cam, F));
+    RG_TRY(make_layout(cam, F, tw, th));
     cudaStream_t st = (cudaStream_t)stream;
     int64_t cap = s->ws.cap > 0 ? s->ws.cap : std::max<int64_t>(1 << 20, 4 * s->n);
     if (cap > MAX_CAP) cap = MAX_CAP;
@@ -1291,8 +1334,10 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
     if (!scenes || !scene_idx || !cams || !opts || !outs) return fail(RG_ERR_INVALID_ARG, "NULL argument");
     const int mode = opts->mode;
     if (mode != RG_MODE_EXACT && mode != RG_MODE_ROOFGS) return fail(RG_ERR_INVALID_ARG, "unknown mode");
-    const int tw = opts->tile_w ? opts->tile_w : TILE, th = opts->tile_h ? opts->tile_h : TILE;
-    if (tw != TILE || th != TILE) return fail(RG_ERR_UNSUPPORTED, "only 16x16 tiles are built");
+    // tile shape: 0 x 0 lets the autotuner choose among the built shapes
+    const int req_tw = opts->tile_w, req_th = opts->tile_h;
+    if ((req_tw || req_th) && !tile_shape_ok(req_tw, req_th))
+        return fail(RG_ERR_UNSUPPORTED, "tile shapes built: 16x16, 32x8, 8x32 (or 0x0: autotuned)");
     std::vector<FrameLayout> F((size_t)n);
     std::vector<rg_scene*> vs((size_t)n);
     for (int v = 0; v < n; v++) {
@@ -1303,7 +1348,7 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
             return fail(RG_ERR_INVALID_ARG, "exact mode needs RG_STORE_FP32");
         if (mode == RG_MODE_ROOFGS && !(s->storage & RG_STORE_COMPACT))
             return fail(RG_ERR_INVALID_ARG, "RoofGS mode needs RG_STORE_COMPACT");
-        RG_TRY(make_layout(&cams[v], F[v]));
+        RG_TRY(make_layout(&cams[v], F[v], req_tw ? req_tw : TILE, req_th ? req_th : TILE));
         vs[v] = s;
     }
     int dev = 0;
@@ -1313,7 +1358,9 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
     BatchPlan* P = nullptr;
     const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL | RG_FLAG_BATCH_CHECKED);
     for (auto& p : g_plans) {
-        if (p->device != dev || p->mode != mode || p->flags != key_flags || p->scenes != vs) continue;
+        if (p->device != dev || p->mode != mode || p->flags != key_flags || p->scenes != vs || p->req_tw != req_tw ||
+            p->req_th != req_th)
+            continue;
         bool same = true;
         for (int v = 0; v < n && same; v++) same = p->widths[v] == F[v].cam.W && p->heights[v] == F[v].cam.H;
         if (same) {
@@ -1328,17 +1375,24 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
         np->scenes = vs;
         np->mode = mode;
         np->flags = key_flags;
+        np->req_tw = req_tw;
+        np->req_th = req_th;
         for (int v = 0; v < n; v++) {
             np->widths.push_back(F[v].cam.W);
             np->heights.push_back(F[v].cam.H);
         }
         RG_TRY(plan_init(*np));
-        RG_TRY(plan_size(*np, F, outs, st));
-        RG_TRY(plan_tune(*np, F, outs, st));
+        for (auto shape : plan_shapes(*np)) { // lanes sized for every candidate tile shape
+            std::vector<FrameLayout> Fs;
+            RG_TRY(layouts_for(cams, n, shape.first, shape.second, Fs));
+            RG_TRY(plan_size(*np, Fs, outs, st));
+        }
+        RG_TRY(plan_tune(*np, cams, outs, st));
         if (g_plans.size() >= 8) g_plans.erase(g_plans.begin());
         g_plans.push_back(std::move(np));
         P = g_plans.back().get();
     }
+    RG_TRY(layouts_for(cams, n, P->tw, P->th, F));
     RG_TRY(plan_capture(*P, F, outs, P->lanes, P->raster_flags));
     RG_CK(cudaGraphLaunch(P->exec, st));
     if (opts->flags & RG_FLAG_BATCH_CHECKED) {
@@ -1364,7 +1418,8 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
 // Lane count and pixels per thread the autotuner chose for the plan of these views
 // (0 lanes if no plan exists yet).
 rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
-                             const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread)
+                             const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread, int32_t* tile_w,
+                             int32_t* tile_h)
 {
     if (!scenes || !scene_idx || !cams || !opts || !lanes || !pixels_per_thread || n <= 0)
         return fail(RG_ERR_INVALID_ARG, "bad arguments");
@@ -1375,13 +1430,17 @@ rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, 
     std::lock_guard<std::mutex> lock(g_batch_mu);
     const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL | RG_FLAG_BATCH_CHECKED);
     for (auto& p : g_plans) {
-        if (p->device != dev || p->mode != opts->mode || p->flags != key_flags || (int)p->scenes.size() != n) continue;
+        if (p->device != dev || p->mode != opts->mode || p->flags != key_flags || (int)p->scenes.size() != n ||
+            p->req_tw != opts->tile_w || p->req_th != opts->tile_h)
+            continue;
         bool same = true;
         for (int v = 0; v < n && same; v++)
             same = p->scenes[v] == scenes[scene_idx[v]] && p->widths[v] == cams[v].width && p->heights[v] == cams[v].height;
         if (same) {
             *lanes = p->lanes;
             *pixels_per_thread = (p->raster_flags & RG_FLAG_SINGLE_PIXEL) ? 1 : ((p->raster_flags & RG_FLAG_QUAD_PIXEL) ? 4 : 2);
+            if (tile_w) *tile_w = p->tw;
+            if (tile_h) *tile_h = p->th;
             return RG_OK;
         }
     }
@@ -1395,12 +1454,12 @@ rg_status rg_backward(rg_scene* s, const rg_camera* cam, const rg_render_opts* o
     if (opts->mode != RG_MODE_EXACT)
         return fail(RG_ERR_UNSUPPORTED, "rg_backward differentiates exact mode only (RoofGS storage is INT8/FP16)");
     if (!(s->storage & RG_STORE_FP32)) return fail(RG_ERR_INVALID_ARG, "rg_backward needs RG_STORE_FP32");
-    const int tw = opts->tile_w ? opts->tile_w : TILE, th = opts->tile_h ? opts->tile_h : TILE;
-    if (tw != TILE || th != TILE) return fail(RG_ERR_UNSUPPORTED, "only 16x16 tiles are built");
+    int tw, th;
+    RG_TRY(tile_shape(opts, tw, th));
     if (s->n > 0 && (!grads->means || !grads->scales || !grads->quats || !grads->opacities || !grads->sh))
         return fail(RG_ERR_INVALID_ARG, "a gradient pointer is NULL");
     FrameLayout F;
-    RG_TRY(make_layout(cam, F));
+    RG_TRY(make_layout(cam, F, tw, th));
     cudaStream_t st = (cudaStream_t)stream;
     int64_t cap = s->ws.cap > 0 ? s->ws.cap : std::max<int64_t>(1 << 20, 4 * s->n);
     if (cap > MAX_CAP) cap = MAX_CAP;

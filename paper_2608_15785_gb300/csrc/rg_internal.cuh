@@ -7,7 +7,7 @@
 
 namespace rg {
 
-constexpr int TILE = 16;                       // tile edge in pixels (16 x 16 tiles)
+constexpr int TILE = 16;                       // default tile edge in pixels (16 x 16 tiles)
 constexpr float LN255F = 5.541263545158426f;   // ln 255: alpha = 1/255 in log space, Eq. (23)
 constexpr unsigned SPIN_LIMIT = 1u << 20;      // bounded device waits: ~1 s of polls with a short sleep
 
@@ -26,6 +26,8 @@ struct CamDev {
     float bg[3];
     float campos[3];  // camera centre -R^T t (for the SH view direction)
     float limx, limy; // 1.3 * tan(half field of view), FP32 pinned: 1.3f * ((0.5f * W) / fx)
+    int tw, th;       // tile shape in pixels: 16 x 16, 32 x 8 or 8 x 32 (tw * th = 256)
+    int tw_log2;      // log2(tw): thread t of a tile block owns column t & (tw - 1)
 };
 
 // Tile grid and resolution-adaptive key split (Sec. IV-A.2).
@@ -230,10 +232,10 @@ __device__ __forceinline__ bool project_bin(const CamDev& c, float mx, float my,
     b.xh = xh;
     b.yl = yl;
     b.yh = yh;
-    b.tx0 = (int)xl / TILE;
-    b.tx1 = (int)xh / TILE;
-    b.ty0 = (int)yl / TILE;
-    b.ty1 = (int)yh / TILE;
+    b.tx0 = (int)xl / c.tw;
+    b.tx1 = (int)xh / c.tw;
+    b.ty0 = (int)yl / c.th;
+    b.ty1 = (int)yh / c.th;
     // det Sigma' = |U0 x U1|^2 + 0.3 (|U0|^2 + |U1|^2) + 0.09 (Lagrange identity:
     // no cancellation for thin Gaussians)
     const float c0 = FS(FM(U[1], U[5]), FM(U[2], U[4]));
@@ -275,10 +277,10 @@ __device__ __forceinline__ RowTest row_test(const Binned& b)
 // Tile range [txa, txb] of tile row ty: the ellipse's x-extent over the row's band of
 // pixel centres, clipped to the box (reading of the Speedy-Splat culling, Sec. IV-A.3).
 // Returns false if no pixel centre of the band lies in it. Pinned FP32 order.
-__device__ __forceinline__ bool row_range(const RowTest& g, int ty, int& txa, int& txb)
+__device__ __forceinline__ bool row_range(const RowTest& g, int ty, int tw, int th, int& txa, int& txb)
 {
-    const float ya = fmaxf((float)(ty * TILE), g.yl);
-    const float yb = fminf((float)(ty * TILE + TILE - 1), g.yh);
+    const float ya = fmaxf((float)(ty * th), g.yl);
+    const float yb = fminf((float)(ty * th + th - 1), g.yh);
     const float d0 = FS(ya, g.v), d1 = FS(yb, g.v);
     const float dmax = fminf(fmaxf(g.ys, d0), d1);
     const float dmin = fminf(fmaxf(-g.ys, d0), d1);
@@ -289,8 +291,8 @@ __device__ __forceinline__ bool row_range(const RowTest& g, int ty, int& txa, in
     const float a0 = fmaxf(ceilf(xf), g.xl);
     const float a1 = fminf(floorf(xr), g.xh);
     if (!(a0 <= a1)) return false;
-    txa = (int)a0 / TILE;
-    txb = (int)a1 / TILE;
+    txa = (int)a0 / tw;
+    txb = (int)a1 / tw;
     return true;
 }
 

@@ -44,11 +44,11 @@ def _cams(k0, zfar_far=56.5):
     return cams
 
 
-def _single(scene, cam, mode, ppt):
+def _single(scene, cam, mode, ppt, tile):
     flags = 0
     if mode == "roofgs":
         flags = {1: binding.RG_FLAG_SINGLE_PIXEL, 2: 0, 4: binding.RG_FLAG_QUAD_PIXEL}[ppt]
-    out = scene.render(cam, mode=mode, flags=flags)
+    out = scene.render(cam, mode=mode, flags=flags, tile=tile)
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
@@ -60,10 +60,11 @@ def test_batch_equals_single_views(scenes, mode):
         cams = _cams(k0)
         outs = binding.render_batch(scenes, idx, cams, mode=mode)
         torch.cuda.synchronize()
-        lanes, ppt = binding.batch_plan_info(scenes, idx, cams, mode=mode)
+        lanes, ppt, tw, th = binding.batch_plan_info(scenes, idx, cams, mode=mode)
         assert lanes in (1, 2, 4) and ppt in ((1, 2, 4) if mode == "roofgs" else (2,))
+        assert (tw, th) in ((16, 16), (32, 8), (8, 32))
         for v, cam in enumerate(cams):
-            ref = _single(scenes[idx[v]], cam, mode, ppt)
+            ref = _single(scenes[idx[v]], cam, mode, ppt, (tw, th))
             assert np.array_equal(outs[v].cpu().numpy(), ref), (mode, call, v)
     for s in scenes:
         s.check()
@@ -78,7 +79,19 @@ def test_batch_checked_overflow_regrows(scenes):
                                                                                         zfar=80.0)]
     outs = binding.render_batch(scenes, idx, near, mode="roofgs", flags=binding.RG_FLAG_BATCH_CHECKED)
     torch.cuda.synchronize()
-    lanes, ppt = binding.batch_plan_info(scenes, idx, near, mode="roofgs")
+    lanes, ppt, tw, th = binding.batch_plan_info(scenes, idx, near, mode="roofgs")
     for v, cam in enumerate(near):
-        assert np.array_equal(outs[v].cpu().numpy(), _single(scenes[1], cam, "roofgs", ppt))
+        assert np.array_equal(outs[v].cpu().numpy(), _single(scenes[1], cam, "roofgs", ppt, (tw, th)))
     scenes[1].check()
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (8, 32)])
+def test_batch_with_a_fixed_tile_shape(scenes, tile):
+    idx = [v % 2 for v in range(len(SIZES))]
+    cams = _cams(3)
+    outs = binding.render_batch(scenes, idx, cams, mode="roofgs", tile=tile)
+    torch.cuda.synchronize()
+    lanes, ppt, tw, th = binding.batch_plan_info(scenes, idx, cams, mode="roofgs", tile=tile)
+    assert (tw, th) == tile
+    for v, cam in enumerate(cams):
+        assert np.array_equal(outs[v].cpu().numpy(), _single(scenes[idx[v]], cam, "roofgs", ppt, tile))

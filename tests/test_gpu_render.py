@@ -43,8 +43,8 @@ def gpu_scene(sc, per_gauss=False):
     return binding.Scene(sc, sh_scale_mode=binding.RG_SH_SCALE_BAND_GAUSS if per_gauss else binding.RG_SH_SCALE_BAND)
 
 
-def render(gs, cam, mode, flags=0, stats=False):
-    out = gs.render(cam, mode=mode, flags=flags, stats=stats)
+def render(gs, cam, mode, flags=0, stats=False, tile=(16, 16)):
+    out = gs.render(cam, mode=mode, flags=flags, stats=stats, tile=tile)
     torch.cuda.synchronize()
     if stats:
         return out[0].cpu().numpy().astype(np.float64), out[1]
@@ -106,8 +106,8 @@ def test_compact_attributes_bit_exact(per_gauss):
     assert np.array_equal(gs.inspect(binding.RG_INSPECT_LOG_OPACITY).view(np.uint32), comp.log_opac.view(np.uint32))
 
 
-def _keys_equal(gs, sc, cam, mode, comp=None):
-    k, v, ranges, _ = oracle.keys(sc, cam, mode, comp=comp)
+def _keys_equal(gs, sc, cam, mode, comp=None, tile=(16, 16)):
+    k, v, ranges, _ = oracle.keys(sc, cam, mode, comp=comp, tile=tile)
     gk = gs.inspect(binding.RG_INSPECT_KEYS)
     gk = gk.view(np.uint64) if mode == oracle.EXACT else gk.view(np.uint32).astype(np.uint64)
     gv = gs.inspect(binding.RG_INSPECT_VALUES)
@@ -420,3 +420,47 @@ def test_8k_three_tile_bit_passes_and_seven_exact_passes():
             assert (err <= tol[mask][None]).all(), (mode, float((err - tol[mask][None]).max()))
             assert float(np.mean((err > base).any(axis=0))) <= 0.02
         gs.check()
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (8, 32)])
+@pytest.mark.parametrize("mode", ["exact", "roofgs"])
+def test_tile_shapes_bit_exact_keys_and_images(tile, mode):
+    """32x8 and 8x32 tiles: keys, values and ranges bit-exact against the oracle's binning
+    with the same tile shape, images within the tolerances, on square, ragged and 1080p views."""
+    om = oracle.EXACT if mode == "exact" else oracle.ROOFGS
+    kind = oracle.EXP_EXACT if mode == "exact" else oracle.EXP_FAST32
+    base = TOL + (HALF_COLOUR if mode == "roofgs" else 0.0)
+    sc, cams = synth.workload("tiny_256")
+    cases = [(sc, cams[0], None), (sc, synth.tiny_camera(100, 37), None)]
+    big, bcams = synth.workload("clustered_1080p")
+    cases.append((big, bcams[0], _sample_tiles(oracle.layout(bcams[0], tile), 48, seed=5)))
+    for scene, cam, tiles in cases:
+        gs = gpu_scene(scene)
+        comp = oracle.compact(scene) if mode == "roofgs" else None
+        flag_sets = [0] if mode == "exact" else [0, binding.RG_FLAG_QUAD_PIXEL]
+        for fl in flag_sets:
+            img, st = render(gs, cam, mode, flags=fl, stats=True, tile=tile)
+            assert st["tiles_x"] == (cam.width + tile[0] - 1) // tile[0]
+            assert st["n_entries"] == _keys_equal(gs, scene, cam, om, comp, tile=tile)
+            ref, diag, _ = oracle.render(scene, cam, om, comp=comp, exp_kind=kind, tile=tile, tiles=tiles)
+            if tiles is None:
+                assert_close(img, ref, diag, base, max_flagged=0.02, label="%s %s" % (mode, tile))
+            else:
+                lay = oracle.layout(cam, tile)
+                m = np.zeros((cam.height, cam.width), bool)
+                for t in tiles:
+                    tx, ty = t % lay["tiles_x"], t // lay["tiles_x"]
+                    m[ty * tile[1]:(ty + 1) * tile[1], tx * tile[0]:(tx + 1) * tile[0]] = True
+                err = np.abs(img - ref)[:, m]
+                assert (err <= (base + allowance(diag))[m][None]).all()
+            # the timed (non-counting) launch gives the same image
+            assert np.array_equal(img, render(gs, cam, mode, flags=fl, tile=tile))
+        gs.check()
+
+
+def test_unsupported_tile_shape_is_rejected():
+    sc, cams = synth.workload("tiny_256")
+    gs = gpu_scene(sc)
+    with pytest.raises(binding.RgError) as e:
+        gs.render(cams[0], tile=(16, 8))
+    assert e.value.status == 8
