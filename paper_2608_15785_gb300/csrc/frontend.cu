@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a
         const unsigned rl = k - __shfl_sync(0xffffffffu, rexcl, owner);
         unsigned w = 0;
         int txa, txb;
-        if (k < wrows && row_range(s_rt[warp * 32 + owner], s_rt[warp * 32 + owner].ty0 + (int)rl, a.cam.tw, a.cam.th, txa, txb))
+        if (k < wrows && row_range(s_rt[warp * 32 + owner], s_rt[warp * 32 + owner].ty0 + (int)rl, a.cam.tw_log2, a.cam.th, txa, txb))
             w = (unsigned)(txb - txa + 1);
         if (k >= wrows) owner = 32; // past the warp's rows: a segment of its own
         // segmented sum of w over the lanes of one owner; its last lane adds it
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a
         if (k < wrows) {
             const RowTest& G = s_rt[warp * 32 + owner];
             ty = G.ty0 + (int)rl;
-            if (row_range(G, ty, a.cam.tw, a.cam.th, txa, txb)) w = (unsigned)(txb - txa + 1);
+            if (row_range(G, ty, a.cam.tw_log2, a.cam.th, txa, txb)) w = (unsigned)(txb - txa + 1);
         }
         const unsigned incl = warp_inclusive_scan(w, lane);
         const unsigned chunk = __shfl_sync(0xffffffffu, incl, 31);

@@ -203,6 +203,7 @@ rg_status make_layout(const rg_camera* c, FrameLayout& f, int tw = TILE, int th 
     d.tw = tw;
     d.th = th;
     d.tw_log2 = tw == 32 ? 5 : (tw == 16 ? 4 : 3);
+    d.th_log2 = th == 32 ? 5 : (th == 16 ? 4 : 3);
     return RG_OK;
 }
 

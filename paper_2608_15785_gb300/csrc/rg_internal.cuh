@@ -28,6 +28,7 @@ struct CamDev {
     float limx, limy; // 1.3 * tan(half field of view), FP32 pinned: 1.3f * ((0.5f * W) / fx)
     int tw, th;       // tile shape in pixels: 16 x 16, 32 x 8 or 8 x 32 (tw * th = 256)
     int tw_log2;      // log2(tw): thread t of a tile block owns column t & (tw - 1)
+    int th_log2;      // log2(th); pixel x >= 0 lies in tile column x >> tw_log2 (= x / tw)
 };
 
 // Tile grid and resolution-adaptive key split (Sec. IV-A.2).
@@ -232,10 +233,10 @@ __device__ __forceinline__ bool project_bin(const CamDev& c, float mx, float my,
     b.xh = xh;
     b.yl = yl;
     b.yh = yh;
-    b.tx0 = (int)xl / c.tw;
-    b.tx1 = (int)xh / c.tw;
-    b.ty0 = (int)yl / c.th;
-    b.ty1 = (int)yh / c.th;
+    b.tx0 = (int)xl >> c.tw_log2; // xl, xh, yl, yh >= 0: the shifts are the divisions by tw, th
+    b.tx1 = (int)xh >> c.tw_log2;
+    b.ty0 = (int)yl >> c.th_log2;
+    b.ty1 = (int)yh >> c.th_log2;
     // det Sigma' = |U0 x U1|^2 + 0.3 (|U0|^2 + |U1|^2) + 0.09 (Lagrange identity:
     // no cancellation for thin Gaussians)
     const float c0 = FS(FM(U[1], U[5]), FM(U[2], U[4]));
@@ -277,7 +278,7 @@ __device__ __forceinline__ RowTest row_test(const Binned& b)
 // Tile range [txa, txb] of tile row ty: the ellipse's x-extent over the row's band of
 // pixel centres, clipped to the box (reading of the Speedy-Splat culling, Sec. IV-A.3).
 // Returns false if no pixel centre of the band lies in it. Pinned FP32 order.
-__device__ __forceinline__ bool row_range(const RowTest& g, int ty, int tw, int th, int& txa, int& txb)
+__device__ __forceinline__ bool row_range(const RowTest& g, int ty, int tw_log2, int th, int& txa, int& txb)
 {
     const float ya = fmaxf((float)(ty * th), g.yl);
     const float yb = fminf((float)(ty * th + th - 1), g.yh);
@@ -291,8 +292,8 @@ __device__ __forceinline__ bool row_range(const RowTest& g, int ty, int tw, int 
     const float a0 = fmaxf(ceilf(xf), g.xl);
     const float a1 = fminf(floorf(xr), g.xh);
     if (!(a0 <= a1)) return false;
-    txa = (int)a0 / tw;
-    txb = (int)a1 / tw;
+    txa = (int)a0 >> tw_log2; // 0 <= a0 <= a1: the division by the tile width
+    txb = (int)a1 >> tw_log2;
     return true;
 }
 
