@@ -57,3 +57,31 @@ def test_stalled_lookback_times_out_and_reports(mode):
     assert torch.equal(again, ref)
     x = torch.ones(1024, device="cuda")
     assert float(x.sum()) == 1024.0
+
+
+def test_server_request_reports_the_timeout():
+    """A request whose frame runs out its bounded wait comes back from rg_poll as
+    RG_ERR_TIMEOUT; its slot is freed and a server without the hook serves normally."""
+    sc = synth.tiny_scene(10_000, seed=0)
+    cam = synth.tiny_camera(256, 256)
+    gs = binding.Scene(sc)
+    ref = gs.render(cam)
+    torch.cuda.synchronize()
+    out = torch.empty((3, 256, 256), device="cuda")
+    for flags, expect in ((binding.RG_FLAG_TEST_STALL_SORT, RG_ERR_TIMEOUT), (0, 0)):
+        srv = binding.Server([gs], 256, 256, mode="roofgs", flags=flags, max_slots=2)
+        for _ in range(2):  # the freed slot takes the next request
+            t = srv.submit(cam, 0)
+            deadline, status = time.time() + 60.0, None
+            while status is None and time.time() < deadline:
+                try:
+                    if srv.poll(t, out):
+                        status = 0
+                except binding.RgError as e:
+                    status = e.status
+                time.sleep(0.01)
+            assert status == expect
+            if expect == 0:
+                torch.cuda.synchronize()
+                assert torch.equal(out, ref)
+        srv.close()
