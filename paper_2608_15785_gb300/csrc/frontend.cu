@@ -1,15 +1,20 @@
 // frontend.cu -- front ends of the renderer and the scene conversion kernels.
 //
 //  * k_frontend_fused: the RoofGS fused preprocess + duplicate + key kernel
-//    (Sec. IV-A.3): one thread per Gaussian projects, culls, decodes INT8 SH
-//    (Eq. (8)) and FP16 geometry (Sec. IV-A.1), computes the tile rectangle
-//    and the 32-bit tile|quantized-depth key (Sec. IV-A.2, Eq. (9)); the block
-//    allocates its entries with one shared-memory prefix sum and one
+//    (Sec. IV-A.3): one thread per Gaussian (taken in quantized-depth order
+//    when the Gaussians were sorted by depth first) projects, culls, decodes
+//    INT8 SH (Eq. (8)) and FP16 geometry (Sec. IV-A.1), computes the snug box
+//    and the 32-bit tile|quantized-depth key (Sec. IV-A.2, Eq. (9)); the warps
+//    then walk the Gaussians' tile rows in parallel (lane k takes the k-th
+//    row), keep per row only the tiles the ellipse reaches, and count entries;
+//    the block allocates its entries with one shared-memory prefix sum and one
 //    device-wide slot (decoupled look-back, ordered by block, so equal keys stay
-//    in Gaussian order) and then writes the (key, value) array cooperatively:
-//    consecutive threads write consecutive entries (coalesced), whichever
-//    Gaussian they belong to. Only the raster record and the key-value array go
-//    to global memory.
+//    in Gaussian order) and writes the (key, value) array cooperatively:
+//    consecutive lanes write consecutive entries (coalesced), whichever
+//    Gaussian and row they belong to. Only the raster record and the key-value
+//    array go to global memory.
+//  * k_depth_keys: quantized depth and index of every Gaussian, the input of
+//    the per-Gaussian depth sort.
 //  * k_exact_*: the plain 3DGS front end (preprocess -> scan -> duplicate,
 //    Sec. II-A), 64-bit keys of 32-bit tile id | 32-bit float depth.
 //  * scene conversion: finite-value check, per-(degree, channel) max |SH|,

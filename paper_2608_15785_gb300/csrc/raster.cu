@@ -1,21 +1,24 @@
-// raster.cu -- tile rasterizers (one thread block per 16x16 tile).
+// raster.cu -- tile rasterizers (one thread block per tile of 256 pixels:
+// 16x16, 32x8 or 8x32).
 //
 // Front-to-back alpha blending of Sec. III-D, Eq. (7): for each pixel, over
 // the tile's depth-sorted Gaussians, alpha = min(0.99, o exp(p)) (Eqs. (10)-(12)),
 // pairs with alpha < 1/255 are skipped, the loop stops (without adding) once
 // the transmittance would fall below 1e-4, C += c alpha T, out = C + T bg.
 //
-// RoofGS mode (Sec. IV-B): while a batch of records is staged in shared
-// memory, each Gaussian's coefficients are folded (Eqs. (13)-(15)) --
-// -1/2 and log o absorbed, C1..C6 -- in TILE-LOCAL coordinates (pixel and mean
-// shifted by the tile origin, so the FP32 terms stay small at 4K); every
-// thread owns PPT vertically adjacent pixels (x, y) ... (x, y+PPT-1), two by
-// default (the paper's dual-pixel scheme), one or four on request: the first
-// exponent is the FMA chain of Eq. (16) on hoisted x^2, xy, y^2, x, y, each
-// next one follows from Eq. (20) (two additions per extra row). Pairs with P < -ln 255 are skipped before any
-// exponential (Eq. (23)); alpha = min(0.99, exp^(P)) with the bit-level
-// exponential of Eq. (24) (Eq. (25)). A warp whose pixels are all finished
-// skips the batch (vote); the block leaves once every pixel is finished.
+// RoofGS mode (Sec. IV-B): the block first finds its tile's [start, end) in
+// the sorted keys (warp-cooperative search). While a batch of records is
+// staged in shared memory, each Gaussian's coefficients are folded (Eqs.
+// (13)-(15)) -- -1/2 and log o absorbed, C1..C6 -- in TILE-LOCAL coordinates
+// (pixel and mean shifted by the tile origin, so the FP32 terms stay small at
+// 4K); every thread owns PPT vertically adjacent pixels (x, y) ... (x,
+// y+PPT-1), two by default (the paper's dual-pixel scheme), one or four on
+// request: the first exponent is the FMA chain of Eq. (16) on hoisted x^2, xy,
+// y^2, x, y, each next one follows from Eq. (20) (two additions per extra
+// row). Pairs with P < -ln 255 are skipped before any exponential (Eq. (23));
+// alpha = min(0.99, exp^(P)) with the bit-level exponential of Eq. (24)
+// (Eq. (25)). A warp whose pixels are all finished skips the batch (vote); the
+// block leaves once every pixel is finished.
 #include "rg_internal.cuh"
 
 namespace rg {

@@ -1,5 +1,7 @@
-// rg_api.cu -- C ABI of the renderer: resident scenes, frame workspace and the
-// per-frame launch sequence of both modes (see include/rg.h).
+// rg_api.cu -- C ABI of the renderer (declared in include/rg.h): resident
+// scenes and scene files, the frame workspace and the per-frame launch sequence
+// of both modes, batched rendering through captured CUDA graphs with an
+// autotuner, the backward, and the request loop (slots, dispatcher thread).
 #include <algorithm>
 #include <chrono>
 #include <cmath>

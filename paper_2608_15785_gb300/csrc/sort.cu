@@ -1,19 +1,23 @@
 // sort.cu -- stable LSD radix sort of (key, value) entries and per-tile ranges.
 //
 // Depth sort of Sec. III-C / Sec. IV-A.2: traffic ~ S_kv * N_dup * N_pass
-// (Eq. (6)). 8-bit digits; 4 passes for the 32-bit RoofGS key and
-// ceil((32 + b_t) / 8) passes for the 64-bit exact-mode key (only the bits
-// that can be non-zero are sorted).
+// (Eq. (6)). 8-bit digits; 4 passes for the 32-bit RoofGS key (or only the
+// ceil(b_t / 8) tile-bit passes when the Gaussians were put in depth order
+// first) and ceil((32 + b_t) / 8) passes for the 64-bit exact-mode key (only
+// the bits that can be non-zero are sorted).
 //
 // One histogram kernel reads every key once and counts the digits of all
 // passes. Each pass is then ONE kernel over tiles of 6144 (32-bit keys) or
-// 4096 (64-bit keys) entries (one-sweep scheme): a persistent grid takes tiles in order from an atomic counter,
-// ranks the tile's digits in shared memory (per-warp counters with match_any,
-// stable), publishes its per-digit counts, obtains the counts of all earlier
-// tiles by decoupled look-back (bounded waits), reorders the tile in shared
-// memory by digit and writes each digit run to its global position (runs of
-// consecutive addresses). Per pass every entry is read once and written once.
-// The number of entries is read on the device: no host round trip.
+// 4096 (64-bit keys) entries (one-sweep scheme): a persistent grid takes tiles
+// in order from an atomic counter, ranks the tile's digits per warp (match_any,
+// or one ballot per digit bit where warps hold many distinct digits; stable),
+// publishes its per-digit counts, obtains the counts of all earlier tiles by
+// decoupled look-back (bounded waits), reorders the tile in shared memory by
+// digit and writes each digit run to its global position (runs of consecutive
+// addresses). Per pass every entry is read once and written once. The number
+// of entries is read on the device: no host round trip. k_ranges finds the
+// per-tile [start, end) of a sorted array (exact mode; RoofGS frames find their
+// ranges inside the rasterizer).
 #include "rg_internal.cuh"
 
 namespace rg {
