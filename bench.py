@@ -176,6 +176,26 @@ def stage_work(mode, st, W, H):
             "ranges": ranges, "raster_ops": raster_ops}
 
 
+def rank_pose(rank, world, k, n_poses):
+    """Pose of rank `rank`'s k-th frame: ranks interleave over the orbit (replicas, no exchange)."""
+    return (rank + k * world) % n_poses
+
+
+def slowest_ms(ms_local, dist=None, device=None):
+    """The job's time for a region every rank timed: the max over ranks (all_reduce MAX)."""
+    if dist is None:
+        return ms_local
+    import torch
+    t = torch.tensor([float(ms_local)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_fps(frames_per_rank, world, ms):
+    """Whole-job frames per second: every rank's frames over the slowest rank's time."""
+    return world * frames_per_rank / (ms / 1000.0)
+
+
 def mean_stats(stats, poses_used):
     keys = ["n_gaussians", "n_front", "n_visible", "n_entries", "n_pairs", "n_blends", "tiles_x", "tiles_y",
             "sort_passes", "b_d"]
@@ -218,15 +238,10 @@ def run_ours(a, rank, world, local_rank):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(steps):
-            gs.render(cams[(rank + k * world) % len(cams)], mode=mode, flags=flags | rflags, out=out)
+            gs.render(cams[rank_pose(rank, world, k, len(cams))], mode=mode, flags=flags | rflags, out=out)
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return slowest_ms(e0.elapsed_time(e1), dist, dev)
 
     # RoofGS ingredient flag for the rasterizer's pixels per thread (ignored in exact mode)
     rflags = {1: binding.RG_FLAG_SINGLE_PIXEL, 2: 0, 4: binding.RG_FLAG_QUAD_PIXEL}[a.ppt]
@@ -251,7 +266,7 @@ def run_ours(a, rank, world, local_rank):
             sampler.mark("timed_end")
         stage_ms, frames = gs.stage_times()
         gs.check()  # no overflow, no timed-out wait in the timed frames
-        poses_used = sorted({(rank + k * world) % len(cams) for k in range(steps)})
+        poses_used = sorted({rank_pose(rank, world, k, len(cams)) for k in range(steps)})
         results[mode] = {"ms": ms, "steps": steps, "stats": mean_stats(stats, poses_used),
                          "stage_ms": [x / max(frames, 1) for x in stage_ms], "frames_timed_by_events": frames}
     # end-to-end through the public API: every frame rendered by rg_render and read back into pinned
@@ -265,11 +280,11 @@ def run_ours(a, rank, world, local_rank):
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        gs.render(cams[(rank + k * world) % len(cams)], mode="roofgs", flags=rflags, out=out)
+        gs.render(cams[rank_pose(rank, world, k, len(cams))], mode="roofgs", flags=rflags, out=out)
         hosts[0].copy_(out, non_blocking=True)
     torch.cuda.synchronize(dev)
     barrier()
-    e2e_serial_s = time.perf_counter() - t0
+    e2e_serial_ms = slowest_ms((time.perf_counter() - t0) * 1e3, dist, dev)
     rs = torch.cuda.current_stream(dev)
     cs = torch.cuda.Stream(dev)
     rendered = [torch.cuda.Event() for _ in range(2)]
@@ -280,7 +295,7 @@ def run_ours(a, rank, world, local_rank):
         b = k & 1
         if k >= 2:
             rs.wait_event(copied[b])
-        gs.render(cams[(rank + k * world) % len(cams)], mode="roofgs", flags=rflags, out=outs[b], stream=rs)
+        gs.render(cams[rank_pose(rank, world, k, len(cams))], mode="roofgs", flags=rflags, out=outs[b], stream=rs)
         rendered[b].record(rs)
         cs.wait_event(rendered[b])
         with torch.cuda.stream(cs):
@@ -288,7 +303,7 @@ def run_ours(a, rank, world, local_rank):
         copied[b].record(cs)
     torch.cuda.synchronize(dev)
     barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_ms = slowest_ms((time.perf_counter() - t0) * 1e3, dist, dev)
     gs.check()
     extra = {}
     if rank == 0 and not a.no_batch:
@@ -308,7 +323,7 @@ def run_ours(a, rank, world, local_rank):
         return None
 
     r = results["roofgs"]
-    fps = world * r["steps"] / (r["ms"] / 1000.0)
+    fps = job_fps(r["steps"], world, r["ms"])
     line = {"metric": METRIC, "value": round(fps, 2), "unit": UNIT, "n_gpus": world, "steps": r["steps"],
             "warmup": a.warmup, "ms_per_step": round(r["ms"] / r["steps"], 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
@@ -322,7 +337,7 @@ def run_ours(a, rank, world, local_rank):
            "stage_ms": dict(zip(STAGES, [round(x, 4) for x in r["stage_ms"]]))}
     if "exact" in results:
         ex = results["exact"]
-        ex_fps = world * ex["steps"] / (ex["ms"] / 1000.0)
+        ex_fps = job_fps(ex["steps"], world, ex["ms"])
         cfg["exact_fps"] = round(ex_fps, 2)
         cfg["speedup_vs_exact"] = round(fps / ex_fps, 3)
         cfg["exact_stage_ms"] = dict(zip(STAGES, [round(x, 4) for x in ex["stage_ms"]]))
@@ -333,11 +348,11 @@ def run_ours(a, rank, world, local_rank):
     # tile-bit passes, rasterizer (which finds the tile ranges itself)
     gp = (int(r["stats"]["b_d"]) + 7) // 8
     line["gpu_launches"] = r["steps"] * (1 + 1 + gp + 1 + 1 + int(r["stats"]["sort_passes"]) + 1)
-    line["e2e"] = {"value": round(world * e2e_steps / e2e_s, 2), "unit": UNIT,
+    line["e2e"] = {"value": round(job_fps(e2e_steps, world, e2e_ms), 2), "unit": UNIT,
                    "h2d_bytes_per_step": 100,  # the rg_camera struct, passed by value per call
                    "d2h_bytes_per_step": 3 * a.width * a.height * 4,
                    "mode": "pipelined: copy of frame k overlaps the render of frame k+1",
-                   "serial_value": round(world * e2e_steps / e2e_serial_s, 2)}
+                   "serial_value": round(job_fps(e2e_steps, world, e2e_serial_ms), 2)}
     line["clocks"] = {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if clocks else None
     line.update(extra)
     if world == 1 and not a.no_cpu_baseline:
