@@ -305,14 +305,17 @@ def run_ours(a, rank, world, local_rank):
     barrier()
     e2e_ms = slowest_ms((time.perf_counter() - t0) * 1e3, dist, dev)
     gs.check()
+    # one-GPU measurements (batch, pruning analog, backward, serving): in the N = 1 run only, so
+    # that ranks of a multi-GPU run do not wait idle on rank 0
     extra = {}
-    if rank == 0 and not a.no_batch:
+    single = world == 1
+    if single and not a.no_batch:
         extra["batch"] = run_batch(a, sc, gs, dev)
-    if rank == 0 and not a.no_ortho:
+    if single and not a.no_ortho:
         extra["ortho"] = run_ortho(a, sc, cams, gs, dev)
-    if rank == 0 and not a.no_backward:
+    if single and not a.no_backward:
         extra["backward"] = run_backward(dev)
-    if rank == 0 and not a.no_serve:
+    if single and not a.no_serve:
         extra["serve"] = run_serve(dev, gs, a.ppt)
     clocks = sampler.stop() if sampler else None
     if dist is not None:
