@@ -106,9 +106,9 @@ __global__ void __launch_bounds__(FE_THREADS, 4) k_frontend_fused(FrontendArgs a
                 // INT8 SH (Eq. (8)) decoded in registers, evaluated per band
                 unsigned w[12];
                 {
-                    const uint4 p0 = __ldg(&a.shq[i]);
-                    const uint4 p1 = __ldg(&a.shq[a.n + i]);
-                    const uint4 p2 = __ldg(&a.shq[2 * a.n + i]);
+                    const uint4 p0 = __ldg(&a.shq[3 * i]); // one 48-byte block per Gaussian
+                    const uint4 p1 = __ldg(&a.shq[3 * i + 1]);
+                    const uint4 p2 = __ldg(&a.shq[3 * i + 2]);
                     w[0] = p0.x; w[1] = p0.y; w[2] = p0.z; w[3] = p0.w;
                     w[4] = p1.x; w[5] = p1.y; w[6] = p1.z; w[7] = p1.w;
                     w[8] = p2.x; w[9] = p2.y; w[10] = p2.z; w[11] = p2.w;
@@ -533,7 +533,7 @@ __global__ void k_compact(const float* means, const float* scales, const float* 
         for (int k = 0; k < 4; k++)
             w[k] = (unsigned)codes[16 * pl + 4 * k] | ((unsigned)codes[16 * pl + 4 * k + 1] << 8) |
                    ((unsigned)codes[16 * pl + 4 * k + 2] << 16) | ((unsigned)codes[16 * pl + 4 * k + 3] << 24);
-        shq[pl * n + i] = make_uint4(w[0], w[1], w[2], w[3]);
+        shq[3 * i + pl] = make_uint4(w[0], w[1], w[2], w[3]);
     }
     geoA[i] = make_float4(means[3 * i], means[3 * i + 1], means[3 * i + 2], logo[i]);
     geoB[i] = make_uint4(pack_h2(quats[4 * i], quats[4 * i + 1]), pack_h2(quats[4 * i + 2], quats[4 * i + 3]),

@@ -1274,11 +1274,8 @@ rg_status rg_inspect(rg_scene* s, int32_t what, void* host_dst, int64_t cap_byte
     case RG_INSPECT_LOG_OPACITY: {
         if (!(s->storage & RG_STORE_COMPACT)) return fail(RG_ERR_INVALID_ARG, "scene has no compact attributes");
         if (what == RG_INSPECT_SH_CODES) {
-            std::vector<unsigned char> planes((size_t)n * 48);
-            if (n) RG_CK(cudaMemcpy(planes.data(), s->shq.p, (size_t)n * 48, cudaMemcpyDeviceToHost));
             tmp.resize((size_t)n * 48);
-            for (int64_t i = 0; i < n; i++)
-                for (int p = 0; p < 3; p++) memcpy(&tmp[(size_t)i * 48 + 16 * p], &planes[((size_t)p * n + i) * 16], 16);
+            if (n) RG_CK(cudaMemcpy(tmp.data(), s->shq.p, (size_t)n * 48, cudaMemcpyDeviceToHost));
             bytes = n * 48;
         } else if (what == RG_INSPECT_LOG_OPACITY) {
             std::vector<float> ga((size_t)n * 4);

@@ -353,7 +353,7 @@ struct FrontendArgs {
     const unsigned* order; // [N] Gaussian processed by thread slot i (depth order), or null (index order)
     const float4* geoA;    // [N] (mean.xyz, log o)
     const uint4* geoB;     // [N] FP16 (qw,qx | qy,qz | s0,s1 | s2,g)
-    const uint4* shq;      // [3][N] INT8 SH codes, 48 bytes per Gaussian in 3 planes
+    const uint4* shq;      // [N][3] INT8 SH codes, 48 contiguous bytes per Gaussian (byte j = 3k + c)
     float band_scale[12];  // s_{d,c}, [d][c]
     int per_gauss_scale;
     int sh_degree;

@@ -48,10 +48,11 @@ def test_save_load_renders_identically(tmp_path, storage):
         ga, ga2, gb = gs.backward(cams[0], w), gs.backward(cams[0], w), g2.backward(cams[0], w)
         for k in ga:
             # per-Gaussian sums use atomics, so two runs on the same scene differ by summation order;
-            # the loaded scene may differ from the saved one by no more than that
-            run_to_run = float((ga[k] - ga2[k]).abs().max())
-            diff = float((ga[k] - gb[k]).abs().max())
-            assert diff <= 2.0 * run_to_run + 1e-6 * float(ga[k].abs().max()) + 1e-12, (k, diff, run_to_run)
+            # the loaded scene may differ from the saved one by about as much (L2 norms: stable
+            # where the largest single difference is not)
+            noise = float((ga[k] - ga2[k]).double().norm())
+            diff = float((ga[k] - gb[k]).double().norm())
+            assert diff <= 4.0 * noise + 1e-7 * float(ga[k].double().norm()) + 1e-12, (k, diff, noise)
     gs.check()
     g2.check()
     g2.close()
