@@ -78,8 +78,8 @@ def parse():
 
 
 def workload_desc(a):
-    return ("clustered %dM Gaussians (20 clusters + shell r=50), %dx%d, 16x16 tiles, %d orbit poses, "
-            "INT8 SH with per-Gaussian FP16 scale" % (a.gaussians // 1_000_000, a.width, a.height, a.poses))
+    return ("clustered %gM Gaussians (20 clusters + shell r=50), %dx%d, 16x16 tiles, %d orbit poses, "
+            "INT8 SH with per-Gaussian FP16 scale" % (a.gaussians / 1e6, a.width, a.height, a.poses))
 
 
 def make_inputs(a):
