@@ -86,9 +86,9 @@ __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ k
     constexpr int V = 16 / sizeof(K); // keys per 16-byte load
     const long long nv = n / V;
     // consecutive keys often share digits (entries of one Gaussian): runs of equal
-    // digits among a thread's V keys take one shared atomic
-    for (long long j = gid; j < nv; j += gsz) {
-        const uint4 q = __ldg(reinterpret_cast<const uint4*>(keys) + j);
+    // digits among a thread's V keys take one shared atomic. Two 16-byte loads per
+    // iteration keep more of the stream in flight.
+    auto count = [&](const uint4& q) {
         K k[V];
         memcpy(k, &q, 16);
         for (int p = 0; p < passes; p++) {
@@ -106,6 +106,13 @@ __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ k
             }
             atomicAdd(&s_h[p][d], c);
         }
+    };
+    for (long long j = gid; j < nv; j += 2 * gsz) {
+        const uint4 q0 = __ldg(reinterpret_cast<const uint4*>(keys) + j);
+        const bool two = j + gsz < nv;
+        const uint4 q1 = two ? __ldg(reinterpret_cast<const uint4*>(keys) + j + gsz) : q0;
+        count(q0);
+        if (two) count(q1);
     }
     // tail (fewer than V keys)
     for (long long j = nv * V + gid; j < n; j += gsz) {
