@@ -1,64 +1,34 @@
 // rg_api.cu -- C ABI of the renderer (declared in include/rg.h): resident
 // scenes and scene files, the frame workspace and the per-frame launch sequence
-// of both modes, batched rendering through captured CUDA graphs with an
-// autotuner, the backward, and the request loop (slots, dispatcher thread).
+// of both modes, inspection, and the backward. Batched rendering is in
+// rg_batch.cu, the request loop in rg_serve.cu.
 #include <algorithm>
-#include <chrono>
 #include <cmath>
-#include <condition_variable>
-#include <deque>
-#include <memory>
-#include <mutex>
-#include <thread>
 #include <cstdio>
 #include <cstring>
-
-#include <nvtx3/nvToolsExt.h>
 #include <string>
 #include <vector>
 
-#include "rg.h"
-#include "rg_internal.cuh"
+#include <nvtx3/nvToolsExt.h>
+
+#include "rg_host.h"
 
 using namespace rg;
 
 namespace {
-
 thread_local std::string g_err;
+} // namespace
 
-rg_status fail(rg_status s, const std::string& msg)
+rg_status rg::fail(rg_status s, const std::string& msg)
 {
     g_err = msg;
     return s;
 }
 
-#define RG_CK(call)                                                                                           \
-    do {                                                                                                      \
-        cudaError_t e_ = (call);                                                                              \
-        if (e_ != cudaSuccess) return fail(RG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-#define RG_TRY(expr)                 \
-    do {                             \
-        rg_status s_ = (expr);       \
-        if (s_ != RG_OK) return s_;  \
-    } while (0)
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    template <typename T>
-    T* as() const { return reinterpret_cast<T*>(p); }
-};
+void rg::set_last_error(const char* msg) { g_err = msg; }
 
 // grow-only device allocation (contents are not preserved)
-rg_status ensure(DevBuf& b, size_t bytes, const char* what)
+rg_status rg::ensure(DevBuf& b, size_t bytes, const char* what)
 {
     if (bytes == 0) bytes = 16;
     if (b.p && b.bytes >= bytes) return RG_OK;
@@ -74,75 +44,7 @@ rg_status ensure(DevBuf& b, size_t bytes, const char* what)
     return RG_OK;
 }
 
-constexpr int EV_RING = 512;
-constexpr int EV_PER_FRAME = 7; // start, depth order, front end, histogram, sort, ranges, raster
-constexpr long long MAX_CAP = (1ll << 30) - 1;
-constexpr size_t CTRL_BYTES = sizeof(Counters) + 8 * 256 * sizeof(unsigned);
-constexpr size_t CTRL_ALLOC = 2 * CTRL_BYTES; // frame counters + the per-Gaussian depth sort's
-
-} // namespace
-
-void rg::set_last_error(const char* msg) { g_err = msg; }
-
-// Frame workspace: everything one frame in flight needs besides the scene.
-// rg_render uses the scene's own workspace; a batch lane or a server slot owns one.
-struct Workspace {
-    int64_t cap = 0;
-    DevBuf keys[2], vals[2];
-    DevBuf ranges;
-    DevBuf ctrl; // Counters followed by hist[8][256] (twice: frame, depth sort)
-    DevBuf lb_status;
-    DevBuf sort_status[2];
-    DevBuf xy, depth, conic, rgb, rect, touched, offsets; // exact per-Gaussian
-    DevBuf rec;                                           // RoofGS raster records
-    DevBuf gkeys[2], gvals[2], gstatus[2];                // RoofGS per-Gaussian depth sort
-    DevBuf gbuf;                                          // backward: image-space gradients [n][9]
-    // last frame
-    int last_mode = -1;
-    int last_passes = 0;
-    int last_tiles = 0;
-    // stage events
-    bool ev_init = false;
-    cudaEvent_t ev[EV_RING][EV_PER_FRAME];
-    int ev_next = 0;
-    int ev_pending = 0;
-
-    void release()
-    {
-        DevBuf* bufs[] = {&keys[0], &keys[1], &vals[0], &vals[1], &ranges, &ctrl, &lb_status, &sort_status[0],
-                          &sort_status[1], &xy, &depth, &conic, &rgb, &rect, &touched, &offsets, &rec, &gkeys[0],
-                          &gkeys[1], &gvals[0], &gvals[1], &gstatus[0], &gstatus[1], &gbuf};
-        for (DevBuf* b : bufs) b->release();
-        if (ev_init)
-            for (int f = 0; f < EV_RING; f++)
-                for (int k = 0; k < EV_PER_FRAME; k++) cudaEventDestroy(ev[f][k]);
-        ev_init = false;
-        cap = 0;
-    }
-};
-
-struct rg_scene {
-    int device = 0;
-    int64_t n = 0;
-    int sh_degree = 3;
-    uint32_t storage = 0;
-    int sh_scale_mode = 0;
-    // exact-mode attributes (FP32)
-    DevBuf means, scales, quats, opac, sh;
-    // compact attributes (RoofGS mode)
-    DevBuf geoA, geoB, shq;
-    float band_scale[12] = {0};
-    DevBuf sticky; // Sticky flags of every frame rendered from this scene
-    Workspace ws;  // frame workspace of rg_render / rg_backward
-};
-
-namespace {
-
-struct FrameLayout {
-    Layout lay;
-    CamDev cam;
-    int tiles;
-};
+namespace rg {
 
 // Tile shapes with kernels: 256 pixels each, width a power of two.
 bool tile_shape_ok(int tw, int th) { return (tw == 16 && th == 16) || (tw == 32 && th == 8) || (tw == 8 && th == 32); }
@@ -156,7 +58,7 @@ rg_status tile_shape(const rg_render_opts* o, int& tw, int& th)
     return RG_OK;
 }
 
-rg_status make_layout(const rg_camera* c, FrameLayout& f, int tw = TILE, int th = TILE)
+rg_status make_layout(const rg_camera* c, FrameLayout& f, int tw, int th)
 {
     if (!tile_shape_ok(tw, th)) return fail(RG_ERR_UNSUPPORTED, "tile shapes built: 16x16, 32x8, 8x32");
     if (!c) return fail(RG_ERR_INVALID_ARG, "camera is NULL");
@@ -267,7 +169,7 @@ struct NvtxScope {
 
 // One frame on `st`; the caller has checked arguments and the workspace.
 rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode, uint32_t flags, float* out,
-                      cudaStream_t st, bool count = false)
+                      cudaStream_t st, bool count)
 {
     Counters* ctr = w.ctrl.as<Counters>();
     unsigned* hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + sizeof(Counters));
@@ -487,383 +389,7 @@ void destroy_scene(rg_scene* s)
 }
 
 
-// ---------------------------------------------------------------------------
-// Batched rendering: a plan per (scenes, resolutions, mode, flags) owns L lanes,
-// each a stream and a workspace; a call captures every view's pipeline on the
-// lanes (view v on lane v mod L) into one CUDA graph, updates the plan's
-// instantiated graph in place and launches it once on the caller's stream.
-// ---------------------------------------------------------------------------
-constexpr int BATCH_MAX_LANES = 4;
-
-struct BatchPlan {
-    int device = 0;
-    std::vector<rg_scene*> scenes;
-    std::vector<int> widths, heights;
-    int mode = 0;
-    uint32_t flags = 0;
-    int lanes = 1;
-    uint32_t raster_flags = 0; // autotuned: 0 (two pixels per thread), RG_FLAG_SINGLE_PIXEL or RG_FLAG_QUAD_PIXEL
-    int req_tw = 0, req_th = 0; // requested tile shape (0 x 0: autotuned)
-    int tw = TILE, th = TILE;   // tile shape in use
-    bool tuned = false;
-    std::unique_ptr<Workspace[]> ws{new Workspace[BATCH_MAX_LANES]};
-    cudaStream_t streams[BATCH_MAX_LANES] = {nullptr};
-    cudaEvent_t join[BATCH_MAX_LANES] = {nullptr};
-    cudaEvent_t fork = nullptr;
-    cudaStream_t cap = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int exec_lanes = 0;
-    uint32_t exec_raster = 0;
-    int exec_tw = 0;
-
-    ~BatchPlan()
-    {
-        if (exec) cudaGraphExecDestroy(exec);
-        for (int l = 0; l < BATCH_MAX_LANES; l++) {
-            if (streams[l]) cudaStreamDestroy(streams[l]);
-            if (join[l]) cudaEventDestroy(join[l]);
-            ws[l].release();
-        }
-        if (fork) cudaEventDestroy(fork);
-        if (cap) cudaStreamDestroy(cap);
-    }
-};
-
-std::mutex g_batch_mu;
-std::vector<std::unique_ptr<BatchPlan>> g_plans;
-
-// drop every plan that renders from scene s (called when s is destroyed)
-void drop_plans_of(const rg_scene* s)
-{
-    std::lock_guard<std::mutex> lock(g_batch_mu);
-    for (size_t k = 0; k < g_plans.size();) {
-        bool uses = false;
-        for (rg_scene* x : g_plans[k]->scenes) uses |= (x == s);
-        if (uses) g_plans.erase(g_plans.begin() + k);
-        else k++;
-    }
-}
-
-rg_status plan_init(BatchPlan& P)
-{
-    for (int l = 0; l < BATCH_MAX_LANES; l++) {
-        RG_CK(cudaStreamCreateWithFlags(&P.streams[l], cudaStreamNonBlocking));
-        RG_CK(cudaEventCreateWithFlags(&P.join[l], cudaEventDisableTiming));
-    }
-    RG_CK(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
-    RG_CK(cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking));
-    return RG_OK;
-}
-
-// Size every lane for every view: render each view once on lane 0's workspace with
-// the checked path, then give all lanes the largest capacity (+25 % headroom for
-// other poses). Also runs each kernel once outside capture (first-use set-up).
-rg_status plan_size(BatchPlan& P, const std::vector<FrameLayout>& F, float* const* outs, cudaStream_t st)
-{
-    int64_t cap = 0;
-    int max_tiles = 1;
-    int64_t max_n = 1;
-    for (size_t v = 0; v < F.size(); v++) {
-        rg_scene* s = P.scenes[v];
-        max_tiles = std::max(max_tiles, F[v].tiles);
-        max_n = std::max<int64_t>(max_n, s->n);
-        int64_t c = P.ws[0].cap > 0 ? P.ws[0].cap : std::max<int64_t>(1 << 20, 4 * s->n);
-        if (c > MAX_CAP) c = MAX_CAP;
-        RG_TRY(ensure_workspace(P.ws[0], s->n, P.mode, F[v].tiles, c));
-        for (int attempt = 0; attempt < 2; attempt++) {
-            RG_TRY(render_once(s, P.ws[0], F[v], P.mode, P.flags, outs[v], st));
-            Counters c2;
-            RG_CK(cudaMemcpyAsync(&c2, P.ws[0].ctrl.p, sizeof(c2), cudaMemcpyDeviceToHost, st));
-            RG_CK(cudaStreamSynchronize(st));
-            if (c2.error) return fail(RG_ERR_TIMEOUT, "a bounded device wait gave up");
-            cap = std::max<int64_t>(cap, (int64_t)c2.n_entries_total);
-            if (c2.n_entries_total <= (unsigned long long)P.ws[0].cap) break;
-            int64_t want = (int64_t)(c2.n_entries_total + c2.n_entries_total / 4 + 1024);
-            if (want > MAX_CAP) return fail(RG_ERR_CAPACITY, "a view needs more than 2^30 - 1 entries");
-            RG_TRY(ensure_workspace(P.ws[0], s->n, P.mode, F[v].tiles, want));
-        }
-    }
-    cap = std::min<int64_t>(MAX_CAP, cap + cap / 4 + 1024);
-    for (int l = 0; l < BATCH_MAX_LANES; l++) {
-        for (size_t v = 0; v < F.size(); v++)
-            RG_TRY(ensure_workspace(P.ws[l], P.scenes[v]->n, P.mode, max_tiles, std::max(cap, P.ws[l].cap)));
-    }
-    // the scenes' sticky flags of the sizing frames are not errors
-    for (rg_scene* s : P.scenes) RG_CK(cudaMemsetAsync(s->sticky.p, 0, sizeof(Sticky), st));
-    RG_CK(cudaStreamSynchronize(st));
-    return RG_OK;
-}
-
-// Capture all views on `lanes` lanes and bring P.exec up to date.
-rg_status plan_capture(BatchPlan& P, const std::vector<FrameLayout>& F, float* const* outs, int lanes,
-                       uint32_t raster_flags)
-{
-    RG_CK(cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal));
-    rg_status err = RG_OK;
-    cudaError_t ce = cudaEventRecord(P.fork, P.cap);
-    for (int l = 0; l < lanes && ce == cudaSuccess; l++) ce = cudaStreamWaitEvent(P.streams[l], P.fork, 0);
-    const uint32_t fl = (P.flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL)) | raster_flags;
-    for (size_t v = 0; v < F.size() && ce == cudaSuccess && err == RG_OK; v++)
-        err = render_once(P.scenes[v], P.ws[v % lanes], F[v], P.mode, fl, outs[v], P.streams[v % lanes]);
-    for (int l = 0; l < lanes && ce == cudaSuccess; l++) {
-        ce = cudaEventRecord(P.join[l], P.streams[l]);
-        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(P.cap, P.join[l], 0);
-    }
-    cudaGraph_t g = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(P.cap, &g);
-    if (err != RG_OK) {
-        if (g) cudaGraphDestroy(g);
-        return err;
-    }
-    if (ce != cudaSuccess || ee != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        return fail(RG_ERR_CUDA, std::string("batch capture failed: ") +
-                                     cudaGetErrorString(ce != cudaSuccess ? ce : ee));
-    }
-    bool fresh = !P.exec || P.exec_lanes != lanes || P.exec_raster != raster_flags || (!F.empty() && P.exec_tw != F[0].cam.tw);
-    if (!fresh) {
-        cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(P.exec, g, &info) != cudaSuccess) {
-            cudaGetLastError();
-            fresh = true;
-        }
-    }
-    if (fresh) {
-        if (P.exec) cudaGraphExecDestroy(P.exec);
-        P.exec = nullptr;
-        const cudaError_t ie = cudaGraphInstantiate(&P.exec, g, 0);
-        if (ie != cudaSuccess) {
-            cudaGraphDestroy(g);
-            P.exec = nullptr;
-            return fail(RG_ERR_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(ie));
-        }
-        P.exec_lanes = lanes;
-        P.exec_raster = raster_flags;
-        P.exec_tw = F.empty() ? 0 : F[0].cam.tw;
-    }
-    cudaGraphDestroy(g);
-    return RG_OK;
-}
-
-// layouts of all views for one tile shape
-rg_status layouts_for(const rg_camera* cams, int n, int tw, int th, std::vector<FrameLayout>& F)
-{
-    F.resize((size_t)n);
-    for (int v = 0; v < n; v++) RG_TRY(make_layout(&cams[v], F[v], tw, th));
-    return RG_OK;
-}
-
-// candidate tile shapes of a plan
-std::vector<std::pair<int, int>> plan_shapes(const BatchPlan& P)
-{
-    if (P.req_tw) return {{P.req_tw, P.req_th}};
-    return {{16, 16}, {32, 8}, {8, 32}};
-}
-
-// Pick the tile shape, the lane count and the pixels per thread by timing the captured batch.
-rg_status plan_tune(BatchPlan& P, const rg_camera* cams, float* const* outs, cudaStream_t st)
-{
-    const int V = (int)P.scenes.size();
-    float best = 1e30f;
-    int best_l = 1, best_tw = TILE, best_th = TILE;
-    uint32_t best_r = 0;
-    cudaEvent_t e0, e1;
-    RG_CK(cudaEventCreate(&e0));
-    RG_CK(cudaEventCreate(&e1));
-    std::vector<FrameLayout> F;
-    rg_status e = RG_OK;
-    for (auto shape : plan_shapes(P)) {
-        e = layouts_for(cams, V, shape.first, shape.second, F);
-        for (int lanes : {1, 2, 4}) {
-            if (e != RG_OK) break;
-            if (lanes > V && lanes > 1) continue;
-            for (uint32_t r : {0u, (uint32_t)RG_FLAG_SINGLE_PIXEL, (uint32_t)RG_FLAG_QUAD_PIXEL}) {
-                if (P.mode != RG_MODE_ROOFGS && r) continue;
-                e = plan_capture(P, F, outs, lanes, r);
-                if (e != RG_OK) break;
-                float ms = 0.f;
-                if (cudaGraphLaunch(P.exec, st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess ||
-                    cudaGraphLaunch(P.exec, st) != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
-                    cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                    e = fail(RG_ERR_CUDA, "timing the captured batch failed");
-                    break;
-                }
-                if (ms < best) {
-                    best = ms;
-                    best_l = lanes;
-                    best_r = r;
-                    best_tw = shape.first;
-                    best_th = shape.second;
-                }
-            }
-        }
-        if (e != RG_OK) break;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (e != RG_OK) return e;
-    P.lanes = best_l;
-    P.raster_flags = best_r;
-    P.tw = best_tw;
-    P.th = best_th;
-    P.tuned = true;
-    return RG_OK;
-}
-
-
-// ---------------------------------------------------------------------------
-// Request loop (serving): slots of stream + workspace + result buffer; a
-// dispatcher thread admits queued requests into free slots as earlier ones
-// complete, so requests overlap on the device (continuous batching).
-// ---------------------------------------------------------------------------
-using Clock = std::chrono::steady_clock;
-
-struct ServeRequest {
-    uint64_t ticket = 0;
-    rg_camera cam;
-    int scene = 0;
-    Clock::time_point submitted;
-};
-
-struct ServeSlot {
-    Workspace ws;
-    cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
-    float* out = nullptr;            // [3][max_h][max_w]
-    Counters* pinned_ctr = nullptr;  // host copy of the frame counters of the request
-    enum { FREE, RUNNING, DONE } state = FREE;
-    ServeRequest req;
-    FrameLayout F;
-    rg_status result = RG_OK;
-    int attempts = 0;
-};
-
-} // namespace
-
-struct rg_server {
-    int device = 0;
-    std::vector<rg_scene*> scenes;
-    int mode = RG_MODE_ROOFGS;
-    uint32_t flags = 0;
-    int max_w = 0, max_h = 0;
-    int64_t budget = 0, slot_bytes = 0;
-    std::vector<std::unique_ptr<ServeSlot>> slots;
-    std::deque<ServeRequest> pending;
-    std::mutex mu;
-    std::condition_variable cv;
-    std::thread worker;
-    bool stop = false;
-    uint64_t next_ticket = 1;
-    std::vector<double> latencies_ms; // submit -> result ready
-    int max_in_flight = 0;
-    int64_t completed = 0;
-    std::string error;
-};
-
-namespace {
-
-rg_status slot_launch(rg_server* sv, ServeSlot& sl)
-{
-    rg_scene* s = sv->scenes[sl.req.scene];
-    RG_TRY(ensure_workspace(sl.ws, s->n, sv->mode, sl.F.tiles, sl.ws.cap > 0 ? sl.ws.cap : (int64_t)1 << 20));
-    RG_TRY(render_once(s, sl.ws, sl.F, sv->mode, sv->flags & ~RG_FLAG_STAGE_EVENTS, sl.out, sl.stream));
-    RG_CK(cudaMemcpyAsync(sl.pinned_ctr, sl.ws.ctrl.p, sizeof(Counters), cudaMemcpyDeviceToHost, sl.stream));
-    RG_CK(cudaEventRecord(sl.done, sl.stream));
-    return RG_OK;
-}
-
-// dispatcher: complete finished slots (re-render after growing on overflow), admit new requests
-void server_loop(rg_server* sv)
-{
-    cudaSetDevice(sv->device);
-    std::unique_lock<std::mutex> lock(sv->mu);
-    while (true) {
-        bool busy = false;
-        for (auto& up : sv->slots) {
-            ServeSlot& sl = *up;
-            if (sl.state != ServeSlot::RUNNING) continue;
-            busy = true;
-            const cudaError_t q = cudaEventQuery(sl.done);
-            if (q == cudaErrorNotReady) continue;
-            if (q != cudaSuccess) {
-                cudaGetLastError();
-                sl.result = RG_ERR_CUDA;
-                sl.state = ServeSlot::DONE;
-                continue;
-            }
-            const Counters& c = *sl.pinned_ctr;
-            if (c.error) {
-                sl.result = RG_ERR_TIMEOUT;
-            } else if (c.n_entries_total > (unsigned long long)sl.ws.cap && sl.attempts < 2) {
-                // grow the slot and render the request again
-                int64_t want = (int64_t)(c.n_entries_total + c.n_entries_total / 4 + 1024);
-                sl.attempts++;
-                rg_scene* s = sv->scenes[sl.req.scene];
-                rg_status e = want > MAX_CAP ? RG_ERR_CAPACITY
-                                             : ensure_workspace(sl.ws, s->n, sv->mode, sl.F.tiles, want);
-                if (e == RG_OK) e = slot_launch(sv, sl);
-                if (e == RG_OK) continue;
-                sl.result = e;
-            } else if (c.n_entries_total > (unsigned long long)sl.ws.cap) {
-                sl.result = RG_ERR_CAPACITY;
-            } else {
-                sl.result = RG_OK;
-            }
-            sl.state = ServeSlot::DONE;
-            sv->latencies_ms.push_back(
-                std::chrono::duration<double, std::milli>(Clock::now() - sl.req.submitted).count());
-            sv->completed++;
-            sv->cv.notify_all();
-        }
-        // admit queued requests into free slots (first come, first served)
-        for (auto& up : sv->slots) {
-            if (sv->pending.empty()) break;
-            ServeSlot& sl = *up;
-            if (sl.state != ServeSlot::FREE) continue;
-            sl.req = sv->pending.front();
-            sv->pending.pop_front();
-            sl.attempts = 0;
-            make_layout(&sl.req.cam, sl.F); // validated at submit
-            sl.state = ServeSlot::RUNNING;
-            const rg_status e = slot_launch(sv, sl);
-            if (e != RG_OK) {
-                sl.result = e;
-                sl.state = ServeSlot::DONE;
-                sv->completed++;
-                sv->cv.notify_all();
-            }
-            busy = true;
-        }
-        int running = 0;
-        for (auto& up : sv->slots) running += up->state == ServeSlot::RUNNING;
-        sv->max_in_flight = std::max(sv->max_in_flight, running);
-        if (sv->stop && !busy && sv->pending.empty()) break;
-        if (busy) {
-            lock.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
-            lock.lock();
-        } else {
-            sv->cv.wait_for(lock, std::chrono::milliseconds(5));
-        }
-    }
-}
-
-void server_free(rg_server* sv)
-{
-    for (auto& up : sv->slots) {
-        ServeSlot& sl = *up;
-        if (sl.stream) cudaStreamSynchronize(sl.stream);
-        sl.ws.release();
-        if (sl.out) cudaFree(sl.out);
-        if (sl.pinned_ctr) cudaFreeHost(sl.pinned_ctr);
-        if (sl.done) cudaEventDestroy(sl.done);
-        if (sl.stream) cudaStreamDestroy(sl.stream);
-    }
-    delete sv;
-}
-
-} // namespace
+} // namespace rg
 
 extern "C" {
 
@@ -1326,127 +852,6 @@ rg_status rg_eval_fast_exp(const float* P_dev, float* out_dev, int64_t n, void* 
     return RG_OK;
 }
 
-rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
-                          const rg_render_opts* opts, float* const* outs, void* stream)
-{
-    if (n < 0) return fail(RG_ERR_INVALID_ARG, "negative view count");
-    if (n == 0) return RG_OK;
-    if (!scenes || !scene_idx || !cams || !opts || !outs) return fail(RG_ERR_INVALID_ARG, "NULL argument");
-    const int mode = opts->mode;
-    if (mode != RG_MODE_EXACT && mode != RG_MODE_ROOFGS) return fail(RG_ERR_INVALID_ARG, "unknown mode");
-    // tile shape: 0 x 0 lets the autotuner choose among the built shapes
-    const int req_tw = opts->tile_w, req_th = opts->tile_h;
-    if ((req_tw || req_th) && !tile_shape_ok(req_tw, req_th))
-        return fail(RG_ERR_UNSUPPORTED, "tile shapes built: 16x16, 32x8, 8x32 (or 0x0: autotuned)");
-    std::vector<FrameLayout> F((size_t)n);
-    std::vector<rg_scene*> vs((size_t)n);
-    for (int v = 0; v < n; v++) {
-        if (scene_idx[v] < 0) return fail(RG_ERR_INVALID_ARG, "negative scene index");
-        rg_scene* s = scenes[scene_idx[v]];
-        if (!s || !outs[v]) return fail(RG_ERR_INVALID_ARG, "NULL scene or output");
-        if (mode == RG_MODE_EXACT && !(s->storage & RG_STORE_FP32))
-            return fail(RG_ERR_INVALID_ARG, "exact mode needs RG_STORE_FP32");
-        if (mode == RG_MODE_ROOFGS && !(s->storage & RG_STORE_COMPACT))
-            return fail(RG_ERR_INVALID_ARG, "RoofGS mode needs RG_STORE_COMPACT");
-        RG_TRY(make_layout(&cams[v], F[v], req_tw ? req_tw : TILE, req_th ? req_th : TILE));
-        vs[v] = s;
-    }
-    int dev = 0;
-    RG_CK(cudaGetDevice(&dev));
-    cudaStream_t st = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lock(g_batch_mu);
-    BatchPlan* P = nullptr;
-    const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL | RG_FLAG_BATCH_CHECKED);
-    for (auto& p : g_plans) {
-        if (p->device != dev || p->mode != mode || p->flags != key_flags || p->scenes != vs || p->req_tw != req_tw ||
-            p->req_th != req_th)
-            continue;
-        bool same = true;
-        for (int v = 0; v < n && same; v++) same = p->widths[v] == F[v].cam.W && p->heights[v] == F[v].cam.H;
-        if (same) {
-            P = p.get();
-            break;
-        }
-    }
-    const bool fresh = P == nullptr;
-    if (fresh) {
-        std::unique_ptr<BatchPlan> np(new BatchPlan());
-        np->device = dev;
-        np->scenes = vs;
-        np->mode = mode;
-        np->flags = key_flags;
-        np->req_tw = req_tw;
-        np->req_th = req_th;
-        for (int v = 0; v < n; v++) {
-            np->widths.push_back(F[v].cam.W);
-            np->heights.push_back(F[v].cam.H);
-        }
-        RG_TRY(plan_init(*np));
-        for (auto shape : plan_shapes(*np)) { // lanes sized for every candidate tile shape
-            std::vector<FrameLayout> Fs;
-            RG_TRY(layouts_for(cams, n, shape.first, shape.second, Fs));
-            RG_TRY(plan_size(*np, Fs, outs, st));
-        }
-        RG_TRY(plan_tune(*np, cams, outs, st));
-        if (g_plans.size() >= 8) g_plans.erase(g_plans.begin());
-        g_plans.push_back(std::move(np));
-        P = g_plans.back().get();
-    }
-    RG_TRY(layouts_for(cams, n, P->tw, P->th, F));
-    RG_TRY(plan_capture(*P, F, outs, P->lanes, P->raster_flags));
-    RG_CK(cudaGraphLaunch(P->exec, st));
-    if (opts->flags & RG_FLAG_BATCH_CHECKED) {
-        // synchronous check: resize and render again if a view overflowed its lane
-        bool over = false;
-        for (rg_scene* s : P->scenes) {
-            Sticky h;
-            RG_CK(cudaMemcpyAsync(&h, s->sticky.p, sizeof(h), cudaMemcpyDeviceToHost, st));
-            RG_CK(cudaStreamSynchronize(st));
-            if (h.error) return fail(RG_ERR_TIMEOUT, "a bounded device wait gave up");
-            over |= h.overflow != 0;
-        }
-        if (over) { // grow the lanes (never shrink) for these views and render again
-            RG_TRY(plan_size(*P, F, outs, st));
-            RG_TRY(plan_capture(*P, F, outs, P->lanes, P->raster_flags));
-            RG_CK(cudaGraphLaunch(P->exec, st));
-            RG_CK(cudaStreamSynchronize(st));
-        }
-    }
-    return RG_OK;
-}
-
-// Lane count and pixels per thread the autotuner chose for the plan of these views
-// (0 lanes if no plan exists yet).
-rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
-                             const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread, int32_t* tile_w,
-                             int32_t* tile_h)
-{
-    if (!scenes || !scene_idx || !cams || !opts || !lanes || !pixels_per_thread || n <= 0)
-        return fail(RG_ERR_INVALID_ARG, "bad arguments");
-    *lanes = 0;
-    *pixels_per_thread = 0;
-    int dev = 0;
-    RG_CK(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lock(g_batch_mu);
-    const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL | RG_FLAG_BATCH_CHECKED);
-    for (auto& p : g_plans) {
-        if (p->device != dev || p->mode != opts->mode || p->flags != key_flags || (int)p->scenes.size() != n ||
-            p->req_tw != opts->tile_w || p->req_th != opts->tile_h)
-            continue;
-        bool same = true;
-        for (int v = 0; v < n && same; v++)
-            same = p->scenes[v] == scenes[scene_idx[v]] && p->widths[v] == cams[v].width && p->heights[v] == cams[v].height;
-        if (same) {
-            *lanes = p->lanes;
-            *pixels_per_thread = (p->raster_flags & RG_FLAG_SINGLE_PIXEL) ? 1 : ((p->raster_flags & RG_FLAG_QUAD_PIXEL) ? 4 : 2);
-            if (tile_w) *tile_w = p->tw;
-            if (tile_h) *tile_h = p->th;
-            return RG_OK;
-        }
-    }
-    return RG_OK;
-}
-
 rg_status rg_backward(rg_scene* s, const rg_camera* cam, const rg_render_opts* opts, const float* dL_dimg,
                       const rg_grads* grads, void* stream)
 {
@@ -1507,180 +912,6 @@ rg_status rg_backward(rg_scene* s, const rg_camera* cam, const rg_render_opts* o
     launch_raster_backward(b, st);
     launch_preprocess_backward(b, st);
     RG_CK(cudaGetLastError());
-    return RG_OK;
-}
-
-rg_status rg_server_create(rg_scene* const* scenes, int32_t n_scenes, const rg_server_config* cfg, rg_server** out)
-{
-    if (!out) return fail(RG_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if (!scenes || n_scenes <= 0 || !cfg) return fail(RG_ERR_INVALID_ARG, "bad arguments");
-    if (cfg->mode != RG_MODE_EXACT && cfg->mode != RG_MODE_ROOFGS) return fail(RG_ERR_INVALID_ARG, "unknown mode");
-    if (cfg->max_width <= 0 || cfg->max_height <= 0) return fail(RG_ERR_INVALID_ARG, "max resolution must be set");
-    for (int k = 0; k < n_scenes; k++) {
-        if (!scenes[k]) return fail(RG_ERR_INVALID_ARG, "NULL scene");
-        if (cfg->mode == RG_MODE_EXACT && !(scenes[k]->storage & RG_STORE_FP32))
-            return fail(RG_ERR_INVALID_ARG, "exact mode needs RG_STORE_FP32");
-        if (cfg->mode == RG_MODE_ROOFGS && !(scenes[k]->storage & RG_STORE_COMPACT))
-            return fail(RG_ERR_INVALID_ARG, "RoofGS mode needs RG_STORE_COMPACT");
-    }
-    std::unique_ptr<rg_server> sv(new rg_server());
-    RG_CK(cudaGetDevice(&sv->device));
-    sv->scenes.assign(scenes, scenes + n_scenes);
-    sv->mode = cfg->mode;
-    sv->flags = cfg->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_BATCH_CHECKED);
-    sv->max_w = cfg->max_width;
-    sv->max_h = cfg->max_height;
-    sv->budget = cfg->memory_budget > 0 ? cfg->memory_budget : (8ll << 30);
-    // calibrate one slot: the largest scene at the largest resolution, pose of the first camera
-    int big = 0;
-    for (int k = 1; k < n_scenes; k++)
-        if (scenes[k]->n > scenes[big]->n) big = k;
-    std::unique_ptr<ServeSlot> probe(new ServeSlot());
-    RG_CK(cudaStreamCreateWithFlags(&probe->stream, cudaStreamNonBlocking));
-    RG_CK(cudaEventCreateWithFlags(&probe->done, cudaEventDisableTiming));
-    const size_t out_bytes = (size_t)3 * sv->max_w * sv->max_h * 4;
-    if (cudaMalloc(&probe->out, out_bytes) != cudaSuccess) return fail(RG_ERR_OOM, "slot output");
-    if (cudaMallocHost(&probe->pinned_ctr, sizeof(Counters)) != cudaSuccess) return fail(RG_ERR_OOM, "pinned counters");
-    int64_t entries = 0;
-    if (cfg->calibration) {
-        probe->req.cam = *cfg->calibration;
-        probe->req.cam.width = sv->max_w;
-        probe->req.cam.height = sv->max_h;
-        probe->req.scene = big;
-        RG_TRY(make_layout(&probe->req.cam, probe->F));
-        RG_TRY(ensure_workspace(probe->ws, scenes[big]->n, sv->mode, probe->F.tiles, (int64_t)1 << 20));
-        for (int attempt = 0; attempt < 2; attempt++) {
-            RG_TRY(render_once(scenes[big], probe->ws, probe->F, sv->mode, sv->flags, probe->out, probe->stream));
-            Counters c;
-            RG_CK(cudaMemcpyAsync(&c, probe->ws.ctrl.p, sizeof(c), cudaMemcpyDeviceToHost, probe->stream));
-            RG_CK(cudaStreamSynchronize(probe->stream));
-            entries = (int64_t)c.n_entries_total;
-            if (c.n_entries_total <= (unsigned long long)probe->ws.cap) break;
-            RG_TRY(ensure_workspace(probe->ws, scenes[big]->n, sv->mode, probe->F.tiles,
-                                    std::min<int64_t>(MAX_CAP, entries + entries / 4 + 1024)));
-        }
-        RG_CK(cudaMemsetAsync(scenes[big]->sticky.p, 0, sizeof(Sticky), probe->stream));
-    }
-    const int64_t cap = std::min<int64_t>(MAX_CAP, std::max<int64_t>(1 << 20, entries + entries / 2 + 1024));
-    const int64_t ngauss = scenes[big]->n;
-    const int64_t tiles = (int64_t)((sv->max_w + TILE - 1) / TILE) * ((sv->max_h + TILE - 1) / TILE);
-    // bytes of one slot: 2 x (keys 8 B + values 4 B) per entry, sort status, per-Gaussian arrays, ranges, image
-    sv->slot_bytes = cap * 24 + (cap / 4096 + 1) * 2048 + ngauss * (sv->mode == RG_MODE_EXACT ? 72 : 56) +
-                     tiles * 8 + (int64_t)out_bytes;
-    int nslots = cfg->max_slots > 0 ? cfg->max_slots : 8;
-    nslots = (int)std::max<int64_t>(1, std::min<int64_t>(nslots, sv->budget / std::max<int64_t>(sv->slot_bytes, 1)));
-    for (int k = 0; k < nslots; k++) {
-        std::unique_ptr<ServeSlot> sl;
-        if (k == 0) {
-            sl = std::move(probe);
-        } else {
-            sl.reset(new ServeSlot());
-            RG_CK(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
-            RG_CK(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
-            if (cudaMalloc(&sl->out, out_bytes) != cudaSuccess) return fail(RG_ERR_OOM, "slot output");
-            if (cudaMallocHost(&sl->pinned_ctr, sizeof(Counters)) != cudaSuccess)
-                return fail(RG_ERR_OOM, "pinned counters");
-        }
-        for (int j = 0; j < n_scenes; j++)
-            RG_TRY(ensure_workspace(sl->ws, scenes[j]->n, sv->mode, (int)tiles, std::max(cap, sl->ws.cap)));
-        sv->slots.push_back(std::move(sl));
-    }
-    RG_CK(cudaDeviceSynchronize());
-    rg_server* raw = sv.release();
-    raw->worker = std::thread(server_loop, raw);
-    *out = raw;
-    return RG_OK;
-}
-
-rg_status rg_server_destroy(rg_server* server)
-{
-    if (!server) return RG_OK;
-    {
-        std::lock_guard<std::mutex> lock(server->mu);
-        server->stop = true;
-        server->cv.notify_all();
-    }
-    if (server->worker.joinable()) server->worker.join();
-    server_free(server);
-    return RG_OK;
-}
-
-rg_status rg_submit(rg_server* server, const rg_camera* cam, int32_t scene_slot, uint64_t* ticket)
-{
-    if (!server || !cam || !ticket) return fail(RG_ERR_INVALID_ARG, "NULL argument");
-    if (scene_slot < 0 || scene_slot >= (int32_t)server->scenes.size()) return fail(RG_ERR_INVALID_ARG, "bad scene slot");
-    FrameLayout F;
-    RG_TRY(make_layout(cam, F));
-    if (cam->width > server->max_w || cam->height > server->max_h)
-        return fail(RG_ERR_INVALID_ARG, "request larger than the server's maximum resolution");
-    ServeRequest r;
-    r.cam = *cam;
-    r.scene = scene_slot;
-    r.submitted = Clock::now();
-    std::lock_guard<std::mutex> lock(server->mu);
-    if (server->stop) return fail(RG_ERR_BUSY, "server is stopping");
-    r.ticket = server->next_ticket++;
-    server->pending.push_back(r);
-    *ticket = r.ticket;
-    server->cv.notify_all();
-    return RG_OK;
-}
-
-rg_status rg_poll(rg_server* server, uint64_t ticket, float* out_chw)
-{
-    if (!server || !out_chw) return fail(RG_ERR_INVALID_ARG, "NULL argument");
-    ServeSlot* hit = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(server->mu);
-        for (auto& up : server->slots)
-            if (up->state != ServeSlot::FREE && up->req.ticket == ticket) hit = up.get();
-        if (!hit) {
-            for (const ServeRequest& r : server->pending)
-                if (r.ticket == ticket) return RG_ERR_NOT_READY;
-            return fail(RG_ERR_INVALID_ARG, "unknown or already collected ticket");
-        }
-        if (hit->state != ServeSlot::DONE) return RG_ERR_NOT_READY;
-    }
-    rg_status res = hit->result;
-    if (res == RG_OK) {
-        const size_t bytes = (size_t)3 * hit->F.cam.W * hit->F.cam.H * 4;
-        cudaError_t e = cudaMemcpyAsync(out_chw, hit->out, bytes, cudaMemcpyDeviceToDevice, hit->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(hit->stream);
-        if (e != cudaSuccess) res = fail(RG_ERR_CUDA, cudaGetErrorString(e));
-    } else {
-        fail(res, "request failed");
-    }
-    std::lock_guard<std::mutex> lock(server->mu);
-    hit->state = ServeSlot::FREE;
-    server->cv.notify_all();
-    return res;
-}
-
-rg_status rg_server_stats(rg_server* server, rg_server_stats_t* st)
-{
-    if (!server || !st) return fail(RG_ERR_INVALID_ARG, "NULL argument");
-    std::lock_guard<std::mutex> lock(server->mu);
-    std::vector<double> l = server->latencies_ms;
-    std::sort(l.begin(), l.end());
-    auto pct = [&](double p) { return l.empty() ? 0.0 : l[std::min(l.size() - 1, (size_t)(p * (l.size() - 1) + 0.5))]; };
-    st->completed = server->completed;
-    st->pending = (int64_t)server->pending.size();
-    st->slots = (int32_t)server->slots.size();
-    st->max_in_flight = server->max_in_flight;
-    st->p50_ms = pct(0.50);
-    st->p99_ms = pct(0.99);
-    st->slot_bytes = server->slot_bytes;
-    return RG_OK;
-}
-
-rg_status rg_server_reset_stats(rg_server* server)
-{
-    if (!server) return fail(RG_ERR_INVALID_ARG, "NULL argument");
-    std::lock_guard<std::mutex> lock(server->mu);
-    server->latencies_ms.clear();
-    server->completed = 0;
-    server->max_in_flight = 0;
     return RG_OK;
 }
 
