@@ -177,20 +177,24 @@ rg_status rg_scene_load(const char* path, void* stream, rg_scene** out);
 rg_status rg_scene_reserve(rg_scene* scene, int64_t n_entries);
 
 /*
- * Render one view into out_chw, a caller-owned device buffer of 3*H*W FP32
- * values laid out [channel][row][column].
+ * Render one view into out_chw, a caller-owned buffer of 3*H*W FP32 values laid
+ * out [channel][row][column]: device memory, or pinned host memory that the
+ * device addresses (the image is then written straight to the host).
  * Pipeline (exact): preprocess -> scan -> duplicate -> 64-bit radix sort ->
  * tile ranges -> rasterizer (Sec. II-A pipeline, Sec. III).
- * Pipeline (RoofGS): fused front end -> 32-bit radix sort (4 passes) ->
- * tile ranges -> dual-pixel fast-exp rasterizer (Sec. IV).
+ * Pipeline (RoofGS): Gaussians ordered by quantized depth -> fused front end ->
+ * stable radix sort of the tile bits of the 32-bit keys (the order of the full
+ * key; RG_FLAG_SORT_FULL_KEY sorts all 32 bits in 4 passes instead) -> fast-exp
+ * rasterizer with 2 (dual-pixel), 1 or 4 pixels per thread, each tile block
+ * finding its own range of the sorted entries (Sec. IV).
  * The number of entries stays on the device: with stats == NULL the call does
  * not synchronise; if the entries exceed the workspace the image is
  * incomplete and the overflow is recorded (see rg_scene_check). With stats
  * != NULL the call synchronises, grows the workspace and renders again if
  * needed, and fills *stats.
- * Errors: RG_ERR_INVALID_ARG (NULL, width/height <= 0, zfar <= znear, tile
- * shape other than 16x16, a mode whose storage the scene lacks),
- * RG_ERR_CAPACITY, RG_ERR_TIMEOUT, RG_ERR_CUDA, RG_ERR_OOM.
+ * Errors: RG_ERR_INVALID_ARG (NULL, width/height <= 0, zfar <= znear, a mode
+ * whose storage the scene lacks), RG_ERR_UNSUPPORTED (a tile shape other than
+ * 16x16, 32x8, 8x32), RG_ERR_CAPACITY, RG_ERR_TIMEOUT, RG_ERR_CUDA, RG_ERR_OOM.
  */
 rg_status rg_render(rg_scene* scene, const rg_camera* cam, const rg_render_opts* opts, float* out_chw,
                     rg_stats* stats, void* stream);

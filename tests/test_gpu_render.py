@@ -497,3 +497,17 @@ def test_input_permutation_invariance():
         assert np.array_equal(a[:, free], b[:, free]), (mode, len(tied))
     ga.check()
     gb.check()
+
+
+@pytest.mark.parametrize("mode", ["exact", "roofgs"])
+def test_render_into_pinned_host_memory(mode):
+    """out may be pinned host memory that the GPU addresses: the image is written straight
+    to the host and equals the device-buffer render."""
+    sc, cams = synth.workload("tiny_256")
+    gs = gpu_scene(sc)
+    dev = gs.render(cams[0], mode=mode)
+    host = torch.empty((3, 256, 256), dtype=torch.float32, pin_memory=True)
+    gs.render(cams[0], mode=mode, out=host)
+    torch.cuda.synchronize()
+    assert torch.equal(dev.cpu(), host)
+    gs.check()
