@@ -43,7 +43,10 @@ __device__ __forceinline__ unsigned pack_h2(float lo, float hi)
 // ---------------------------------------------------------------------------
 // Fused front end (RoofGS)
 // ---------------------------------------------------------------------------
-constexpr int FE_THREADS = 256;
+#ifndef RG_FE_THREADS
+#define RG_FE_THREADS 256
+#endif
+constexpr int FE_THREADS = RG_FE_THREADS;
 constexpr int FE_WARPS = FE_THREADS / 32;
 
 __device__ __forceinline__ unsigned warp_sum(unsigned x)
@@ -63,10 +66,10 @@ __device__ __forceinline__ unsigned warp_inclusive_scan(unsigned x, int lane)
     return x;
 }
 
-// 8 blocks per SM (64 warps, 32 registers): the kernel is latency-bound on its
-// depth-ordered gathers and shuffles, and full occupancy measured 0.41 ms at 4K
-// against 0.52 ms at 4 blocks per SM (61 registers)
-__global__ void __launch_bounds__(FE_THREADS, 8) k_frontend_fused(FrontendArgs a)
+// Full occupancy (64 warps per SM, 32 registers): the kernel is latency-bound on
+// its depth-ordered gathers and shuffles, and 8 blocks of 256 threads per SM
+// measured 0.41 ms at 4K against 0.52 ms at 4 blocks per SM (61 registers)
+__global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fused(FrontendArgs a)
 {
     __shared__ unsigned s_vb;
     __shared__ unsigned s_wsum[FE_WARPS];
@@ -286,6 +289,8 @@ void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Co
     const unsigned blocks = (unsigned)((a.n + 255) / 256);
     k_depth_keys<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(a, keys, vals, ctr);
 }
+
+int frontend_block_threads() { return FE_THREADS; }
 
 void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s)
 {

@@ -129,7 +129,8 @@ rg_status ensure_workspace(Workspace& w, int64_t n_gauss, int mode, int tiles, i
     }
     RG_TRY(ensure(w.ranges, (size_t)tiles * sizeof(uint2), "ranges"));
     RG_TRY(ensure(w.ctrl, CTRL_ALLOC, "counters"));
-    RG_TRY(ensure(w.lb_status, (size_t)((n + 255) / 256 + 1) * 8, "look-back status"));
+    const int64_t fe_blocks = (n + frontend_block_threads() - 1) / frontend_block_threads();
+    RG_TRY(ensure(w.lb_status, (size_t)(std::max<int64_t>(fe_blocks, (n + 2047) / 2048) + 1) * 8, "look-back status"));
     if (mode == RG_MODE_EXACT) {
         RG_TRY(ensure(w.xy, (size_t)n * 8, "xy"));
         RG_TRY(ensure(w.depth, (size_t)n * 4, "depth"));
@@ -261,7 +262,8 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         a.status = w.lb_status.as<unsigned long long>();
         a.ctr = ctr;
         a.sticky = sticky;
-        RG_CK(cudaMemsetAsync(w.lb_status.p, 0, (size_t)((n + 255) / 256 + 1) * 8, st));
+        RG_CK(cudaMemsetAsync(w.lb_status.p, 0,
+                              (size_t)((n + frontend_block_threads() - 1) / frontend_block_threads() + 1) * 8, st));
         sa.key_bytes = 4;
         if (flags & RG_FLAG_SORT_FULL_KEY) {
             // the paper's scheme: entries in Gaussian order, 4 passes over the 32-bit key

@@ -369,6 +369,8 @@ struct FrontendArgs {
     Sticky* sticky;
 };
 void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s);
+// threads per block of the fused front end (one look-back status word per block)
+int frontend_block_threads();
 // quantized depth (Eq. (9)) of every Gaussian as a sort key, Gaussian index as value;
 // culled Gaussians get 2^b_d - 1 (the fused front end skips them); writes n to ctr
 void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, cudaStream_t s);
