@@ -73,8 +73,7 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
 {
     __shared__ unsigned s_vb;
     __shared__ unsigned s_wsum[FE_WARPS];
-    __shared__ unsigned s_excl[FE_THREADS]; // block-local exclusive prefix of entry counts
-    __shared__ RowTest s_rt[FE_THREADS];    // per-row test of each thread's Gaussian
+    __shared__ RowTestS s_rt[FE_THREADS];   // per-row test of each thread's Gaussian
     __shared__ unsigned s_q[FE_THREADS];    // quantized depth, Eq. (9)
     __shared__ unsigned s_id[FE_THREADS];   // Gaussian index of each slot
     __shared__ unsigned s_cnt[FE_THREADS];  // entries of each slot's Gaussian
@@ -147,15 +146,16 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
             }
         }
     }
-    s_rt[tid] = rt;
+    s_rt[tid] = shared_row_test(rt);
     s_q[tid] = qd;
     s_id[tid] = (unsigned)i;
     __syncwarp();
 
     // Entries per Gaussian. The warp's Gaussians have rows_l tile rows each; the
     // warp walks all of its rows 32 at a time (lane k takes the k-th row of the
-    // chunk, whichever Gaussian it belongs to) and sums the row widths per
-    // Gaussian with a segmented reduction.
+    // chunk, whichever Gaussian it belongs to) and adds each row's width to its
+    // Gaussian's count with a shared-memory atomic (measured faster than a
+    // segmented warp reduction: a chunk's rows belong to few Gaussians).
     const int rows_l = rt.ty1 - rt.ty0 + 1 > 0 ? rt.ty1 - rt.ty0 + 1 : 0;
     const unsigned rincl = warp_inclusive_scan((unsigned)rows_l, lane);
     const unsigned rexcl = rincl - (unsigned)rows_l;
@@ -173,18 +173,9 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
         int txa, txb;
         if (k < wrows && row_range(s_rt[warp * 32 + owner], s_rt[warp * 32 + owner].ty0 + (int)rl, a.cam.tw_log2, a.cam.th, txa, txb))
             w = (unsigned)(txb - txa + 1);
-        if (k >= wrows) owner = 32; // past the warp's rows: a segment of its own
-        // segmented sum of w over the lanes of one owner; its last lane adds it
-        const unsigned owner_prev = __shfl_up_sync(0xffffffffu, (unsigned)owner, 1);
-        const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || owner_prev != (unsigned)owner);
-        const unsigned wi = warp_inclusive_scan(w, lane);
-        const int seg0 = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
-        const unsigned before = __shfl_sync(0xffffffffu, wi, seg0 > 0 ? seg0 - 1 : 0);
-        const unsigned owner_next = __shfl_down_sync(0xffffffffu, (unsigned)owner, 1);
-        if ((lane == 31 || owner_next != (unsigned)owner) && k < wrows)
-            s_cnt[warp * 32 + owner] += wi - (seg0 > 0 ? before : 0u);
-        __syncwarp();
+        if (w) atomicAdd(&s_cnt[warp * 32 + owner], w);
     }
+    __syncwarp();
     const unsigned cnt = s_cnt[tid];
 
     // block-level prefix sum of the entry counts
@@ -198,7 +189,6 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
         if (lane < FE_WARPS) s_wsum[lane] = ws; // inclusive warp totals
     }
     __syncthreads();
-    s_excl[tid] = x - cnt + (warp ? s_wsum[warp - 1] : 0u);
     const unsigned block_total = s_wsum[FE_WARPS - 1];
 
     // one device-wide allocation per block, ordered by block
@@ -227,10 +217,11 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
     // Emission: the warp's entries are contiguous and in (Gaussian, row, tile)
     // order, so the warp walks its rows again 32 at a time, scans the row
     // widths, and writes 32 consecutive entries per store instruction (lane e
-    // finds the row of its entry with a 5-step search over the scan).
+    // finds the row of its entry with a 5-step search over the scan and takes
+    // the row's first tile, depth and Gaussian from that lane).
     const int b_d = a.lay.b_d;
     const unsigned tiles_x = (unsigned)a.lay.tiles_x;
-    unsigned long long out = base + s_excl[warp * 32];
+    unsigned long long out = base + (warp ? s_wsum[warp - 1] : 0u); // the warp's first entry
     for (unsigned r0 = 0; r0 < wrows; r0 += 32) {
         const unsigned k = r0 + (unsigned)lane;
         int owner = 0;
@@ -238,34 +229,38 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
         for (int step = 16; step > 0; step >>= 1)
             if (__shfl_sync(0xffffffffu, rincl, owner + step - 1) <= k) owner += step;
         const unsigned rl = k - __shfl_sync(0xffffffffu, rexcl, owner);
-        unsigned w = 0;
-        int txa = 0, txb = -1, ty = 0;
+        unsigned w = 0, tb = 0, q = 0, id = 0;
         if (k < wrows) {
-            const RowTest& G = s_rt[warp * 32 + owner];
-            ty = G.ty0 + (int)rl;
-            if (row_range(G, ty, a.cam.tw_log2, a.cam.th, txa, txb)) w = (unsigned)(txb - txa + 1);
+            const RowTestS& G = s_rt[warp * 32 + owner];
+            const int ty = G.ty0 + (int)rl;
+            int txa, txb;
+            if (row_range(G, ty, a.cam.tw_log2, a.cam.th, txa, txb)) {
+                w = (unsigned)(txb - txa + 1);
+                tb = (unsigned)ty * tiles_x + (unsigned)txa; // tile of the row's first entry
+            }
+            q = s_q[warp * 32 + owner];
+            id = s_id[warp * 32 + owner];
         }
         const unsigned incl = warp_inclusive_scan(w, lane);
         const unsigned chunk = __shfl_sync(0xffffffffu, incl, 31);
+        tb -= incl - w; // entry e of the chunk, if in this row, has tile tb + e (mod 2^32)
+        // entries at or past the capacity are counted but not written
+        const bool fits = out < (unsigned long long)a.cap;
+        const unsigned room = fits ? (unsigned)((unsigned long long)a.cap - out) : 0u;
+        unsigned* const kp = a.keys + (fits ? out : 0ull);
+        unsigned* const vp = a.vals + (fits ? out : 0ull);
         for (unsigned e0 = 0; e0 < chunk; e0 += 32) {
             const unsigned e = e0 + (unsigned)lane;
             int pos = 0; // row (lane) of entry e
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1)
                 if (__shfl_sync(0xffffffffu, incl, pos + step - 1) <= e) pos += step;
-            const unsigned ex = __shfl_sync(0xffffffffu, incl - w, pos);
-            const int ta = __shfl_sync(0xffffffffu, txa, pos);
-            const int tr = __shfl_sync(0xffffffffu, ty, pos);
-            const int ow = __shfl_sync(0xffffffffu, owner, pos);
-            if (e < chunk) {
-                const unsigned t = (unsigned)(warp * 32 + ow);
-                const unsigned tile = (unsigned)tr * tiles_x + (unsigned)ta + (e - ex);
-                const unsigned key = (b_d >= 32) ? s_q[t] : ((tile << b_d) | s_q[t]);
-                const unsigned long long dst = out + e;
-                if (dst < (unsigned long long)a.cap) {
-                    a.keys[dst] = key;
-                    a.vals[dst] = s_id[t];
-                }
+            const unsigned tile = __shfl_sync(0xffffffffu, tb, pos) + e;
+            const unsigned qe = __shfl_sync(0xffffffffu, q, pos);
+            const unsigned ide = __shfl_sync(0xffffffffu, id, pos);
+            if (e < chunk && e < room) {
+                kp[e] = (b_d >= 32) ? qe : ((tile << b_d) | qe);
+                vp[e] = ide;
             }
         }
         out += chunk;

@@ -275,10 +275,23 @@ __device__ __forceinline__ RowTest row_test(const Binned& b)
     return r;
 }
 
+// The per-row test as the other lanes of a warp read it (shared memory): the
+// constants and the first tile row.
+struct RowTestS {
+    float u, v, tt, isc, ys, cc, kk, xl, xh, yl, yh;
+    int ty0;
+};
+
+__device__ __forceinline__ RowTestS shared_row_test(const RowTest& r)
+{
+    return RowTestS{r.u, r.v, r.tt, r.isc, r.ys, r.cc, r.kk, r.xl, r.xh, r.yl, r.yh, r.ty0};
+}
+
 // Tile range [txa, txb] of tile row ty: the ellipse's x-extent over the row's band of
 // pixel centres, clipped to the box (reading of the Speedy-Splat culling, Sec. IV-A.3).
 // Returns false if no pixel centre of the band lies in it. Pinned FP32 order.
-__device__ __forceinline__ bool row_range(const RowTest& g, int ty, int tw_log2, int th, int& txa, int& txb)
+template <class G>
+__device__ __forceinline__ bool row_range(const G& g, int ty, int tw_log2, int th, int& txa, int& txb)
 {
     const float ya = fmaxf((float)(ty * th), g.yl);
     const float yb = fminf((float)(ty * th + th - 1), g.yh);
