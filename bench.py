@@ -160,7 +160,13 @@ def stage_work(mode, st, W, H):
         # depth/opacity range, 48 B INT8 SH + 32 B record if visible, 8 B key+value per entry
         front = 20 * N + 16 * nf + 80 * nv + 8 * nd
         sort_pass = 16 * nd  # one pass: each (key, value) entry read once and written once
-        hist = 4 * nd
+        if passes <= 2:
+            # the front end counted the tile digits: the histogram kernel clears the first pass's
+            # look-back status (1 KB per 6144-entry tile) and sums the front end's 16 copies of the
+            # [2][256] counts
+            hist = 1024 * ((nd + 6143) // 6144) + (16 + 1) * 512 * 4
+        else:
+            hist = 4 * nd
         ranges = 0  # no ranges pass: every rasterizer block searches its tile's range in the sorted keys
     else:
         depth = 0

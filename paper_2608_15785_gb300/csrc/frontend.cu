@@ -12,7 +12,9 @@
 //    in Gaussian order) and writes the (key, value) array cooperatively:
 //    consecutive lanes write consecutive entries (coalesced), whichever
 //    Gaussian and row they belong to. Only the raster record and the key-value
-//    array go to global memory.
+//    array go to global memory, besides the digit counts of the entry sort
+//    (each tile row is a run of consecutive tile ids; counted per block in
+//    shared memory, added to one of a few global copies).
 //  * k_depth_keys: quantized depth and index of every Gaussian, the input of
 //    the per-Gaussian depth sort.
 //  * k_exact_*: the plain 3DGS front end (preprocess -> scan -> duplicate,
@@ -48,6 +50,37 @@ __device__ __forceinline__ unsigned pack_h2(float lo, float hi)
 #endif
 constexpr int FE_THREADS = RG_FE_THREADS;
 constexpr int FE_WARPS = FE_THREADS / 32;
+constexpr int RADIX_FE = 256;
+
+// Adds the digits of the w consecutive tiles t0 .. t0 + w - 1 to the block's
+// digit counts: pass 0 digit t & 255 (difference array: +1 where a run of digits
+// starts, -1 after it ends, full cycles of 256 added to every digit via entry 0),
+// pass 1 digit t >> 8 (t < 2^16).
+__device__ __forceinline__ void count_tile_digits(unsigned* s_d0, unsigned* s_h1, int passes, unsigned t0, unsigned w)
+{
+    const unsigned full = w >> 8, r = w & 255u;
+    if (full) atomicAdd(&s_d0[0], full);
+    if (r) {
+        const unsigned d = t0 & 255u, e = d + r;
+        atomicAdd(&s_d0[d], 1u);
+        if (e < 256u) {
+            atomicSub(&s_d0[e], 1u);
+        } else if (e > 256u) { // the run wraps past digit 255
+            atomicAdd(&s_d0[0], 1u);
+            atomicSub(&s_d0[e - 256u], 1u);
+        }
+    }
+    if (passes > 1) {
+        const unsigned t1 = t0 + w - 1u, h0 = t0 >> 8, h1 = t1 >> 8;
+        if (h0 == h1) {
+            atomicAdd(&s_h1[h0], w);
+        } else {
+            atomicAdd(&s_h1[h0], ((h0 + 1u) << 8) - t0);
+            for (unsigned h = h0 + 1u; h < h1; h++) atomicAdd(&s_h1[h], 256u);
+            atomicAdd(&s_h1[h1], t1 - (h1 << 8) + 1u);
+        }
+    }
+}
 
 __device__ __forceinline__ unsigned warp_sum(unsigned x)
 {
@@ -78,9 +111,15 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
     __shared__ unsigned s_id[FE_THREADS];   // Gaussian index of each slot
     __shared__ unsigned s_cnt[FE_THREADS];  // entries of each slot's Gaussian
     __shared__ unsigned long long s_base;
+    // digit counts of the block's entries for the entry sort (8-bit digits of the
+    // tile id): pass 0 as a difference array over the digits (tile rows are runs of
+    // consecutive tiles), pass 1 as plain counts
+    __shared__ unsigned s_d0[RADIX_FE + 1], s_h1[RADIX_FE];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
+    if (a.hist_passes)
+        for (int j = tid; j < 2 * RADIX_FE + 1; j += FE_THREADS) (j <= RADIX_FE ? s_d0[j] : s_h1[j - RADIX_FE - 1]) = 0u;
     __syncthreads();
     const unsigned vb = s_vb;
     const long long slot = (long long)vb * FE_THREADS + tid;
@@ -171,9 +210,14 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
         const unsigned rl = k - __shfl_sync(0xffffffffu, rexcl, owner);
         unsigned w = 0;
         int txa, txb;
-        if (k < wrows && row_range(s_rt[warp * 32 + owner], s_rt[warp * 32 + owner].ty0 + (int)rl, a.cam.tw_log2, a.cam.th, txa, txb))
+        const int ty = k < wrows ? s_rt[warp * 32 + owner].ty0 + (int)rl : 0;
+        if (k < wrows && row_range(s_rt[warp * 32 + owner], ty, a.cam.tw_log2, a.cam.th, txa, txb))
             w = (unsigned)(txb - txa + 1);
-        if (w) atomicAdd(&s_cnt[warp * 32 + owner], w);
+        if (w) {
+            atomicAdd(&s_cnt[warp * 32 + owner], w);
+            if (a.hist_passes)
+                count_tile_digits(s_d0, s_h1, a.hist_passes, (unsigned)ty * (unsigned)a.lay.tiles_x + (unsigned)txa, w);
+        }
     }
     __syncwarp();
     const unsigned cnt = s_cnt[tid];
@@ -264,6 +308,31 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
             }
         }
         out += chunk;
+    }
+
+    // The block's digit counts (complete since the barriers after the count
+    // loop) go to one copy of the frame's histograms: the last warp turns the
+    // difference array into counts, 8 digits per lane.
+    if (a.hist_passes && warp == FE_WARPS - 1) {
+        unsigned* const H = a.hist + (size_t)(vb % FE_HIST_COPIES) * (2 * RADIX_FE);
+        unsigned c[8], run = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            run += s_d0[8 * lane + j];
+            c[j] = run;
+        }
+        const unsigned incl = warp_inclusive_scan(run, lane);
+        const unsigned before = incl - run;
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if (c[j] + before) atomicAdd(&H[8 * lane + j], c[j] + before);
+        if (a.hist_passes > 1) {
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const unsigned v = s_h1[8 * lane + j];
+                if (v) atomicAdd(&H[RADIX_FE + 8 * lane + j], v);
+            }
+        }
     }
 }
 

@@ -305,6 +305,14 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
             // depth-ordered entries of one Gaussian row carry consecutive tiles, so the warp
             // holds many distinct low tile digits: rank that pass with ballots
             sa.ballot_mask = 1;
+            // up to 2 tile-bit passes (b_t <= 16): the front end counts the digits of its
+            // entries per tile row, and the sort's histogram pass only runs on overflow
+            if (sa.passes <= 2) {
+                a.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + 2 * CTRL_BYTES);
+                a.hist_passes = sa.passes;
+                sa.hist_copies = a.hist;
+                sa.hist_pre = hist + 4 * 256; // rows 4-5 of the frame's [8][256] histograms
+            }
         }
         {
             NvtxScope r_("rg front end");

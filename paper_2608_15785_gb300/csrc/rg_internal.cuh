@@ -362,6 +362,10 @@ __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f),
 // ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files).
 // ---------------------------------------------------------------------------
+// The front end's blocks add their digit counts to one of these copies (block id
+// modulo the count): the atomics spread over many L2 lines instead of 512 words.
+constexpr int FE_HIST_COPIES = 16;
+
 struct FrontendArgs {
     const unsigned* order; // [N] Gaussian processed by thread slot i (depth order), or null (index order)
     const float4* geoA;    // [N] (mean.xyz, log o)
@@ -380,6 +384,8 @@ struct FrontendArgs {
     unsigned long long* status; // [ceil(N/256)]
     Counters* ctr;
     Sticky* sticky;
+    unsigned* hist;             // [FE_HIST_COPIES][2][256] digit counts of the tile field, or null
+    int hist_passes;            // 0, 1 or 2: 8-bit digits of the tile id counted (b_t <= 16)
 };
 void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s);
 // threads per block of the fused front end (one look-back status word per block)
@@ -425,6 +431,8 @@ struct SortArgs {
     int bit0;             // lowest key bit sorted (digit p = bits bit0 + 8p ..)
     int ballot_mask;      // bit p: rank pass p with ballots instead of match_any
     unsigned* hist;       // [8][256]
+    unsigned* hist_pre;   // [passes][256] digit counts from the producer of the keys, or null
+    const unsigned* hist_copies; // [FE_HIST_COPIES][2][256] the producer's partial counts (summed into hist_pre)
     unsigned* status[2];  // [max_tiles][256] look-back status per pass (alternating)
     long long max_tiles;
     Counters* ctr;

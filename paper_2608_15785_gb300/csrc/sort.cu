@@ -7,7 +7,9 @@
 // the bits that can be non-zero are sorted).
 //
 // One histogram kernel reads every key once and counts the digits of all
-// passes. Each pass is then ONE kernel over tiles of 6144 (32-bit keys) or
+// passes, unless the producer of the keys counted them (the RoofGS front end
+// counts the tile digits of its entries per tile row; the kernel then only
+// clears look-back state, and counts if entries overflowed). Each pass is then ONE kernel over tiles of 6144 (32-bit keys) or
 // 4096 (64-bit keys) entries (one-sweep scheme): a persistent grid takes tiles
 // in order from an atomic counter, ranks the tile's digits per warp (match_any,
 // or one ballot per digit bit where warps hold many distinct digits; stable),
@@ -66,12 +68,25 @@ static int sm_count()
     return sms;
 }
 
+// The producer's digit counts cover every entry it made; they are not used when
+// entries did not fit (overflow) or its allocation gave up waiting (the error bit
+// of its look-back): the histogram kernel then counts the stored keys. Both flags
+// are final before the sort starts.
+__device__ __forceinline__ bool recount_digits(const Counters* ctr)
+{
+    return ctr->overflow != 0u || (ctr->error & ERR_FE_LOOKBACK) != 0u;
+}
+
 // Digit histograms of every pass in one read of the keys (vector loads; the
 // counts of equal digits within a warp are combined before the shared atomic).
+// When the producer of the keys counted the digits already (only_on_overflow),
+// this kernel clears the first pass's look-back status and counts only when
+// recount_digits() says so.
 template <typename K>
 __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ keys, int passes, int bit0,
                                                          unsigned* hist, unsigned* status0,
-                                                         const Counters* __restrict__ ctr)
+                                                         const Counters* __restrict__ ctr, unsigned* hist_pre,
+                                                         const unsigned* __restrict__ hist_copies)
 {
     __shared__ unsigned s_h[8][RADIX];
     for (int j = threadIdx.x; j < 8 * RADIX; j += H_THREADS) (&s_h[0][0])[j] = 0u;
@@ -83,6 +98,15 @@ __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ k
     const long long gid = (long long)blockIdx.x * H_THREADS + threadIdx.x;
     // clear the look-back status words of the first pass
     for (long long j = gid; j < ntiles * RADIX; j += gsz) status0[j] = 0u;
+    if (hist_pre && !recount_digits(ctr)) {
+        // the producer's counts: sum its copies, one digit of one pass per thread
+        for (long long c = gid; c < (long long)passes * RADIX; c += gsz) {
+            unsigned sum = 0u;
+            for (int j = 0; j < FE_HIST_COPIES; j++) sum += hist_copies[(size_t)j * 2 * RADIX + c];
+            hist_pre[c] = sum;
+        }
+        return;
+    }
     constexpr int V = 16 / sizeof(K); // keys per 16-byte load
     const long long nv = n / V;
     // consecutive keys often share digits (entries of one Gaussian): runs of equal
@@ -170,7 +194,7 @@ template <typename K>
 __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k_onesweep(const K* __restrict__ kin, const unsigned* __restrict__ vin,
                                                         K* __restrict__ kout, unsigned* __restrict__ vout, int pass,
                                                         int bit0, int ballot_rank, const unsigned* __restrict__ hist,
-                                                        unsigned* status,
+                                                        const unsigned* __restrict__ hist_pre, unsigned* status,
                                                         unsigned* status_next, Counters* ctr, Sticky* sticky)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -183,7 +207,8 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
     const unsigned n = ctr->n_entries;
     const unsigned ntiles = (n + S_TILE - 1) / S_TILE;
     {
-        const unsigned h = tid < RADIX ? hist[pass * RADIX + tid] : 0u;
+        const unsigned* H = (hist_pre && !recount_digits(ctr)) ? hist_pre : hist;
+        const unsigned h = tid < RADIX ? H[pass * RADIX + tid] : 0u;
         const unsigned e = digit_exclusive_scan(h, S.scan);
         if (tid < RADIX) S.goff[tid] = e;
     }
@@ -376,13 +401,15 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
     const int hist_grid = 8 * sm_count();
     const K* kin = (const K*)a.keys[0];
     if (a.passes <= 0) return;
-    k_sort_hist<K><<<hist_grid, H_THREADS, 0, s>>>(kin, a.passes, a.bit0, a.hist, a.status[0], a.ctr);
+    k_sort_hist<K><<<hist_grid, H_THREADS, 0, s>>>(kin, a.passes, a.bit0, a.hist, a.status[0], a.ctr, a.hist_pre,
+                                                   a.hist_copies);
     if (ev_after_hist) cudaEventRecord(ev_after_hist, s);
     for (int p = 0; p < a.passes; p++) {
         const int src = p & 1, dst = src ^ 1;
         unsigned* nxt = (p + 1 < a.passes) ? a.status[(p + 1) & 1] : nullptr;
         k_onesweep<K><<<grid, SortCfg<K>::THREADS, smem, s>>>((const K*)a.keys[src], a.vals[src], (K*)a.keys[dst], a.vals[dst], p,
-                                                    a.bit0, (a.ballot_mask >> p) & 1, a.hist, a.status[p & 1], nxt,
+                                                    a.bit0, (a.ballot_mask >> p) & 1, a.hist, a.hist_pre,
+                                                    a.status[p & 1], nxt,
                                                     a.ctr, a.sticky);
     }
 }

@@ -320,6 +320,17 @@ def test_capacity_overflow_regrows_and_is_reported():
     # asynchronous render: image incomplete, overflow recorded
     small.render(cam)
     torch.cuda.synchronize()
+    # the sort covers the entries that fit, i.e. the first ones the front end emitted
+    # (Gaussians in (depth code, index) order, each one's tiles ascending): its digit
+    # counts are taken from the stored keys, not from the front end's count of all
+    gk = small.inspect(binding.RG_INSPECT_KEYS).view(np.uint32).astype(np.uint64)
+    gv = small.inspect(binding.RG_INSPECT_VALUES)
+    k, v, _, _ = oracle.keys(sc, cam, oracle.ROOFGS, comp=oracle.compact(sc))
+    b_d = np.uint64(oracle.layout(cam)["b_d"])
+    assert 0 < gk.size < k.size
+    emitted = np.lexsort((k >> b_d, v, k & ((np.uint64(1) << b_d) - np.uint64(1))))[: gk.size]
+    expect = emitted[np.lexsort((v[emitted], k[emitted]))]
+    assert np.array_equal(gk, k[expect]) and np.array_equal(gv, v[expect])
     with pytest.raises(binding.RgError) as e:
         small.check()
     assert e.value.status == 4
