@@ -82,13 +82,6 @@ __device__ __forceinline__ void count_tile_digits(unsigned* s_d0, unsigned* s_h1
     }
 }
 
-__device__ __forceinline__ unsigned warp_sum(unsigned x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
 __device__ __forceinline__ unsigned warp_inclusive_scan(unsigned x, int lane)
 {
 #pragma unroll

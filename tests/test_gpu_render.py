@@ -469,6 +469,29 @@ def test_tile_shapes_bit_exact_keys_and_images(tile, mode):
         gs.check()
 
 
+@pytest.mark.parametrize("wh,tile", [((8000, 128), (16, 16)), ((4000, 128), (8, 32))])
+def test_tile_rows_wider_than_256_tiles(wh, tile):
+    """Wide, flat Gaussians whose tile rows span more than 256 tiles: the front end's count of the
+    sort's low tile digit then takes full cycles of 256 besides runs that wrap past digit 255 (500
+    tiles per row: rows start at different low digits). Keys, values and ranges bit-exact against
+    the oracle (a wrong digit count misplaces entries)."""
+    base = small_random_scene(3000, seed=11, spread=1.0)
+    wide = single_scene(means=[[0.0, 0.0, 0.0], [0.4, 0.0, 0.5], [-0.3, 0.0, -0.5]],
+                        scales=[[1.2, 0.02, 0.02], [2.0, 0.03, 0.02], [0.8, 0.01, 0.05]],
+                        quats=[[1.0, 0.0, 0.0, 0.0]] * 3, opac=[0.9, 0.6, 0.95], dc=[[0.8, 0.2, 0.1]] * 3)
+    sc = synth.Scene(*(np.concatenate([getattr(base, f), getattr(wide, f)])
+                       for f in ("means", "scales", "quats", "opacities", "sh")))
+    cam = synth.tiny_camera(*wh)
+    gs = gpu_scene(sc)
+    comp = oracle.compact(sc)
+    _, st = render(gs, cam, "roofgs", stats=True, tile=tile)
+    assert st["sort_passes"] == 2  # the front end counts the digits of both passes
+    bins = oracle.keys(sc, cam, oracle.ROOFGS, comp=comp, tile=tile)[3]
+    assert (bins[-3:, 0] == 1).all() and (bins[-3:, 3] - bins[-3:, 1] + 1 > 256).all()
+    assert st["n_entries"] == _keys_equal(gs, sc, cam, oracle.ROOFGS, comp, tile=tile)
+    gs.check()
+
+
 def test_unsupported_tile_shape_is_rejected():
     sc, cams = synth.workload("tiny_256")
     gs = gpu_scene(sc)
