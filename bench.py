@@ -49,10 +49,10 @@ REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_powe
 #     + 3 FFMA + T update = 20.
 OPS = {"roofgs": (5, 11), "exact": (10, 20)}
 STAGES = ["depth_order", "front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"]
-# DRAM bytes per entry of one tile-bit one-sweep pass: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the tile-bit passes on the 1M-Gaussian 4K case
-# (220.2 + 173.2 MB and 220.0 + 169.0 MB for 27.03 M entries), scaled by the entries of the launch
-SORT_PASS_TRAFFIC_PER_ENTRY = 14.5
+# DRAM bytes per entry of one tile-bit one-sweep pass (16-bit tile ids + 32-bit values): ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of the tile-bit passes on the 1M-Gaussian 4K case,
+# scaled by the entries of the launch; None until measured for the current kernel
+SORT_PASS_TRAFFIC_PER_ENTRY = None
 
 
 def parse():
@@ -156,10 +156,13 @@ def stage_work(mode, st, W, H):
         # sort of those N pairs (4 B histogram + 16 B per pass)
         gpasses = (st["b_d"] + 7) // 8
         depth = 24 * N + (4 + 16 * gpasses) * N
+        # up to 2 tile-bit passes: entries carry a 16-bit tile id and a 32-bit value (6 B), else a
+        # 32-bit key and a 32-bit value (8 B)
+        entry = 6 if passes <= 2 else 8
         # fused front end: 4 B order + 16 B mean+log o per Gaussian, 16 B FP16 geometry if inside the
-        # depth/opacity range, 48 B INT8 SH + 32 B record if visible, 8 B key+value per entry
-        front = 20 * N + 16 * nf + 80 * nv + 8 * nd
-        sort_pass = 16 * nd  # one pass: each (key, value) entry read once and written once
+        # depth/opacity range, 48 B INT8 SH + 32 B record if visible, one entry per entry
+        front = 20 * N + 16 * nf + 80 * nv + entry * nd
+        sort_pass = 2 * entry * nd  # one pass: each entry read once and written once
         if passes <= 2:
             # the front end counted the tile digits: the histogram kernel clears the first pass's
             # look-back status (1 KB per 6144-entry tile) and sums the front end's 16 copies of the
@@ -641,7 +644,7 @@ def rooflines(r, a, props, clocks):
     traffic = None
     if dom == "sort_pass" and SORT_PASS_TRAFFIC_PER_ENTRY:
         traffic = round(SORT_PASS_TRAFFIC_PER_ENTRY * st["n_entries"])
-    names = {"sort_pass": "k_onesweep<uint32> (one tile-bit pass)",
+    names = {"sort_pass": "k_onesweep<uint16 tile id> (one tile-bit pass)",
              "raster": "k_raster_roofgs<fast exp, %d pixels per thread>" % a.ppt,
              "front_end": "k_frontend_fused", "depth_order": "k_depth_keys + per-Gaussian sort",
              "sort_hist": "k_sort_hist<uint32>", "ranges": "k_ranges<uint32>"}

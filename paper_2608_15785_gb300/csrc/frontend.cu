@@ -284,8 +284,10 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
         // entries at or past the capacity are counted but not written
         const bool fits = out < (unsigned long long)a.cap;
         const unsigned room = fits ? (unsigned)((unsigned long long)a.cap - out) : 0u;
-        unsigned* const kp = a.keys + (fits ? out : 0ull);
-        unsigned* const vp = a.vals + (fits ? out : 0ull);
+        const unsigned long long o = fits ? out : 0ull;
+        unsigned* const kp = a.keys + o;
+        unsigned short* const kp16 = a.keys16 ? a.keys16 + o : nullptr;
+        unsigned* const vp = a.vals + o;
         for (unsigned e0 = 0; e0 < chunk; e0 += 32) {
             const unsigned e = e0 + (unsigned)lane;
             int pos = 0; // row (lane) of entry e
@@ -296,7 +298,8 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
             const unsigned qe = __shfl_sync(0xffffffffu, q, pos);
             const unsigned ide = __shfl_sync(0xffffffffu, id, pos);
             if (e < chunk && e < room) {
-                kp[e] = (b_d >= 32) ? qe : ((tile << b_d) | qe);
+                if (a.keys16) kp16[e] = (unsigned short)tile;
+                else kp[e] = (b_d >= 32) ? qe : ((tile << b_d) | qe);
                 vp[e] = ide;
             }
         }

@@ -83,8 +83,9 @@ __device__ __forceinline__ void flush_counts(Counters* c, unsigned n_eval, unsig
 // First index i in [0, n) with (keys[i] >> shift) >= t, n if none (keys sorted): a
 // 33-ary search by one warp, each round 32 lanes probe and one ballot keeps the part
 // that holds the boundary (six dependent loads for 68 M keys). Warp-uniform result.
-__device__ __forceinline__ unsigned warp_lower_bound(const unsigned* __restrict__ keys, unsigned n, int shift,
-                                                     unsigned t)
+// K: 32-bit keys or 16-bit tile ids.
+template <typename K>
+__device__ __forceinline__ unsigned warp_lower_bound(const K* __restrict__ keys, unsigned n, int shift, unsigned t)
 {
     const int lane = threadIdx.x & 31;
     unsigned lo = 0, hi = n; // the answer lies in [lo, hi]
@@ -131,11 +132,13 @@ __global__ void __launch_bounds__(256 / PPT) k_raster_roofgs(RasterArgs a)
     const float xx = x * x, xy = x * y, yy = y * y, y2p1 = 2.0f * y + 1.0f;
     unsigned n_eval = 0, n_blend = 0;
     uint2 range;
-    if (a.skeys) { // warps 0 and 1 search the first entries of tiles `tile` and `tile + 1`
+    if (a.skeys || a.skeys16) { // warps 0 and 1 search the first entries of tiles `tile` and `tile + 1`
         __shared__ unsigned s_bound[2];
         const int warp = t >> 5;
         if (warp < 2) {
-            const unsigned b = warp_lower_bound(a.skeys, a.ctr->n_entries, a.tile_shift, (unsigned)(tile + warp));
+            const unsigned n = a.ctr->n_entries;
+            const unsigned b = a.skeys16 ? warp_lower_bound(a.skeys16, n, 0, (unsigned)(tile + warp))
+                                         : warp_lower_bound(a.skeys, n, a.tile_shift, (unsigned)(tile + warp));
             if ((t & 31) == 0) s_bound[warp] = b;
         }
         __syncthreads();

@@ -187,6 +187,7 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     // RoofGS frames that rasterize find each tile's range inside the rasterizer (a search of
     // the sorted keys per tile block); the others run the ranges pass
     const bool search_ranges = mode == RG_MODE_ROOFGS && out != nullptr;
+    w.last_key16 = false;
     RG_CK(cudaMemsetAsync(w.ctrl.p, 0, CTRL_ALLOC, st));
     if (flags & RG_FLAG_TEST_STALL_SORT) { // tile 0 of the first entry-sort pass is never claimed
         k_set_word<<<1, 1, 0, st>>>(&ctr->sort_tile_ctr[0], 1u);
@@ -306,19 +307,27 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
             // holds many distinct low tile digits: rank that pass with ballots
             sa.ballot_mask = 1;
             // up to 2 tile-bit passes (b_t <= 16): the front end counts the digits of its
-            // entries per tile row, and the sort's histogram pass only runs on overflow
+            // entries per tile row, and the sort's histogram pass only runs on overflow;
+            // the entries carry the 16-bit tile id alone (the depth code of a 32-bit key
+            // follows from the value: entries stay in depth order within a tile)
             if (sa.passes <= 2) {
                 a.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + 2 * CTRL_BYTES);
                 a.hist_passes = sa.passes;
                 sa.hist_copies = a.hist;
                 sa.hist_pre = hist + 4 * 256; // rows 4-5 of the frame's [8][256] histograms
+                a.keys16 = w.keys[0].as<unsigned short>();
+                sa.key_bytes = 2;
+                sa.bit0 = 0;
             }
+            w.last_gfin = ga.passes & 1;
         }
         {
             NvtxScope r_("rg front end");
             launch_frontend_fused(a, st);
         }
-        tile_shift = F.lay.b_d;
+        tile_shift = a.keys16 ? 0 : F.lay.b_d;
+        w.last_key16 = a.keys16 != nullptr;
+        w.last_bd = F.lay.b_d;
     }
     if (ev) RG_CK(cudaEventRecord(E[2], st));
     if (ev && sa.passes <= 0) RG_CK(cudaEventRecord(E[3], st));
@@ -366,7 +375,8 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         launch_raster_exact(r, st);
     } else {
         r.rec = w.rec.as<float4>();
-        r.skeys = w.keys[fin].as<unsigned>();
+        if (w.last_key16) r.skeys16 = w.keys[fin].as<unsigned short>();
+        else r.skeys = w.keys[fin].as<unsigned>();
         r.tile_shift = tile_shift;
         r.ranges_out = w.ranges.as<uint2>();
         r.ctr = ctr;
@@ -792,7 +802,33 @@ rg_status rg_inspect(rg_scene* s, int32_t what, void* host_dst, int64_t cap_byte
         Counters c;
         RG_CK(cudaMemcpy(&c, s->ws.ctrl.p, sizeof(c), cudaMemcpyDeviceToHost));
         const int fin = s->ws.last_passes & 1;
-        if (what == RG_INSPECT_KEYS) {
+        if (what == RG_INSPECT_KEYS && s->ws.last_key16) {
+            // the entries carried 16-bit tile ids: each 32-bit key (tile << b_d | q_d) is rebuilt
+            // from the tile and the depth code of its Gaussian (the per-Gaussian depth sort's result)
+            const size_t ne = c.n_entries, ng = (size_t)n;
+            std::vector<uint16_t> t16(ne);
+            std::vector<uint32_t> val(ne), gq(ng), gi(ng), q(ng, 0u);
+            if (ne) {
+                RG_CK(cudaMemcpy(t16.data(), s->ws.keys[fin].p, ne * 2, cudaMemcpyDeviceToHost));
+                RG_CK(cudaMemcpy(val.data(), s->ws.vals[fin].p, ne * 4, cudaMemcpyDeviceToHost));
+            }
+            if (ng) {
+                RG_CK(cudaMemcpy(gq.data(), s->ws.gkeys[s->ws.last_gfin].p, ng * 4, cudaMemcpyDeviceToHost));
+                RG_CK(cudaMemcpy(gi.data(), s->ws.gvals[s->ws.last_gfin].p, ng * 4, cudaMemcpyDeviceToHost));
+            }
+            for (size_t k = 0; k < ng; k++)
+                if (gi[k] < ng) q[gi[k]] = gq[k];
+            const int bd = s->ws.last_bd;
+            tmp.resize(ne * 4);
+            for (size_t j = 0; j < ne; j++) {
+                const uint32_t qd = val[j] < ng ? q[val[j]] : 0u;
+                const uint32_t key = bd >= 32 ? qd : (((uint32_t)t16[j] << bd) | qd);
+                memcpy(&tmp[j * 4], &key, 4);
+            }
+            src = tmp.data();
+            device_src = false;
+            bytes = (int64_t)ne * 4;
+        } else if (what == RG_INSPECT_KEYS) {
             src = s->ws.keys[fin].p;
             bytes = (int64_t)c.n_entries * (s->ws.last_mode == RG_MODE_EXACT ? 8 : 4);
         } else if (what == RG_INSPECT_VALUES) {

@@ -68,6 +68,9 @@ struct Workspace {
     int last_mode = -1;
     int last_passes = 0;
     int last_tiles = 0;
+    bool last_key16 = false; // entries carried 16-bit tile ids (the 32-bit keys are rebuilt on inspection)
+    int last_bd = 0;         // b_d of the last RoofGS frame
+    int last_gfin = 0;       // buffer of the per-Gaussian depth sort's result
     // stage events
     bool ev_init = false;
     cudaEvent_t ev[EV_RING][EV_PER_FRAME];

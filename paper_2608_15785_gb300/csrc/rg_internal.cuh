@@ -378,7 +378,9 @@ struct FrontendArgs {
     CamDev cam;
     Layout lay;
     float4* rec;           // [N][2] raster record
-    unsigned* keys;        // [cap]
+    unsigned* keys;        // [cap] 32-bit keys (tile << b_d | q_d), unless keys16 is set
+    unsigned short* keys16; // [cap] or null: the tile id alone (b_t <= 16; the entries come out in
+                            // depth order, so the 32-bit key follows from the tile and the value)
     unsigned* vals;        // [cap]
     long long cap;
     unsigned long long* status; // [ceil(N/256)]
@@ -426,7 +428,7 @@ struct SortArgs {
     void* keys[2];        // ping-pong key buffers (uint32 or uint64)
     unsigned* vals[2];
     long long cap;
-    int key_bytes;        // 4 or 8
+    int key_bytes;        // 2 (16-bit tile ids), 4 or 8
     int passes;           // 8-bit digits
     int bit0;             // lowest key bit sorted (digit p = bits bit0 + 8p ..)
     int ballot_mask;      // bit p: rank pass p with ballots instead of match_any
@@ -457,6 +459,7 @@ struct RasterArgs {
     // (tile id = key >> tile_shift, n_entries from the counters) and writes it to
     // ranges_out; `ranges` is then unused
     const unsigned* skeys;
+    const unsigned short* skeys16; // instead of skeys: 16-bit tile ids (tile_shift 0)
     int tile_shift;
     uint2* ranges_out;
     const Counters* ctr;  // frame counters (n_entries) for the search
