@@ -217,7 +217,10 @@ rg_status rg_scene_check(rg_scene* scene, void* stream);
 rg_status rg_stage_times(rg_scene* scene, float* ms7, int32_t* frames);
 
 /* rg_inspect selectors: copy internal buffers of the last frame to host memory */
-#define RG_INSPECT_KEYS 1        /* sorted keys: uint32 (RoofGS) or uint64 (exact), n_entries of them */
+#define RG_INSPECT_KEYS 1        /* sorted keys: uint32 (RoofGS) or uint64 (exact), n_entries of them;
+                                    RoofGS frames with at most 16 tile bits sort 16-bit tile ids and
+                                    the 32-bit keys (tile << b_d | q_d) are rebuilt on the host from
+                                    the values and the per-Gaussian depth codes */
 #define RG_INSPECT_VALUES 2      /* sorted values: uint32 Gaussian indices */
 #define RG_INSPECT_RANGES 3      /* uint32 [tiles][2] = [start, end) per tile */
 #define RG_INSPECT_SH_CODES 4    /* int8 [n][16][3] compact SH codes */
