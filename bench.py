@@ -152,10 +152,10 @@ def stage_work(mode, st, W, H):
     tiles = st["tiles_x"] * st["tiles_y"]
     passes = st["sort_passes"]
     if mode == "roofgs":
-        # depth order: 16 B mean+log o read, 8 B (q_d, index) written per Gaussian, then the stable
-        # sort of those N pairs (4 B histogram + 16 B per pass)
+        # depth order: 16 B mean+log o read, 8 B (q_d, index) written per Gaussian (digits counted on
+        # the way), then the stable sort of those N pairs (16 B per pass)
         gpasses = (st["b_d"] + 7) // 8
-        depth = 24 * N + (4 + 16 * gpasses) * N
+        depth = 24 * N + 16 * gpasses * N
         # up to 2 tile-bit passes: entries carry a 16-bit tile id and a 32-bit value (6 B), else a
         # 32-bit key and a 32-bit value (8 B)
         entry = 6 if passes <= 2 else 8

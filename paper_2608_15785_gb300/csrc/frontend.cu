@@ -332,22 +332,45 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
     }
 }
 
-__global__ void __launch_bounds__(256) k_depth_keys(FrontendArgs a, unsigned* keys, unsigned* vals, Counters* ctr)
+// Grid-stride over the Gaussians; each block also counts the 8-bit digits of its
+// keys for the depth sort's passes in shared memory and adds them to `hist`
+// ([passes][256], zeroed beforehand) once at the end.
+__global__ void __launch_bounds__(256) k_depth_keys(FrontendArgs a, unsigned* keys, unsigned* vals, Counters* ctr,
+                                                    unsigned* hist, int passes)
 {
-    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
-    if (i == 0) ctr->n_entries = (unsigned)a.n;
-    if (i >= a.n) return;
-    const float4 ga = __ldg(&a.geoA[i]);
-    const float pz = view_z(a.cam, ga.x, ga.y, ga.z);
-    const bool front = pz > a.cam.zn && pz <= a.cam.zf && ga.w >= -LN255F;
-    keys[i] = front ? quantize_depth(pz, a.cam.zn, a.lay) : a.lay.qmax;
-    vals[i] = (unsigned)i;
+    __shared__ unsigned s_h[4][256];
+    for (int j = threadIdx.x; j < 4 * 256; j += 256) (&s_h[0][0])[j] = 0u;
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_entries = (unsigned)a.n;
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < a.n; i += (long long)gridDim.x * 256) {
+        const float4 ga = __ldg(&a.geoA[i]);
+        const float pz = view_z(a.cam, ga.x, ga.y, ga.z);
+        const bool front = pz > a.cam.zn && pz <= a.cam.zf && ga.w >= -LN255F;
+        const unsigned q = front ? quantize_depth(pz, a.cam.zn, a.lay) : a.lay.qmax;
+        keys[i] = q;
+        vals[i] = (unsigned)i;
+        for (int p = 0; p < passes; p++) atomicAdd(&s_h[p][(q >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < passes * 256; j += 256) {
+        const unsigned c = (&s_h[0][0])[j];
+        if (c) atomicAdd(&hist[j], c);
+    }
 }
 
-void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, cudaStream_t s)
+void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, unsigned* hist,
+                       int passes, cudaStream_t s)
 {
-    const unsigned blocks = (unsigned)((a.n + 255) / 256);
-    k_depth_keys<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(a, keys, vals, ctr);
+    static int grid_cap = 0;
+    if (grid_cap == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid_cap = 8 * (sms > 0 ? sms : 1);
+    }
+    const long long need = (a.n + 255) / 256;
+    const unsigned blocks = (unsigned)(need < 1 ? 1 : (need < grid_cap ? need : grid_cap));
+    k_depth_keys<<<blocks, 256, 0, s>>>(a, keys, vals, ctr, hist, passes);
 }
 
 int frontend_block_threads() { return FE_THREADS; }

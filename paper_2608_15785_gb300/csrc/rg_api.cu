@@ -296,7 +296,10 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
             ga.sticky = sticky;
             {
                 NvtxScope r_("rg depth order");
-                launch_depth_keys(a, w.gkeys[0].as<unsigned>(), w.gvals[0].as<unsigned>(), gctr, st);
+                // the depth keys' digits are counted as they are written (ga.passes <= 4)
+                ga.hist_pre = ga.hist;
+                launch_depth_keys(a, w.gkeys[0].as<unsigned>(), w.gvals[0].as<unsigned>(), gctr, ga.hist, ga.passes,
+                                  st);
                 launch_sort(ga, st, nullptr);
             }
             a.order = w.gvals[ga.passes & 1].as<unsigned>();

@@ -393,8 +393,10 @@ void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s);
 // threads per block of the fused front end (one look-back status word per block)
 int frontend_block_threads();
 // quantized depth (Eq. (9)) of every Gaussian as a sort key, Gaussian index as value;
-// culled Gaussians get 2^b_d - 1 (the fused front end skips them); writes n to ctr
-void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, cudaStream_t s);
+// culled Gaussians get 2^b_d - 1 (the fused front end skips them); writes n to ctr and
+// adds the keys' 8-bit digit counts of `passes` (<= 4) passes to hist [passes][256]
+void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, unsigned* hist,
+                       int passes, cudaStream_t s);
 
 struct ExactArgs {
     const float* means;
@@ -434,7 +436,8 @@ struct SortArgs {
     int ballot_mask;      // bit p: rank pass p with ballots instead of match_any
     unsigned* hist;       // [8][256]
     unsigned* hist_pre;   // [passes][256] digit counts from the producer of the keys, or null
-    const unsigned* hist_copies; // [FE_HIST_COPIES][2][256] the producer's partial counts (summed into hist_pre)
+    const unsigned* hist_copies; // [FE_HIST_COPIES][2][256] the producer's partial counts (summed into
+                                 // hist_pre), or null if hist_pre is complete already
     unsigned* status[2];  // [max_tiles][256] look-back status per pass (alternating)
     long long max_tiles;
     Counters* ctr;

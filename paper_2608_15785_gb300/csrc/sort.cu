@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ k
     // clear the look-back status words of the first pass
     for (long long j = gid; j < ntiles * RADIX; j += gsz) status0[j] = 0u;
     if (hist_pre && !recount_digits(ctr)) {
-        // the producer's counts: sum its copies, one digit of one pass per thread
+        // the producer's counts: complete, or sum its copies (one digit of one pass per thread)
+        if (!hist_copies) return;
         for (long long c = gid; c < (long long)passes * RADIX; c += gsz) {
             unsigned sum = 0u;
             for (int j = 0; j < FE_HIST_COPIES; j++) sum += hist_copies[(size_t)j * 2 * RADIX + c];
