@@ -9,14 +9,14 @@
 //    row), keep per row only the tiles the ellipse reaches, and count entries;
 //    the block allocates its entries with one shared-memory prefix sum and one
 //    device-wide slot (decoupled look-back, ordered by block, so equal keys stay
-//    in Gaussian order) and writes the (key, value) array cooperatively:
-//    consecutive lanes write consecutive entries (coalesced), whichever
+//    in Gaussian order) and writes the (key or 16-bit tile id, value) array
+//    cooperatively: consecutive lanes write consecutive entries (coalesced), whichever
 //    Gaussian and row they belong to. Only the raster record and the key-value
 //    array go to global memory, besides the digit counts of the entry sort
 //    (each tile row is a run of consecutive tile ids; counted per block in
 //    shared memory, added to one of a few global copies).
 //  * k_depth_keys: quantized depth and index of every Gaussian, the input of
-//    the per-Gaussian depth sort.
+//    the per-Gaussian depth sort, and the digit counts of that sort.
 //  * k_exact_*: the plain 3DGS front end (preprocess -> scan -> duplicate,
 //    Sec. II-A), 64-bit keys of 32-bit tile id | 32-bit float depth.
 //  * scene conversion: finite-value check, per-(degree, channel) max |SH|,

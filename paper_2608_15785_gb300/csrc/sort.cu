@@ -3,14 +3,17 @@
 // Depth sort of Sec. III-C / Sec. IV-A.2: traffic ~ S_kv * N_dup * N_pass
 // (Eq. (6)). 8-bit digits; 4 passes for the 32-bit RoofGS key (or only the
 // ceil(b_t / 8) tile-bit passes when the Gaussians were put in depth order
-// first) and ceil((32 + b_t) / 8) passes for the 64-bit exact-mode key (only
-// the bits that can be non-zero are sorted).
+// first: then, with b_t <= 16, the entries carry the 16-bit tile id alone) and
+// ceil((32 + b_t) / 8) passes for the 64-bit exact-mode key (only the bits
+// that can be non-zero are sorted).
 //
 // One histogram kernel reads every key once and counts the digits of all
-// passes, unless the producer of the keys counted them (the RoofGS front end
-// counts the tile digits of its entries per tile row; the kernel then only
-// clears look-back state, and counts if entries overflowed). Each pass is then ONE kernel over tiles of 6144 (32-bit keys) or
-// 4096 (64-bit keys) entries (one-sweep scheme): a persistent grid takes tiles
+// passes, unless the producer of the keys counted them (the depth-key kernel
+// counts its codes' digits; the RoofGS front end counts the tile digits of its
+// entries per tile row; the kernel then only clears look-back state, and counts
+// if entries overflowed). Each pass is then ONE kernel over tiles of 6144
+// (16- and 32-bit keys) or 4096 (64-bit keys) entries (one-sweep scheme): a
+// persistent grid takes tiles
 // in order from an atomic counter, ranks the tile's digits per warp (match_any,
 // or one ballot per digit bit where warps hold many distinct digits; stable),
 // publishes its per-digit counts, obtains the counts of all earlier tiles by
@@ -28,7 +31,8 @@ namespace rg {
 // Larger tiles amortise the per-tile barriers and look-back; two resident blocks
 // per SM keep one block's loads in flight while the other waits at a barrier.
 // 32-bit keys: 384 x 16 = 6144 entries at 80 registers; 64-bit keys: 512 x 8 =
-// 4096 entries at 64 registers (16 keys of 64 bits would spill).
+// 4096 entries at 64 registers (16 keys of 64 bits would spill); 16-bit tile
+// ids: 256 x 24 = 6144 entries, three blocks per SM (below).
 template <typename K>
 struct SortCfg;
 #ifndef RG_SORT_T32
