@@ -85,6 +85,7 @@ typedef struct {
     double u, v, z;
     double a, b, c;           /* paper's (a, b, c): q = a dx^2 + b dx dy + c dy^2 */
     double s00, s01, s11;     /* EWA covariance Sigma' incl. 0.3 I */
+    double gg;                /* exact mode: product of the natural row sizes of U (see below) */
     double op;                /* opacity o (exact) or log o (RoofGS) */
     double rgb[3];
 } orc_g64;
@@ -383,6 +384,30 @@ void orc_project64(const float* mf, const float* qf, const float* sf, const orc_
     out[9] = det;
 }
 
+/*
+ * Rounding scale of a single-precision evaluation of the 2x3 factor
+ * U = J W Q diag(s) of Sigma' - 0.3 I = U U^T (test tolerance only, not part of
+ * the render): each entry of row r is a sum of products whose magnitudes are
+ * bounded by |J_r| max(s), so an FP32 evaluation errs by a few units in the
+ * last place of that size, whatever cancellation the sum has. Returns
+ * |J_0| |J_1| max(s)^2.
+ */
+static double u_rows_scale(const float* mf, const float* sf, const orc_camera* c)
+{
+    double p[3];
+    for (int i = 0; i < 3; i++)
+        p[i] = (double)c->R[3 * i] * mf[0] + (double)c->R[3 * i + 1] * mf[1] + (double)c->R[3 * i + 2] * mf[2] + c->t[i];
+    double limx = 1.3 * (0.5 * c->width / (double)c->fx), limy = 1.3 * (0.5 * c->height / (double)c->fy);
+    double xz = p[0] / p[2], yz = p[1] / p[2];
+    double cxz = xz < -limx ? -limx : (xz > limx ? limx : xz);
+    double cyz = yz < -limy ? -limy : (yz > limy ? limy : yz);
+    double smax = sf[0] > sf[1] ? sf[0] : sf[1];
+    if (sf[2] > smax) smax = sf[2];
+    double j0 = fabs((double)c->fx / p[2]) * sqrt(1.0 + cxz * cxz);
+    double j1 = fabs((double)c->fy / p[2]) * sqrt(1.0 + cyz * cyz);
+    return j0 * j1 * smax * smax;
+}
+
 /* View-dependent colour: sum_k Y_k(d) SH_k + 0.5, clamped to [0,1]. sh is [16][3]. */
 void orc_sh_colour(const float* mf, const double* sh, int deg, const orc_camera* c, double* rgb)
 {
@@ -448,17 +473,29 @@ static int cmp_ord(const void* pa, const void* pb)
  * means [n][3], quats [n][4] (w,x,y,z), scales [n][3] (activated), op [n]
  * (o in exact mode, log o in RoofGS mode), sh [n][16][3] FP64 coefficients.
  * img [3][H][W] receives C + T bg for every pixel of the rendered tiles.
- * diag (optional) [H][W][4] receives, per pixel:
+ * diag (optional) [H][W][4] receives, per pixel (test tolerances, not part of
+ * the render):
  *   [0] sum over contributing pairs of T_i alpha_i E_i, where E_i estimates the
  *       absolute FP32 rounding error of the pair's exponent (see below);
- *   [1] 2 T_i max(alpha_i, 1/255) for the first pair whose skip decision lies
- *       within E_i + 1e-5 of the threshold (0 if none);
+ *   [1] the sum of 2 T_i max(alpha_i, 1/255) over the pairs whose skip
+ *       decision lies within E_i + slack of the 1/255 threshold (0 if none):
+ *       the most the colour can jump if a single-precision renderer takes such
+ *       a decision the other way;
  *   [2] the transmittance T_i before the first pair whose stop decision lies
- *       within the accumulated E + 1e-5 of the 1e-4 threshold (0 if none);
+ *       within the accumulated error of log T (sum of (alpha E + 2^-23) /
+ *       (1 - alpha) over the blended pairs) + slack of the 1e-4 threshold;
  *   [3] number of pairs that contributed.
- * E_i = 2^-23 * (S_i + G_i (|u|+|v|) + 16), with S_i the sum of the absolute
- * terms of the exponent in tile-local coordinates and G_i = |grad_mu q|; this
- * is the first-order size of FP32 rounding in a single-precision renderer.
+ * E_i is the first-order size of FP32 rounding in the exponent as the two
+ * modes evaluate it:
+ *   RoofGS mode (the folded polynomial of Eqs. (13)-(16) in tile-local
+ *   coordinates, single-precision projected mean):
+ *   E_i = 2^-23 (S_i + G_i (|u|+|v|) + 16), S_i the sum of the absolute terms of
+ *   the exponent in tile-local coordinates, G_i = |grad_mu q|; slack 1e-5;
+ *   exact mode (Eq. (10) as -1/2 (a' t^2 + dy^2 / Sigma'_yy) with
+ *   t = dx - (Sigma'_xy / Sigma'_yy) dy, a' = Sigma'_yy / det, the mean carried
+ *   at twice single precision):
+ *   E_i = 2^-23 (32 |p| + 16 a' |t| (|dx| + |c| |dy| + |dy| g / Sigma'_yy) + 16),
+ *   c = Sigma'_xy / Sigma'_yy, g = u_rows_scale(); slack 1e-6.
  * Returns the number of (tile, Gaussian) entries of the listed tiles, or -1.
  */
 int64_t orc_render(int64_t n, const float* means, const float* quats, const float* scales,
@@ -524,6 +561,7 @@ int64_t orc_render(int64_t n, const float* means, const float* quats, const floa
         g[i].u = pr[0]; g[i].v = pr[1]; g[i].z = pr[2];
         g[i].s00 = pr[3]; g[i].s01 = pr[4]; g[i].s11 = pr[5];
         g[i].a = pr[6]; g[i].b = pr[7]; g[i].c = pr[8];
+        g[i].gg = (mode == ORC_EXACT) ? u_rows_scale(means + 3 * i, scales + 3 * i, cam) : 0.0;
         g[i].op = op[i];
         orc_sh_colour(means + 3 * i, sh + 48 * i, sh_deg, cam, g[i].rgb);
     }
@@ -556,12 +594,23 @@ int64_t orc_render(int64_t n, const float* means, const float* quats, const floa
                     double dx = px - G->u, dy = py - G->v;
                     double p = -0.5 * (G->a * dx * dx + G->b * dx * dy + G->c * dy * dy);
                     /* rounding-size estimate of a single-precision evaluation */
-                    double lx = px - x0, ly = py - y0, lu = G->u - x0, lv = G->v - y0;
-                    double ax = fabs(lx) + fabs(lu), ay = fabs(ly) + fabs(lv);
-                    double S = fabs(G->a) * ax * ax + fabs(G->b) * ax * ay + fabs(G->c) * ay * ay;
-                    double gx = 2 * G->a * dx + G->b * dy, gy = G->b * dx + 2 * G->c * dy;
-                    double Gm = sqrt(gx * gx + gy * gy);
-                    double E = eps32 * (S + Gm * (fabs(G->u) + fabs(G->v)) + 16.0);
+                    double E, slack;
+                    if (mode == ORC_EXACT) {
+                        double cc = G->s01 / G->s11;
+                        double t = dx - cc * dy;
+                        E = eps32 * (32.0 * fabs(p) +
+                                     16.0 * G->a * fabs(t) * (fabs(dx) + fabs(cc) * fabs(dy) + fabs(dy) * G->gg / G->s11) +
+                                     16.0);
+                        slack = 1e-6;
+                    } else {
+                        double lx = px - x0, ly = py - y0, lu = G->u - x0, lv = G->v - y0;
+                        double ax = fabs(lx) + fabs(lu), ay = fabs(ly) + fabs(lv);
+                        double S = fabs(G->a) * ax * ax + fabs(G->b) * ax * ay + fabs(G->c) * ay * ay;
+                        double gx = 2 * G->a * dx + G->b * dy, gy = G->b * dx + 2 * G->c * dy;
+                        double Gm = sqrt(gx * gx + gy * gy);
+                        E = eps32 * (S + Gm * (fabs(G->u) + fabs(G->v)) + 16.0);
+                        slack = 1e-5;
+                    }
                     double alpha, margin;
                     if (mode == ORC_EXACT) {
                         if (p > 0) continue;
@@ -569,14 +618,14 @@ int64_t orc_render(int64_t n, const float* means, const float* quats, const floa
                         margin = log(255.0 * at);
                         alpha = at < 0.99 ? at : 0.99;
                         if (alpha < 1.0 / 255.0) {
-                            if (d1 == 0 && fabs(margin) < E + 1e-5) d1 = 2.0 * T / 255.0;
+                            if (fabs(margin) < E + slack) d1 += 2.0 * T / 255.0;
                             continue;
                         }
                     } else {
                         double P = p + G->op; /* Eq. (17) */
                         margin = P + ORC_LN255;
                         if (P < -ORC_LN255) { /* outside the range of Eq. (23) */
-                            if (d1 == 0 && fabs(margin) < E + 1e-5) d1 = 2.0 * T / 255.0;
+                            if (fabs(margin) < E + slack) d1 += 2.0 * T / 255.0;
                             continue;
                         }
                         double at;
@@ -585,10 +634,10 @@ int64_t orc_render(int64_t n, const float* means, const float* quats, const floa
                         else at = exp(P);
                         alpha = at < 0.99 ? at : 0.99; /* Eq. (25) */
                     }
-                    if (d1 == 0 && fabs(margin) < E + 1e-5) d1 = 2.0 * T * (alpha > 1.0 / 255 ? alpha : 1.0 / 255);
+                    if (fabs(margin) < E + slack) d1 += 2.0 * T * (alpha > 1.0 / 255 ? alpha : 1.0 / 255);
                     double Tn = T * (1.0 - alpha);
-                    eacc += alpha * E;
-                    if (d2 == 0 && fabs(log(Tn / 1e-4)) < eacc + 1e-5) d2 = T;
+                    eacc += (alpha * E + eps32) / (1.0 - alpha);
+                    if (d2 == 0 && fabs(log(Tn / 1e-4)) < eacc + slack) d2 = T;
                     if (Tn < 1e-4) break; /* stop without adding this pair */
                     for (int ch = 0; ch < 3; ch++) C[ch] += G->rgb[ch] * alpha * T;
                     d0 += T * alpha * E;

@@ -378,6 +378,41 @@ def test_box_contains_every_pixel_it_must(tiny, mode):
     assert checked > 50
 
 
+@pytest.mark.parametrize("ties", [False, True])
+def test_exact_key_low_word_is_depth_ascending_within_tiles(ties):
+    """Exact mode's 64-bit key (the baseline key of Sec. IV-A.2): its low word, read as an
+    IEEE single, is the camera depth of the entry's Gaussian (the FP64 depth within FP32
+    rounding); inside every tile the entries ascend by that depth, equal depths by
+    ascending Gaussian index, and the order agrees with the FP64 depths up to rounding."""
+    if ties:  # 60 Gaussians share the mean (hence the depth) of another one
+        sc = small_random_scene(300, seed=4)
+        sc.means[200:260] = sc.means[0:60]
+        cam = synth.tiny_camera(64, 64)
+    else:
+        sc, cams = synth.workload("tiny_256")
+        cam = cams[0]
+    k, v, ranges, bins = oracle.keys(sc, cam, oracle.EXACT)
+    assert k.size > 100
+    R = np.asarray(cam.R, dtype=np.float64).reshape(3, 3)
+    z = (sc.means.astype(np.float64) @ R.T + np.asarray(cam.t, np.float64))[:, 2]
+    low = (k & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32).astype(np.float64)
+    zv = z[v.astype(np.int64)]
+    assert np.all(np.abs(low - zv) <= 4.0 * 2.0 ** -24 * np.abs(zv))
+    tile = (k >> np.uint64(32)).astype(np.int64)
+    assert np.all(np.diff(tile) >= 0)
+    same = tile[1:] == tile[:-1]
+    assert np.all(low[1:][same] >= low[:-1][same])
+    eq = same & (low[1:] == low[:-1])
+    assert np.all(v[1:][eq] > v[:-1][eq])
+    assert np.all(zv[1:][same] >= zv[:-1][same] - 8.0 * 2.0 ** -24 * np.abs(zv[1:][same]))
+    if ties:
+        assert eq.sum() >= 20  # tied depths were met and ordered by index
+    # the tile word and the ranges agree
+    for t in np.unique(tile):
+        s, e = ranges[t]
+        assert np.all(tile[s:e] == t) and e - s == np.count_nonzero(tile == t)
+
+
 # --------------------------------------------------------------------------
 # Quantized depth key (Eq. (9))
 # --------------------------------------------------------------------------
