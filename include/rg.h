@@ -254,7 +254,9 @@ rg_status rg_eval_fast_exp(const float* P_dev, float* out_dev, int64_t n, void* 
  * buffers, histograms, look-back status, counters) is one static device array
  * of about 4.3 MiB that every GPU loading the library keeps until the process
  * exits; nothing is allocated or freed.
- *   keys, vals  device arrays of n uint32 (input and output)
+ *   keys, vals  device arrays of n uint32 (input and output), each starting on a
+ *               16-byte boundary (cudaMalloc gives 256); a misaligned pointer
+ *               returns RG_ERR_INVALID_ARG before anything is launched
  *   n           0 .. 524288; larger n returns RG_ERR_INVALID_ARG
  *   error_dev   optional device uint32: receives 0, or non-zero error bits if a
  *               bounded device wait gave up (the output is then invalid)
@@ -264,7 +266,8 @@ rg_status rg_eval_fast_exp(const float* P_dev, float* out_dev, int64_t n, void* 
  * scratch array, which keeps the previous call's contents (the sort clears
  * what must start at zero): calls that overlap on the GPU -- on different
  * streams, or from different host threads -- race and must be ordered by the
- * caller.
+ * caller. A CUDA error left pending by an earlier call is reported as
+ * RG_ERR_CUDA and left pending (nothing is launched).
  */
 rg_status rg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, int64_t n, int32_t key_bits, uint32_t* error_dev,
                                 void* stream);

@@ -22,16 +22,17 @@ namespace rg {
 
 constexpr int B_THREADS = 256;
 
-// forward per-pair opacity of the exact rasterizer; false if the pair is skipped
-__device__ __forceinline__ bool exact_alpha(float2 m, float4 co, float fx, float fy, float& dx, float& dy,
-                                            float& power, float& e, float& alpha)
+// forward per-pair opacity of the exact rasterizer (the same exponent, exact_power);
+// false if the pair is skipped. m is the mean shifted to the tile origin, (lx, ly)
+// the pixel in the tile; dx = u - x, dy = v - y are returned for the gradients
+__device__ __forceinline__ bool exact_alpha(const float4& m, const float4& q, float lx, float ly, float& dx, float& dy,
+                                            float& e, float& alpha)
 {
-    dx = m.x - fx;
-    dy = m.y - fy;
-    power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-    if (power > 0.0f) return false;
+    const float power = exact_power(m, q, lx, ly);
+    dx = (m.x - lx) + m.y;
+    dy = (m.z - ly) + m.w;
     e = expf(power);
-    alpha = fminf(0.99f, co.w * e);
+    alpha = fminf(0.99f, q.w * e);
     return alpha >= 1.0f / 255.0f;
 }
 
@@ -45,16 +46,18 @@ __device__ __forceinline__ float warp_red(float x)
 __global__ void __launch_bounds__(B_THREADS) k_raster_backward(BackwardArgs a)
 {
     __shared__ unsigned s_id[B_THREADS];
-    __shared__ float2 s_xy[B_THREADS];
+    __shared__ float4 s_xy[B_THREADS];
     __shared__ float4 s_co[B_THREADS];
     __shared__ float4 s_rgb[B_THREADS];
     __shared__ int s_last;
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * a.cam.tw + (threadIdx.x & (a.cam.tw - 1)), py = ty * a.cam.th + (threadIdx.x >> a.cam.tw_log2);
+    const int x0 = tx * a.cam.tw, y0 = ty * a.cam.th;
+    const int lxi = threadIdx.x & (a.cam.tw - 1), lyi = threadIdx.x >> a.cam.tw_log2;
+    const int px = x0 + lxi, py = y0 + lyi;
     const int W = a.cam.W, H = a.cam.H;
     const bool inside = px < W && py < H;
-    const float fx = (float)px, fy = (float)py;
+    const float fx = (float)lxi, fy = (float)lyi; // pixel in the tile
     const uint2 range = a.ranges[tile];
     if (threadIdx.x == 0) s_last = -1;
 
@@ -68,14 +71,15 @@ __global__ void __launch_bounds__(B_THREADS) k_raster_backward(BackwardArgs a)
         if (j < range.y) {
             unsigned id = a.vals[j];
             if (id >= (unsigned long long)a.n) id = 0;
-            s_xy[threadIdx.x] = a.xy[id];
-            s_co[threadIdx.x] = a.conic_op[id];
+            const float4 m = a.mean2[id];
+            s_xy[threadIdx.x] = make_float4(m.x - (float)x0, m.y, m.z - (float)y0, m.w);
+            s_co[threadIdx.x] = a.quad[id];
         }
         __syncthreads();
         const int cnt = min((unsigned)B_THREADS, range.y - start);
         for (int k = 0; !done && k < cnt; k++) {
-            float dx, dy, power, e, alpha;
-            if (!exact_alpha(s_xy[k], s_co[k], fx, fy, dx, dy, power, e, alpha)) continue;
+            float dx, dy, e, alpha;
+            if (!exact_alpha(s_xy[k], s_co[k], fx, fy, dx, dy, e, alpha)) continue;
             const float Tn = T * (1.0f - alpha);
             if (Tn < 1e-4f) {
                 done = true;
@@ -109,8 +113,9 @@ __global__ void __launch_bounds__(B_THREADS) k_raster_backward(BackwardArgs a)
             unsigned id = a.vals[j];
             if (id >= (unsigned long long)a.n) id = 0;
             s_id[threadIdx.x] = id;
-            s_xy[threadIdx.x] = a.xy[id];
-            s_co[threadIdx.x] = a.conic_op[id];
+            const float4 m = a.mean2[id];
+            s_xy[threadIdx.x] = make_float4(m.x - (float)x0, m.y, m.z - (float)y0, m.w);
+            s_co[threadIdx.x] = a.quad[id];
             s_rgb[threadIdx.x] = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], 0.f);
         }
         __syncthreads();
@@ -120,9 +125,12 @@ __global__ void __launch_bounds__(B_THREADS) k_raster_backward(BackwardArgs a)
             float g_u = 0.f, g_v = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_o = 0.f, g_r = 0.f, g_g = 0.f, g_bl = 0.f;
             bool act = false;
             if (jj <= last) {
-                float dx, dy, power, e, alpha;
-                const float4 co = s_co[k];
-                if (exact_alpha(s_xy[k], co, fx, fy, dx, dy, power, e, alpha)) {
+                float dx, dy, e, alpha;
+                const float4 qd = s_co[k];
+                if (exact_alpha(s_xy[k], qd, fx, fy, dx, dy, e, alpha)) {
+                    // the conic (A, B, C) = Sigma'^-1 of the completed-square coefficients
+                    const float cA = -2.0f * qd.x, cB = 2.0f * qd.x * qd.y;
+                    const float4 co = make_float4(cA, cB, fmaf(-cB, qd.y, -2.0f * qd.z), qd.w);
                     act = true;
                     const float4 c = s_rgb[k];
                     const float inv = 1.0f / (1.0f - alpha);
@@ -249,7 +257,10 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(BackwardArgs a)
     const float sa = U[0] * U[0] + U[1] * U[1] + U[2] * U[2] + 0.3f;
     const float sc = U[3] * U[3] + U[4] * U[4] + U[5] * U[5] + 0.3f;
     const float sb = U[0] * U[3] + U[1] * U[4] + U[2] * U[5];
-    const float det = sa * sc - sb * sb;
+    // det Sigma' by the Lagrange identity |U0 x U1|^2 + 0.3 (|U0|^2 + |U1|^2) + 0.09, as the
+    // forward computes it (sa sc - sb^2 cancels for thin Gaussians)
+    const float x0 = U[1] * U[5] - U[2] * U[4], x1 = U[2] * U[3] - U[0] * U[5], x2 = U[0] * U[4] - U[1] * U[3];
+    const float det = x0 * x0 + x1 * x1 + x2 * x2 + 0.3f * (sa + sc - 0.6f) + 0.09f;
     const float idet = 1.0f / det;
     // K = Sigma'^-1 = [[A, B], [B, C]]; dL/dSigma' = -K Gs K with Gs = [[gA, gB/2], [gB/2, gC]]
     const float KA = sc * idet, KB = -sb * idet, KC = sa * idet;

@@ -361,13 +361,7 @@ __global__ void __launch_bounds__(256) k_depth_keys(FrontendArgs a, unsigned* ke
 void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, unsigned* hist,
                        int passes, cudaStream_t s)
 {
-    static int grid_cap = 0;
-    if (grid_cap == 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid_cap = 8 * (sms > 0 ? sms : 1);
-    }
+    const int grid_cap = 8 * device_sm_count();
     const long long need = (a.n + 255) / 256;
     const unsigned blocks = (unsigned)(need < 1 ? 1 : (need < grid_cap ? need : grid_cap));
     k_depth_keys<<<blocks, 256, 0, s>>>(a, keys, vals, ctr, hist, passes);
@@ -403,10 +397,12 @@ __global__ void __launch_bounds__(EX_THREADS) k_exact_preprocess(ExactArgs a)
     if (!project_bin(a.cam, mx, my, mz, pz, q.x, q.y, q.z, q.w, a.scales[3 * i], a.scales[3 * i + 1],
                      a.scales[3 * i + 2], false, 0.0f, b))
         return;
-    const float inv = 1.0f / b.det;
-    // conic as plain 3DGS stores it: (inv00, inv01, inv11, opacity)
-    a.conic_op[i] = make_float4(b.sc * inv, -b.sb * inv, b.sa * inv, a.opac[i]);
-    a.xy[i] = make_float2(b.u, b.v);
+    // the rasterizer's exponent (Eq. (10)) with the quadratic form completed in dx:
+    // -1/2 ((Sigma'_yy / det) (dx - c dy)^2 + dy^2 / Sigma'_yy), c = Sigma'_xy / Sigma'_yy
+    // (no cancellation for thin Gaussians); the mean as double-floats (the FP32 u, v
+    // above only bin the Gaussian)
+    a.quad[i] = make_float4(-0.5f * __fdiv_rn(b.sc, b.det), __fdiv_rn(b.sb, b.sc), __fdiv_rn(-0.5f, b.sc), a.opac[i]);
+    a.mean2[i] = project_mean_df(a.cam, mx, my, mz);
     a.depth[i] = pz;
     a.rect[i] = make_int4(b.tx0, b.ty0, b.tx1, b.ty1);
     a.touched[i] = (unsigned)((b.tx1 - b.tx0 + 1) * (b.ty1 - b.ty0 + 1));

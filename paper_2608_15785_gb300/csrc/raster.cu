@@ -232,22 +232,26 @@ void launch_raster_roofgs(const RasterArgs& a, cudaStream_t s)
     else raster_roofgs_variant<false>(a, s);
 }
 
-// Plain 3DGS rasterizer: one pixel per thread, expf, un-folded quadratic form.
+// Plain 3DGS rasterizer: one pixel per thread, expf. The exponent of Eq. (10) is
+// evaluated in the completed-square form of exact_power() from the double-float
+// mean, shifted to the tile origin when a record is staged (u.hi - x0 is exact).
 constexpr int E_THREADS = 256;
 
 template <bool COUNT>
 __global__ void __launch_bounds__(E_THREADS) k_raster_exact(RasterArgs a)
 {
-    __shared__ float2 s_xy[E_THREADS];
-    __shared__ float4 s_co[E_THREADS];
+    __shared__ float4 s_m[E_THREADS];
+    __shared__ float4 s_q[E_THREADS];
     __shared__ float4 s_rgb[E_THREADS];
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int px = tx * a.cam.tw + (threadIdx.x & (a.cam.tw - 1)), py = ty * a.cam.th + (threadIdx.x >> a.cam.tw_log2);
+    const int x0 = tx * a.cam.tw, y0 = ty * a.cam.th;
+    const int lxi = threadIdx.x & (a.cam.tw - 1), lyi = threadIdx.x >> a.cam.tw_log2;
+    const int px = x0 + lxi, py = y0 + lyi;
     const int W = a.cam.W, H = a.cam.H;
     const bool inside = px < W && py < H;
     bool done = !inside;
-    const float fx = (float)px, fy = (float)py;
+    const float lx = (float)lxi, ly = (float)lyi;
     float T = 1.0f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
     unsigned n_eval = 0, n_blend = 0;
     const uint2 range = a.ranges[tile];
@@ -257,20 +261,18 @@ __global__ void __launch_bounds__(E_THREADS) k_raster_exact(RasterArgs a)
         if (j < range.y) {
             unsigned id = a.vals[j];
             if (id >= (unsigned long long)a.n) id = 0; // only after a failed (timed-out) sort
-            s_xy[threadIdx.x] = a.xy[id];
-            s_co[threadIdx.x] = a.conic_op[id];
+            const float4 m = a.mean2[id];
+            s_m[threadIdx.x] = make_float4(m.x - (float)x0, m.y, m.z - (float)y0, m.w);
+            s_q[threadIdx.x] = a.quad[id];
             s_rgb[threadIdx.x] = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], 0.f);
         }
         __syncthreads();
         const int cnt = min((unsigned)E_THREADS, range.y - start);
         for (int k = 0; !done && k < cnt; k++) {
-            const float2 m = s_xy[k];
-            const float4 co = s_co[k];
-            const float dx = m.x - fx, dy = m.y - fy;
-            const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy; // Eq. (10)
+            const float4 q = s_q[k];
+            const float power = exact_power(s_m[k], q, lx, ly); // Eq. (10), <= 0
             if (COUNT) n_eval++;
-            if (power > 0.0f) continue;
-            const float alpha = fminf(0.99f, co.w * expf(power)); // Eqs. (11)-(12)
+            const float alpha = fminf(0.99f, q.w * expf(power)); // Eqs. (11)-(12)
             if (alpha < 1.0f / 255.0f) continue;
             if (COUNT) n_blend++;
             const float Tn = T * (1.0f - alpha);

@@ -132,9 +132,9 @@ rg_status ensure_workspace(Workspace& w, int64_t n_gauss, int mode, int tiles, i
     const int64_t fe_blocks = (n + frontend_block_threads() - 1) / frontend_block_threads();
     RG_TRY(ensure(w.lb_status, (size_t)(std::max<int64_t>(fe_blocks, (n + 2047) / 2048) + 1) * 8, "look-back status"));
     if (mode == RG_MODE_EXACT) {
-        RG_TRY(ensure(w.xy, (size_t)n * 8, "xy"));
+        RG_TRY(ensure(w.mean2, (size_t)n * 16, "projected means"));
         RG_TRY(ensure(w.depth, (size_t)n * 4, "depth"));
-        RG_TRY(ensure(w.conic, (size_t)n * 16, "conic"));
+        RG_TRY(ensure(w.quad, (size_t)n * 16, "exponent coefficients"));
         RG_TRY(ensure(w.rgb, (size_t)n * 12, "rgb"));
         RG_TRY(ensure(w.rect, (size_t)n * 16, "rect"));
         RG_TRY(ensure(w.touched, (size_t)n * 4, "touched"));
@@ -220,9 +220,9 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         a.n = n;
         a.cam = F.cam;
         a.lay = F.lay;
-        a.xy = w.xy.as<float2>();
+        a.mean2 = w.mean2.as<float4>();
         a.depth = w.depth.as<float>();
-        a.conic_op = w.conic.as<float4>();
+        a.quad = w.quad.as<float4>();
         a.rgb = w.rgb.as<float>();
         a.rect = w.rect.as<int4>();
         a.touched = w.touched.as<unsigned>();
@@ -371,8 +371,8 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     r.out = out;
     r.count = count ? ctr : nullptr;
     if (mode == RG_MODE_EXACT) {
-        r.xy = w.xy.as<float2>();
-        r.conic_op = w.conic.as<float4>();
+        r.mean2 = w.mean2.as<float4>();
+        r.quad = w.quad.as<float4>();
         r.rgb = w.rgb.as<float>();
         NvtxScope r_("rg raster");
         launch_raster_exact(r, st);
@@ -942,8 +942,8 @@ rg_status rg_backward(rg_scene* s, const rg_camera* cam, const rg_render_opts* o
     b.tiles_x = F.lay.tiles_x;
     b.tiles_y = F.lay.tiles_y;
     b.cam = F.cam;
-    b.xy = s->ws.xy.as<float2>();
-    b.conic_op = s->ws.conic.as<float4>();
+    b.mean2 = s->ws.mean2.as<float4>();
+    b.quad = s->ws.quad.as<float4>();
     b.rgb = s->ws.rgb.as<float>();
     b.touched = s->ws.touched.as<unsigned>();
     b.means = s->means.as<float>();

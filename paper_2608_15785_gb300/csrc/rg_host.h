@@ -60,7 +60,7 @@ struct Workspace {
     DevBuf ctrl; // Counters followed by hist[8][256] (twice: frame, depth sort)
     DevBuf lb_status;
     DevBuf sort_status[2];
-    DevBuf xy, depth, conic, rgb, rect, touched, offsets; // exact per-Gaussian
+    DevBuf mean2, depth, quad, rgb, rect, touched, offsets; // exact per-Gaussian
     DevBuf rec;                                           // RoofGS raster records
     DevBuf gkeys[2], gvals[2], gstatus[2];                // RoofGS per-Gaussian depth sort
     DevBuf gbuf;                                          // backward: image-space gradients [n][9]
@@ -80,7 +80,7 @@ struct Workspace {
     void release()
     {
         DevBuf* bufs[] = {&keys[0], &keys[1], &vals[0], &vals[1], &ranges, &ctrl, &lb_status, &sort_status[0],
-                          &sort_status[1], &xy, &depth, &conic, &rgb, &rect, &touched, &offsets, &rec, &gkeys[0],
+                          &sort_status[1], &mean2, &depth, &quad, &rgb, &rect, &touched, &offsets, &rec, &gkeys[0],
                           &gkeys[1], &gvals[0], &gvals[1], &gstatus[0], &gstatus[1], &gbuf};
         for (DevBuf* b : bufs) b->release();
         if (ev_init)

@@ -360,6 +360,98 @@ __device__ __forceinline__ void view_dir(const CamDev& c, float mx, float my, fl
 __device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
 
 // ---------------------------------------------------------------------------
+// Double-float arithmetic: a value carried as the unevaluated sum hi + lo of two
+// FP32 numbers (Dekker 1971: the exact product by a fused multiply-add; Knuth's
+// two-sum; the compensated dot product of Ogita, Rump and Oishi 2005, which is
+// as accurate as evaluation in twice the working precision). Exact mode carries
+// the projected mean this way: in FP32 alone u has an error of ~1e-3 pixel at
+// 4K (the camera transform and the division), which moves the exponent of a
+// small Gaussian by up to 1e-2.
+// ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ DF fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// r0 m0 + r1 m1 + r2 m2 + t
+__device__ __forceinline__ DF dot3_df(float r0, float r1, float r2, float m0, float m1, float m2, float t)
+{
+    const DF p0 = two_prod(r0, m0), p1 = two_prod(r1, m1), p2 = two_prod(r2, m2);
+    const DF s1 = two_sum(p0.hi, p1.hi);
+    const DF s2 = two_sum(s1.hi, p2.hi);
+    const DF s3 = two_sum(s2.hi, t);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, s1.lo)), __fadd_rn(s2.lo, s3.lo));
+    return two_sum(s3.hi, lo);
+}
+
+// (a.hi + a.lo) / (b.hi + b.lo): quotient q1 = a.hi / b.hi, remainder a - q1 b
+// (a.hi - hi(q1 b.hi) is exact), correction q2 = remainder / b.hi
+__device__ __forceinline__ DF div_df(DF a, DF b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const DF p = two_prod(q1, b.hi);
+    float r = __fsub_rn(a.hi, p.hi);
+    r = __fsub_rn(r, p.lo);
+    r = __fadd_rn(r, a.lo);
+    r = __fmaf_rn(-q1, b.lo, r);
+    return fast_two_sum(q1, __fdiv_rn(r, b.hi));
+}
+
+// f q + c
+__device__ __forceinline__ DF affine_df(float f, DF q, float c)
+{
+    const DF p = two_prod(f, q.hi);
+    const float plo = __fmaf_rn(f, q.lo, p.lo);
+    const DF s = two_sum(p.hi, c);
+    return two_sum(s.hi, __fadd_rn(s.lo, plo));
+}
+
+// Projected mean u = fx x/z + cx, v = fy y/z + cy of (x, y, z) = R m + t as
+// double-floats: (u.hi, u.lo, v.hi, v.lo).
+__device__ __forceinline__ float4 project_mean_df(const CamDev& c, float mx, float my, float mz)
+{
+    const DF x = dot3_df(c.R[0], c.R[1], c.R[2], mx, my, mz, c.t[0]);
+    const DF y = dot3_df(c.R[3], c.R[4], c.R[5], mx, my, mz, c.t[1]);
+    const DF z = dot3_df(c.R[6], c.R[7], c.R[8], mx, my, mz, c.t[2]);
+    const DF u = affine_df(c.fx, div_df(x, z), c.cx);
+    const DF v = affine_df(c.fy, div_df(y, z), c.cy);
+    return make_float4(u.hi, u.lo, v.hi, v.lo);
+}
+
+// Exact-mode exponent p = -1/2 d^T Sigma'^-1 d of Eq. (10) at the pixel offset
+// d = (dx, dy) from the mean, with the quadratic form completed in dx:
+//   d^T Sigma'^-1 d = (Sigma'_yy / det) (dx - c dy)^2 + dy^2 / Sigma'_yy,  c = Sigma'_xy / Sigma'_yy.
+// Both terms are non-negative, so a thin Gaussian does not cancel large terms as
+// the expanded a dx^2 + b dx dy + c dy^2 does. quad = (-Sigma'_yy / (2 det), c,
+// -1/(2 Sigma'_yy), opacity); m = (u.hi - x0, u.lo, v.hi - y0, v.lo) with the
+// pixel at (x0 + lx, y0 + ly).
+__device__ __forceinline__ float exact_power(const float4& m, const float4& quad, float lx, float ly)
+{
+    const float dy = __fsub_rn(__fsub_rn(ly, m.z), m.w);
+    const float t = __fsub_rn(__fmaf_rn(-quad.y, dy, __fsub_rn(lx, m.x)), m.y);
+    return __fmaf_rn(__fmul_rn(quad.x, t), t, __fmul_rn(__fmul_rn(quad.z, dy), dy));
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files).
 // ---------------------------------------------------------------------------
 // The front end's blocks add their digit counts to one of these copies (block id
@@ -408,9 +500,9 @@ struct ExactArgs {
     long long n;
     CamDev cam;
     Layout lay;
-    float2* xy;
+    float4* mean2;         // [N] projected mean as double-floats (u.hi, u.lo, v.hi, v.lo)
     float* depth;
-    float4* conic_op;
+    float4* quad;          // [N] (-Sigma'_yy / (2 det), Sigma'_xy / Sigma'_yy, -1 / (2 Sigma'_yy), opacity)
     float* rgb;            // [N][3]
     int4* rect;            // [N] tx0, ty0, tx1, ty1
     unsigned* touched;     // [N]
@@ -476,8 +568,8 @@ struct RasterArgs {
     int fast_exp;
     int ppt;              // pixels per thread: 1, 2 (Eq. (20)) or 4
     // exact
-    const float2* xy;
-    const float4* conic_op;
+    const float4* mean2;
+    const float4* quad;
     const float* rgb;
     Counters* count;      // non-null: count evaluated / blended pairs (separate kernel variant)
 };
@@ -492,8 +584,8 @@ struct BackwardArgs {
     long long n;
     int tiles_x, tiles_y;
     CamDev cam;
-    const float2* xy;
-    const float4* conic_op;
+    const float4* mean2;
+    const float4* quad;
     const float* rgb;
     const unsigned* touched;
     // scene attributes (FP32)
@@ -515,6 +607,9 @@ struct BackwardArgs {
 };
 void launch_raster_backward(const BackwardArgs& a, cudaStream_t s);
 void launch_preprocess_backward(const BackwardArgs& a, cudaStream_t s);
+
+// SMs of the current device (looked up once per device).
+int device_sm_count();
 
 // Sets the message that rg_last_error() returns on this thread.
 void set_last_error(const char* msg);

@@ -23,6 +23,8 @@
 // of entries is read on the device: no host round trip. k_ranges finds the
 // per-tile [start, end) of a sorted array (exact mode; RoofGS frames find their
 // ranges inside the rasterizer).
+#include <mutex>
+
 #include "rg_internal.cuh"
 
 namespace rg {
@@ -77,18 +79,41 @@ int sort_tile_items()
     return t;
 }
 
-// SMs of the current device, looked up once (kept out of stream capture)
-static int sm_count()
+// Launch shapes that depend on the device (SM count, resident one-sweep CTAs, the
+// one-sweep kernels' shared-memory attribute), looked up once per device with that
+// device current (the first launch on a device should come before any stream
+// capture) and kept in a small table guarded by a mutex.
+namespace {
+constexpr int MAX_DEVICES = 64;
+struct DeviceShape {
+    int sms = 0;
+    int onesweep_grid[3] = {0, 0, 0}; // 16-, 32- and 64-bit keys
+};
+std::mutex g_shape_mu;
+DeviceShape g_shape[MAX_DEVICES];
+
+int current_device()
 {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0, v = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        sms = v > 0 ? v : 1;
-    }
-    return sms;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) dev = 0;
+    return dev;
 }
+} // namespace
+
+int device_sm_count()
+{
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(g_shape_mu);
+    DeviceShape& d = g_shape[dev];
+    if (d.sms == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        d.sms = v > 0 ? v : 1;
+    }
+    return d.sms;
+}
+
+static int sm_count() { return device_sm_count(); }
 
 // The producer's digit counts cover every entry it made; they are not used when
 // entries did not fit (overflow) or its allocation gave up waiting (the error bit
@@ -413,17 +438,23 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
 template <typename K>
 static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hist)
 {
-    static int grid = 0;
     const size_t smem = sizeof(SortSmem<K>);
-    if (grid == 0) {
-        cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0, sms = 0, dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K>, SortCfg<K>::THREADS, smem);
-        grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    const int kind = sizeof(K) == 2 ? 0 : (sizeof(K) == 4 ? 1 : 2);
+    const int sms = sm_count();
+    int grid;
+    {
+        const int dev = current_device();
+        std::lock_guard<std::mutex> lock(g_shape_mu);
+        int& g = g_shape[dev].onesweep_grid[kind];
+        if (g == 0) { // once per device and key width, with the device current
+            cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K>, SortCfg<K>::THREADS, smem);
+            g = (per_sm > 0 ? per_sm : 1) * sms;
+        }
+        grid = g;
     }
-    const int hist_grid = 8 * sm_count();
+    const int hist_grid = 8 * sms;
     const K* kin = (const K*)a.keys[0];
     if (a.passes <= 0) return;
     k_sort_hist<K><<<hist_grid, H_THREADS, 0, s>>>(kin, a.passes, a.bit0, a.hist, a.status[0], a.ctr, a.hist_pre,

@@ -9,6 +9,7 @@
 // allocation inside the recorded region. They pass their own key and value
 // arrays; the sort's alternate buffers, digit histograms, look-back status
 // words and counters live in g_noalloc_scratch below.
+#include <cstdint>
 #include <mutex>
 
 #include "rg.h"
@@ -72,9 +73,16 @@ extern "C" rg_status rg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, int64
 {
     if (n < 0 || n > NA_MAX) return na_fail(RG_ERR_INVALID_ARG, "rg_sort_pairs_noalloc: n must be in [0, 524288]");
     if (n > 0 && (!keys || !vals)) return na_fail(RG_ERR_INVALID_ARG, "rg_sort_pairs_noalloc: keys or vals is NULL");
+    // the histogram kernel reads the keys 16 bytes at a time
+    if (n > 0 && ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u))
+        return na_fail(RG_ERR_INVALID_ARG, "rg_sort_pairs_noalloc: keys and vals must be 16-byte aligned");
     if (key_bits != 8 && key_bits != 16 && key_bits != 24 && key_bits != 32)
         return na_fail(RG_ERR_INVALID_ARG, "rg_sort_pairs_noalloc: key_bits must be 8, 16, 24 or 32");
     if (sort_tile_items() < NA_TILE) return na_fail(RG_ERR_CUDA, "rg_sort_pairs_noalloc: sort tile below the sized minimum");
+    // an error left by an earlier, unrelated launch is not this call's: report it and leave
+    // it pending for its owner
+    if (cudaPeekAtLastError() != cudaSuccess)
+        return na_fail(RG_ERR_CUDA, "rg_sort_pairs_noalloc: a CUDA error from an earlier call is pending");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
         return na_fail(RG_ERR_CUDA, "rg_sort_pairs_noalloc: no usable current device");

@@ -110,3 +110,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[cname]) == C.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
+
+
+def test_noalloc_sort_rejects_misaligned_arrays_before_any_launch(L):
+    """rg_sort_pairs_noalloc reads keys 16 bytes at a time: pointers off a 16-byte boundary
+    are refused on the host (no CUDA call is made, so this runs without a GPU; the
+    addresses are never dereferenced)."""
+    for keys, vals in ((0x10004, 0x20000), (0x10000, 0x20008), (0x1000c, 0x2000c)):
+        st = L.rg_sort_pairs_noalloc(C.c_void_p(keys), C.c_void_p(vals), 1000, 32, None, None)
+        assert st == 1, st  # RG_ERR_INVALID_ARG
+        assert b"16-byte" in L.rg_last_error()
+    assert L.rg_sort_pairs_noalloc(C.c_void_p(0x10000), C.c_void_p(0x20000), -1, 32, None, None) == 1
+    assert L.rg_sort_pairs_noalloc(C.c_void_p(0x10000), C.c_void_p(0x20000), 10, 12, None, None) == 1

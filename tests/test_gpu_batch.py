@@ -2,7 +2,9 @@
 
 Each image of a batch must equal, bit for bit, the single-view rg_render image
 of the same scene and camera with the pixels-per-thread variant the batch's
-autotuner chose (the kernels are deterministic). Views mix resolutions and two
+autotuner chose (the kernels are deterministic), and sampled tiles of every
+view must match the FP64 oracle with the tile shape the plan uses, under the
+same tolerances as the single-view parity tests. Views mix resolutions and two
 resident scenes; a second call with new poses exercises the in-place graph
 update, and RG_FLAG_BATCH_CHECKED the re-sizing after an overflow.
 """
@@ -12,6 +14,7 @@ import numpy as np
 import pytest
 
 from paper_2608_15785_gb300 import binding, synth
+from tests._parity import check_view, sample_tiles
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -25,9 +28,12 @@ def _built():
     build()
 
 
+SOURCES = [synth.tiny_scene(10_000, seed=0), synth.clustered_scene(60_000, seed=5)]
+
+
 @pytest.fixture(scope="module")
 def scenes():
-    return [binding.Scene(synth.tiny_scene(10_000, seed=0)), binding.Scene(synth.clustered_scene(60_000, seed=5))]
+    return [binding.Scene(sc) for sc in SOURCES]
 
 
 SIZES = [(256, 256), (320, 200), (640, 360), (100, 37), (512, 288), (1280, 720)]
@@ -64,8 +70,13 @@ def test_batch_equals_single_views(scenes, mode):
         assert lanes in (1, 2, 4) and ppt in ((1, 2, 4) if mode == "roofgs" else (2,))
         assert (tw, th) in ((16, 16), (32, 8), (8, 32))
         for v, cam in enumerate(cams):
+            img = outs[v].cpu().numpy()
             ref = _single(scenes[idx[v]], cam, mode, ppt, (tw, th))
-            assert np.array_equal(outs[v].cpu().numpy(), ref), (mode, call, v)
+            assert np.array_equal(img, ref), (mode, call, v)
+            # the oracle, on a few sampled tiles of every view (both calls)
+            tiles = sample_tiles(cam, 6, seed=10 * call + v, tile=(tw, th))
+            check_view(img.astype(np.float64), SOURCES[idx[v]], cam, mode, tile=(tw, th), tiles=tiles,
+                       max_flagged=0.05, label="batch call %d view %d" % (call, v))
     for s in scenes:
         s.check()
 

@@ -3,7 +3,8 @@
 Continuous batching: requests submitted while others render are admitted into
 slots as slots free up and overlap on the device. Every result must equal, bit
 for bit, the same request rendered alone (rg_render, and the same request sent
-to an idle server), whatever else was in the mix.
+to an idle server), whatever else was in the mix, and sampled tiles of every
+result must match the FP64 oracle under the single-view parity tolerances.
 """
 from __future__ import annotations
 
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 from paper_2608_15785_gb300 import binding, synth
+from tests._parity import check_view, sample_tiles
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -26,9 +28,12 @@ def _built():
     build()
 
 
+SOURCES = [synth.tiny_scene(10_000, seed=0), synth.clustered_scene(60_000, seed=5)]
+
+
 @pytest.fixture(scope="module")
 def scenes():
-    return [binding.Scene(synth.tiny_scene(10_000, seed=0)), binding.Scene(synth.clustered_scene(60_000, seed=5))]
+    return [binding.Scene(sc) for sc in SOURCES]
 
 
 SIZES = [(640, 360), (320, 200), (256, 256), (100, 37)]
@@ -67,6 +72,9 @@ def test_results_alone_equal_results_in_the_mix(scenes, mode):
         ref = scenes[s].render(cam, mode=mode)
         torch.cuda.synchronize()
         assert torch.equal(outs[k], ref), k
+        # the oracle, on a few sampled tiles of every served result
+        check_view(outs[k].cpu().numpy().astype(np.float64), SOURCES[s], cam, mode,
+                   tiles=sample_tiles(cam, 6, seed=k), max_flagged=0.05, label="served request %d" % k)
     # the same request alone on the idle server
     cam, s = reqs[5]
     alone = torch.empty_like(outs[5])

@@ -81,3 +81,16 @@ def test_noalloc_sort_partial_key_width_and_limits(lib):
     assert empty_k.size == 0
     status = lib.rg_sort_pairs_noalloc(None, None, MAX_PAIRS + 1, 32, None, None)
     assert status == 1 and b"524288" in lib.rg_last_error()
+
+
+@pytest.mark.parametrize("key_bits", [16, 8])
+def test_noalloc_sort_at_the_size_limit(lib, key_bits):
+    """Exactly 524,288 random pairs: every look-back status row and the whole alternate
+    buffers are used (16 bits: two passes, the result ends in the caller's arrays; 8 bits:
+    one pass, the result is copied back from the scratch array)."""
+    rng = np.random.default_rng(key_bits)
+    keys = rng.integers(0, 2 ** 32, size=MAX_PAIRS, dtype=np.uint64).astype(np.uint32)
+    vals = rng.permutation(MAX_PAIRS).astype(np.uint32)
+    got_k, got_v = _noalloc_sort(lib, keys, vals, key_bits=key_bits)
+    order = np.argsort(keys & np.uint32((1 << key_bits) - 1), kind="stable")
+    assert np.array_equal(got_v, vals[order]) and np.array_equal(got_k, keys[order])
