@@ -86,6 +86,8 @@ def _load():
         lib.orc_fast_exp_many.argtypes = [C.c_int64, P, P, C.c_int]
         lib.orc_log_opacity.restype = None
         lib.orc_log_opacity.argtypes = [C.c_int64, P, P]
+        lib.orc_backward.restype = C.c_int
+        lib.orc_backward.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, P, C.c_int32, C.c_int32, P, P, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -222,6 +224,27 @@ def render(scene, cam, mode=EXACT, tile=(16, 16), exp_kind=EXP_EXACT, comp: Comp
     if total < 0:
         raise RuntimeError("oracle render failed")
     return img, diag, int(total)
+
+
+def backward(scene, cam, dL_dimg, tile=(16, 16), sh_degree=3) -> dict:
+    """FP64 gradient of L = sum(dL_dimg * img) for the exact-mode image of ``render``, with
+    respect to the scene's FP32 attributes: dict of means [N,3], scales [N,3], quats [N,4],
+    opacities [N], sh [N,16,3] (float64)."""
+    lib = _load()
+    m, q, s, op, sh = _inputs(scene, EXACT, None)
+    n = m.shape[0]
+    H, W = int(cam.height), int(cam.width)
+    g = np.ascontiguousarray(dL_dimg, dtype=np.float64).reshape(3, H, W)
+    nn = max(n, 1)
+    out = {"means": np.zeros((nn, 3)), "scales": np.zeros((nn, 3)), "quats": np.zeros((nn, 4)),
+           "opacities": np.zeros(nn), "sh": np.zeros((nn, 16, 3))}
+    c = cam_struct(cam)
+    rc = lib.orc_backward(n, _ptr(m), _ptr(q), _ptr(s), _ptr(op), _ptr(sh), int(sh_degree), C.byref(c),
+                          int(tile[0]), int(tile[1]), _ptr(g), _ptr(out["means"]), _ptr(out["scales"]),
+                          _ptr(out["quats"]), _ptr(out["opacities"]), _ptr(out["sh"]))
+    if rc != 0:
+        raise RuntimeError("oracle backward failed")
+    return {k: v[:n] for k, v in out.items()}
 
 
 def keys(scene, cam, mode=EXACT, tile=(16, 16), comp: Compact | None = None):

@@ -33,6 +33,8 @@
  * -ffp-contract=off). The GPU renderer implements the same operation order
  * independently, so culling, tile rectangles and keys are bit-exact.
  */
+#include <complex.h>
+#undef I /* the imaginary unit is written _Complex_I; I names integers below */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -764,4 +766,299 @@ void orc_fast_exp_many(int64_t n, const double* P, double* out, int kind)
 {
     for (int64_t i = 0; i < n; i++)
         out[i] = (kind == ORC_EXP_FAST32) ? orc_fast_exp32((float)P[i]) : orc_fast_exp64(P[i]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* FP64 gradient of the exact-mode render.                                      */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * The per-Gaussian map of the exact mode in complex arithmetic, for
+ * complex-step differentiation (Squire and Trapp 1998: for a real-analytic f,
+ * f'(x) = Im f(x + i h) / h up to rounding, with no difference of nearby
+ * values, so h = 1e-30 gives the derivative to FP64 precision). The
+ * definitions are those of orc_project64 and orc_sh_colour: mean, raw
+ * quaternion and scale -> (u, v, a, b, c) of Eq. (10); mean -> the raw colour
+ * sum_k Y_k(d) SH_k + 0.5 before the clamp. The tangent clamp compares real
+ * parts (a piecewise map: the derivative of the branch taken).
+ */
+typedef double _Complex cplx;
+
+static cplx cmin_re(cplx a, double lim) { return creal(a) > lim ? (cplx)lim : a; }
+static cplx cmax_re(cplx a, double lim) { return creal(a) < lim ? (cplx)lim : a; }
+
+static void proj_cplx(const cplx* m, const cplx* q, const cplx* s, const orc_camera* c, cplx* out)
+{
+    double R[9];
+    for (int i = 0; i < 9; i++) R[i] = c->R[i];
+    cplx p[3];
+    for (int i = 0; i < 3; i++) p[i] = R[3 * i] * m[0] + R[3 * i + 1] * m[1] + R[3 * i + 2] * m[2] + (double)c->t[i];
+    cplx nq = csqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    cplx w = q[0] / nq, x = q[1] / nq, y = q[2] / nq, z = q[3] / nq;
+    cplx Q[9];
+    Q[0] = 1.0 - 2.0 * (y * y + z * z); Q[1] = 2.0 * (x * y - w * z);       Q[2] = 2.0 * (x * z + w * y);
+    Q[3] = 2.0 * (x * y + w * z);       Q[4] = 1.0 - 2.0 * (x * x + z * z); Q[5] = 2.0 * (y * z - w * x);
+    Q[6] = 2.0 * (x * z - w * y);       Q[7] = 2.0 * (y * z + w * x);       Q[8] = 1.0 - 2.0 * (x * x + y * y);
+    cplx S[9]; /* Sigma = Q diag(s)^2 Q^T */
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            cplx acc = 0;
+            for (int k = 0; k < 3; k++) acc += Q[3 * i + k] * s[k] * s[k] * Q[3 * j + k];
+            S[3 * i + j] = acc;
+        }
+    double fx = c->fx, fy = c->fy;
+    double limx = 1.3 * (0.5 * c->width / fx), limy = 1.3 * (0.5 * c->height / fy);
+    cplx xz = p[0] / p[2], yz = p[1] / p[2];
+    cplx cxz = cmax_re(cmin_re(xz, limx), -limx), cyz = cmax_re(cmin_re(yz, limy), -limy);
+    cplx J[6] = {fx / p[2], 0, -fx * cxz / p[2], 0, fy / p[2], -fy * cyz / p[2]};
+    cplx T[6];
+    for (int i = 0; i < 2; i++)
+        for (int k = 0; k < 3; k++) T[3 * i + k] = J[3 * i] * R[k] + J[3 * i + 1] * R[3 + k] + J[3 * i + 2] * R[6 + k];
+    cplx C2[4];
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++) {
+            cplx acc = 0;
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++) acc += T[3 * i + k] * S[3 * k + l] * T[3 * j + l];
+            C2[2 * i + j] = acc;
+        }
+    cplx s00 = C2[0] + 0.3, s01 = C2[1], s11 = C2[3] + 0.3;
+    cplx det = s00 * s11 - s01 * s01;
+    out[0] = fx * xz + (double)c->cx;
+    out[1] = fy * yz + (double)c->cy;
+    out[2] = s11 / det;
+    out[3] = -2.0 * s01 / det;
+    out[4] = s00 / det;
+}
+
+static void sh_basis_cplx(cplx x, cplx y, cplx z, cplx* Y)
+{
+    const double pi = 3.14159265358979323846;
+    Y[0] = 0.5 * sqrt(1.0 / pi);
+    double k1 = sqrt(3.0 / (4.0 * pi));
+    Y[1] = k1 * y;
+    Y[2] = k1 * z;
+    Y[3] = k1 * x;
+    double k2a = 0.5 * sqrt(15.0 / pi), k20 = 0.25 * sqrt(5.0 / pi), k22 = 0.25 * sqrt(15.0 / pi);
+    Y[4] = k2a * x * y;
+    Y[5] = k2a * y * z;
+    Y[6] = k20 * (3.0 * z * z - 1.0);
+    Y[7] = k2a * x * z;
+    Y[8] = k22 * (x * x - y * y);
+    double k33 = 0.25 * sqrt(35.0 / (2.0 * pi)), k32 = 0.5 * sqrt(105.0 / pi);
+    double k31 = 0.25 * sqrt(21.0 / (2.0 * pi)), k30 = 0.25 * sqrt(7.0 / pi), k32b = 0.25 * sqrt(105.0 / pi);
+    Y[9] = k33 * y * (3.0 * x * x - y * y);
+    Y[10] = k32 * x * y * z;
+    Y[11] = k31 * y * (5.0 * z * z - 1.0);
+    Y[12] = k30 * z * (5.0 * z * z - 3.0);
+    Y[13] = k31 * x * (5.0 * z * z - 1.0);
+    Y[14] = k32b * z * (x * x - y * y);
+    Y[15] = k33 * x * (x * x - 3.0 * y * y);
+}
+
+/* raw colour (before the [0, 1] clamp) of one Gaussian; sh is [16][3] */
+static void colour_raw_cplx(const cplx* m, const double* sh, int deg, const orc_camera* c, cplx* raw)
+{
+    double campos[3];
+    for (int j = 0; j < 3; j++)
+        campos[j] = -((double)c->R[j] * c->t[0] + (double)c->R[3 + j] * c->t[1] + (double)c->R[6 + j] * c->t[2]);
+    cplx d[3] = {m[0] - campos[0], m[1] - campos[1], m[2] - campos[2]};
+    cplx nd = csqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    cplx Y[16];
+    sh_basis_cplx(d[0] / nd, d[1] / nd, d[2] / nd, Y);
+    int nk = (deg + 1) * (deg + 1);
+    for (int ch = 0; ch < 3; ch++) {
+        cplx acc = 0.5;
+        for (int k = 0; k < nk; k++) acc += Y[k] * sh[3 * k + ch];
+        raw[ch] = acc;
+    }
+}
+
+/*
+ * Gradient of L = sum(dL_dimg * img) for the exact-mode image of orc_render
+ * (all tiles), with respect to the FP32 inputs: means [n][3], scales [n][3]
+ * (activated), quats [n][4] (raw, normalised inside), opacities [n], sh
+ * [n][16][3]. Outputs are FP64 and fully written.
+ *
+ * Per pixel (Sec. III-D, Eq. (7)): C = sum_i c_i alpha_i T_i + T_N bg with
+ * T_i = prod_{j<i} (1 - alpha_j) over the pairs the forward blends (same skip
+ * and stop rules, same FP64 depth order). Walking the pairs back to front with
+ * R_i = sum_{j>i} c_j alpha_j T_j + T_N bg (the colour behind pair i):
+ *   dC/dc_i = alpha_i T_i,   dC/dalpha_i = c_i T_i - R_i / (1 - alpha_i);
+ * alpha = min(0.99, o e^p) (Eqs. (11)-(12)): below the clamp dalpha/do = e^p,
+ * dalpha/dp = alpha, at the clamp both are 0; p = -1/2 (a dx^2 + b dx dy +
+ * c dy^2) (Eq. (10)) with dx = x - u, dy = y - v gives dp/du = a dx + b dy / 2,
+ * dp/dv = b dx / 2 + c dy, dp/da = -dx^2 / 2, dp/db = -dx dy / 2,
+ * dp/dc = -dy^2 / 2. Per Gaussian, the sums over its pixels go through the
+ * Jacobian of the map (mean, quaternion, scale) -> (u, v, a, b, c) and mean ->
+ * raw colour, taken by complex steps; the clamp of the colour to [0, 1] passes
+ * no gradient outside (0, 1); dL/dSH_k = Y_k(d) dL/draw.
+ * Returns 0, or -1 on a bad layout or allocation failure.
+ */
+int orc_backward(int64_t n, const float* means, const float* quats, const float* scales, const float* opac,
+                 const double* sh, int sh_deg, const orc_camera* cam, int32_t tile_w, int32_t tile_h,
+                 const double* dL_dimg, double* dmeans, double* dscales, double* dquats, double* dopac, double* dsh)
+{
+    orc_layout L;
+    if (orc_layout_compute(cam, tile_w, tile_h, &L) != 0) return -1;
+    const int W = cam->width, H = cam->height;
+    const int64_t NT = (int64_t)L.tiles_x * L.tiles_y;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    memset(dmeans, 0, sizeof(double) * 3 * nn);
+    memset(dscales, 0, sizeof(double) * 3 * nn);
+    memset(dquats, 0, sizeof(double) * 4 * nn);
+    memset(dopac, 0, sizeof(double) * nn);
+    memset(dsh, 0, sizeof(double) * 48 * nn);
+
+    orc_bin* bins = (orc_bin*)malloc(sizeof(orc_bin) * nn);
+    int64_t* cnt = (int64_t*)calloc((size_t)NT + 1, sizeof(int64_t));
+    if (!bins || !cnt) { free(bins); free(cnt); return -1; }
+    for (int64_t i = 0; i < n; i++) bin32(means + 3 * i, quats + 4 * i, scales + 3 * i, opac[i], ORC_EXACT, cam, &L, &bins[i]);
+    for (int64_t i = 0; i < n; i++) {
+        if (!bins[i].vis) continue;
+        for (int ty = bins[i].ty0; ty <= bins[i].ty1; ty++)
+            for (int tx = bins[i].tx0; tx <= bins[i].tx1; tx++) cnt[(int64_t)ty * L.tiles_x + tx + 1]++;
+    }
+    for (int64_t t = 0; t < NT; t++) cnt[t + 1] += cnt[t];
+    const int64_t total = cnt[NT];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(NT + 1));
+    int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(total > 0 ? total : 1));
+    orc_g64* g = (orc_g64*)malloc(sizeof(orc_g64) * nn);
+    double* gimg = (double*)calloc(nn * 9, sizeof(double)); /* per Gaussian: d(u, v, a, b, c), d(o), d(rgb) */
+    if (!fill || !list || !g || !gimg) { free(bins); free(cnt); free(fill); free(list); free(g); free(gimg); return -1; }
+    memcpy(fill, cnt, sizeof(int64_t) * (size_t)(NT + 1));
+    for (int64_t i = 0; i < n; i++) {
+        if (!bins[i].vis) continue;
+        for (int ty = bins[i].ty0; ty <= bins[i].ty1; ty++)
+            for (int tx = bins[i].tx0; tx <= bins[i].tx1; tx++) list[fill[(int64_t)ty * L.tiles_x + tx]++] = i;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        if (!bins[i].vis) continue;
+        double pr[10];
+        orc_project64(means + 3 * i, quats + 4 * i, scales + 3 * i, cam, pr);
+        g[i].u = pr[0]; g[i].v = pr[1]; g[i].z = pr[2];
+        g[i].a = pr[6]; g[i].b = pr[7]; g[i].c = pr[8];
+        g[i].op = opac[i];
+        orc_sh_colour(means + 3 * i, sh + 48 * i, sh_deg, cam, g[i].rgb);
+    }
+
+    typedef struct { int64_t i; double alpha, T, e, dx, dy; int clamped; } pair_t;
+    orc_ord* ord = NULL;
+    pair_t* pr = NULL;
+    int64_t cap = 0;
+    for (int64_t t = 0; t < NT; t++) {
+        int64_t len = cnt[t + 1] - cnt[t];
+        if (len == 0) continue;
+        if (len > cap) {
+            free(ord); free(pr);
+            cap = len;
+            ord = (orc_ord*)malloc(sizeof(orc_ord) * (size_t)cap);
+            pr = (pair_t*)malloc(sizeof(pair_t) * (size_t)cap);
+        }
+        for (int64_t e = 0; e < len; e++) {
+            ord[e].idx = list[cnt[t] + e];
+            ord[e].key = g[ord[e].idx].z;
+        }
+        qsort(ord, (size_t)len, sizeof(orc_ord), cmp_ord);
+        int tx = (int)(t % L.tiles_x), ty = (int)(t / L.tiles_x);
+        for (int py = ty * tile_h; py < ty * tile_h + tile_h && py < H; py++)
+            for (int px = tx * tile_w; px < tx * tile_w + tile_w && px < W; px++) {
+                /* forward: the blended pairs of this pixel */
+                double T = 1.0;
+                int64_t np_ = 0;
+                for (int64_t e = 0; e < len; e++) {
+                    const orc_g64* G = &g[ord[e].idx];
+                    double dx = px - G->u, dy = py - G->v;
+                    double p = -0.5 * (G->a * dx * dx + G->b * dx * dy + G->c * dy * dy);
+                    if (p > 0) continue;
+                    double ex = exp(p), at = G->op * ex;
+                    double alpha = at < 0.99 ? at : 0.99;
+                    if (alpha < 1.0 / 255.0) continue;
+                    double Tn = T * (1.0 - alpha);
+                    if (Tn < 1e-4) break;
+                    pr[np_].i = ord[e].idx; pr[np_].alpha = alpha; pr[np_].T = T; pr[np_].e = ex;
+                    pr[np_].dx = dx; pr[np_].dy = dy; pr[np_].clamped = !(at < 0.99);
+                    np_++;
+                    T = Tn;
+                }
+                double Gc[3], R[3];
+                for (int ch = 0; ch < 3; ch++) {
+                    Gc[ch] = dL_dimg[(int64_t)ch * H * W + (int64_t)py * W + px];
+                    R[ch] = T * (double)cam->bg[ch];
+                }
+                /* backward: back to front */
+                for (int64_t k = np_ - 1; k >= 0; k--) {
+                    const pair_t* P = &pr[k];
+                    const orc_g64* G = &g[P->i];
+                    double* gi = gimg + 9 * P->i;
+                    double dal = 0;
+                    for (int ch = 0; ch < 3; ch++) {
+                        gi[6 + ch] += Gc[ch] * P->alpha * P->T;
+                        dal += Gc[ch] * (G->rgb[ch] * P->T - R[ch] / (1.0 - P->alpha));
+                        R[ch] += G->rgb[ch] * P->alpha * P->T;
+                    }
+                    if (P->clamped) continue;
+                    gi[5] += dal * P->e;
+                    double dp = dal * P->alpha;
+                    gi[0] += dp * (G->a * P->dx + 0.5 * G->b * P->dy);
+                    gi[1] += dp * (0.5 * G->b * P->dx + G->c * P->dy);
+                    gi[2] += dp * (-0.5 * P->dx * P->dx);
+                    gi[3] += dp * (-0.5 * P->dx * P->dy);
+                    gi[4] += dp * (-0.5 * P->dy * P->dy);
+                }
+            }
+    }
+
+    /* per Gaussian: through (u, v, a, b, c) and the raw colour to the inputs */
+    const double h = 1e-30;
+    for (int64_t i = 0; i < n; i++) {
+        if (!bins[i].vis) continue;
+        const double* gi = gimg + 9 * i;
+        dopac[i] = gi[5];
+        cplx m0[3], q0[4], s0[3], raw[3];
+        for (int k = 0; k < 3; k++) { m0[k] = means[3 * i + k]; s0[k] = scales[3 * i + k]; }
+        for (int k = 0; k < 4; k++) q0[k] = quats[4 * i + k];
+        colour_raw_cplx(m0, sh + 48 * i, sh_deg, cam, raw);
+        double draw[3];
+        for (int ch = 0; ch < 3; ch++) {
+            double r = creal(raw[ch]);
+            draw[ch] = (r > 0.0 && r < 1.0) ? gi[6 + ch] : 0.0;
+        }
+        /* dL/dSH_k = Y_k dL/draw */
+        {
+            double campos[3];
+            for (int j = 0; j < 3; j++)
+                campos[j] = -((double)cam->R[j] * cam->t[0] + (double)cam->R[3 + j] * cam->t[1] +
+                              (double)cam->R[6 + j] * cam->t[2]);
+            double d[3] = {means[3 * i] - campos[0], means[3 * i + 1] - campos[1], means[3 * i + 2] - campos[2]};
+            double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double Y[16];
+            orc_sh_basis(d[0] / nd, d[1] / nd, d[2] / nd, Y);
+            int nk = (sh_deg + 1) * (sh_deg + 1);
+            for (int k = 0; k < nk; k++)
+                for (int ch = 0; ch < 3; ch++) dsh[48 * i + 3 * k + ch] = Y[k] * draw[ch];
+        }
+        for (int j = 0; j < 10; j++) { /* inputs: mean 0-2, quaternion 3-6, scale 7-9 */
+            cplx m[3], q[4], s[3], out[5];
+            for (int k = 0; k < 3; k++) { m[k] = m0[k]; s[k] = s0[k]; }
+            for (int k = 0; k < 4; k++) q[k] = q0[k];
+            if (j < 3) m[j] += h * _Complex_I;
+            else if (j < 7) q[j - 3] += h * _Complex_I;
+            else s[j - 7] += h * _Complex_I;
+            proj_cplx(m, q, s, cam, out);
+            double acc = 0;
+            for (int o = 0; o < 5; o++) acc += gi[o] * cimag(out[o]) / h;
+            if (j < 3) {
+                colour_raw_cplx(m, sh + 48 * i, sh_deg, cam, raw);
+                for (int ch = 0; ch < 3; ch++) acc += draw[ch] * cimag(raw[ch]) / h;
+                dmeans[3 * i + j] = acc;
+            } else if (j < 7) {
+                dquats[4 * i + j - 3] = acc;
+            } else {
+                dscales[3 * i + j - 7] = acc;
+            }
+        }
+    }
+    free(ord); free(pr); free(gimg); free(g); free(list); free(fill); free(cnt); free(bins);
+    return 0;
 }
