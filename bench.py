@@ -173,11 +173,18 @@ def stage_work(mode, st, W, H):
         ranges = 0  # no ranges pass: every rasterizer block searches its tile's range in the sorted keys
     else:
         depth = 0
-        # preprocess: 44 B geometry per Gaussian, 192 B FP32 SH + 56 B outputs if visible, 4 B count;
-        # scan: 8 B per Gaussian; duplicate: 4 B per Gaussian + 24 B per visible + 12 B per entry
-        front = 44 * N + 248 * nv + 4 * N + 8 * N + 4 * N + 24 * nv + 12 * nd
+        # preprocess: 12 B mean + 4 B entry count per Gaussian, 28 B quaternion + scale if in front,
+        # 4 B opacity + 192 B FP32 SH read and 64 B written (double-float mean, exponent
+        # coefficients, colour, rectangle, depth) if visible; scan: 8 B per Gaussian; duplicate: 8 B
+        # per Gaussian + 20 B per visible + 12 B per entry (64-bit key + value)
+        front = 32 * N + 28 * nf + 280 * nv + 12 * nd
         sort_pass = 24 * nd
-        hist = 8 * nd
+        if passes <= 6:
+            # the duplicate kernel counted every digit: the histogram kernel clears 1 KB of look-back
+            # status per 4096-entry tile and sums 16 copies of the [6][256] counts
+            hist = 1024 * ((nd + 4095) // 4096) + 17 * passes * 256 * 4
+        else:
+            hist = 8 * nd
         ranges = 8 * nd + 8 * tiles
     a, b = OPS[mode]
     raster_ops = a * st["n_pairs"] + b * st["n_blends"]

@@ -394,9 +394,11 @@ __global__ void __launch_bounds__(EX_THREADS) k_exact_preprocess(ExactArgs a)
     if (!front) return;
     const float4 q = *reinterpret_cast<const float4*>(&a.quats[4 * i]);
     Binned b;
-    if (!project_bin(a.cam, mx, my, mz, pz, q.x, q.y, q.z, q.w, a.scales[3 * i], a.scales[3 * i + 1],
-                     a.scales[3 * i + 2], false, 0.0f, b))
-        return;
+    const bool vis = project_bin(a.cam, mx, my, mz, pz, q.x, q.y, q.z, q.w, a.scales[3 * i], a.scales[3 * i + 1],
+                                 a.scales[3 * i + 2], false, 0.0f, b);
+    const unsigned vm = __ballot_sync(__activemask(), vis);
+    if (vis && __popc(vm & ((1u << (threadIdx.x & 31)) - 1u)) == 0) atomicAdd(&a.ctr->n_visible, (unsigned)__popc(vm));
+    if (!vis) return;
     // the rasterizer's exponent (Eq. (10)) with the quadratic form completed in dx:
     // -1/2 ((Sigma'_yy / det) (dx - c dy)^2 + dy^2 / Sigma'_yy), c = Sigma'_xy / Sigma'_yy
     // (no cancellation for thin Gaussians); the mean as double-floats (the FP32 u, v
@@ -495,23 +497,113 @@ __global__ void __launch_bounds__(EX_THREADS) k_exact_scan(ExactArgs a)
     }
 }
 
+// Duplicate (plain 3DGS, Sec. II-A): one (64-bit key, value) entry per tile of each
+// Gaussian's rectangle, at the Gaussian's exclusive-scan offset. The entries of a
+// warp's 32 consecutive Gaussians are contiguous and in (Gaussian, row, tile) order,
+// so the warp walks their tile rows 32 at a time (lane k takes the k-th row) and
+// writes 32 consecutive entries per store instruction, as the fused front end does.
+// It also counts the sort's digits: the four depth digits are the same for every
+// entry of a Gaussian (one shared atomic each per Gaussian), the tile digits of a
+// row are a run of consecutive tile ids (count_tile_digits); the block's counts go
+// to one of FE_HIST_COPIES copies once, at the end of its grid-stride loop.
+constexpr int DUP_HIST_STRIDE = 8; // passes per copy of the digit counts ([copy][8][256])
+
 __global__ void __launch_bounds__(EX_THREADS) k_exact_duplicate(ExactArgs a)
 {
-    const long long i = (long long)blockIdx.x * EX_THREADS + threadIdx.x;
-    if (i >= a.n) return;
-    const unsigned cnt = a.touched[i];
-    if (cnt == 0) return;
-    const unsigned long long off = a.offsets[i];
-    const int4 r = a.rect[i];
-    const unsigned long long zbits = (unsigned long long)__float_as_uint(a.depth[i]);
-    unsigned long long dst = off;
-    for (int ty = r.y; ty <= r.w; ty++)
-        for (int tx = r.x; tx <= r.z; tx++, dst++) {
-            if (dst >= (unsigned long long)a.cap) return;
-            const unsigned long long tile = (unsigned long long)(ty * a.lay.tiles_x + tx);
-            a.keys[dst] = (tile << 32) | zbits;
-            a.vals[dst] = (unsigned)i;
+    __shared__ unsigned s_hd[4][RADIX_FE];             // depth digits (key bits 0..31)
+    __shared__ unsigned s_d0[RADIX_FE + 1], s_h1[RADIX_FE]; // tile digits (key bits 32..47)
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool count = a.hist != nullptr;
+    if (count) {
+        for (int j = tid; j < 4 * RADIX_FE; j += EX_THREADS) (&s_hd[0][0])[j] = 0u;
+        for (int j = tid; j < 2 * RADIX_FE + 1; j += EX_THREADS) (j <= RADIX_FE ? s_d0[j] : s_h1[j - RADIX_FE - 1]) = 0u;
+        __syncthreads();
+    }
+    const unsigned tiles_x = (unsigned)a.lay.tiles_x;
+    for (long long base = (long long)blockIdx.x * EX_THREADS; base < a.n; base += (long long)gridDim.x * EX_THREADS) {
+        const long long i = base + tid;
+        unsigned cnt = 0, zb = 0, off = 0;
+        int4 r = make_int4(0, 0, -1, -1);
+        if (i < a.n) {
+            cnt = a.touched[i];
+            off = a.offsets[i];
+            if (cnt) {
+                r = a.rect[i];
+                zb = __float_as_uint(a.depth[i]);
+                if (count)
+#pragma unroll
+                    for (int p = 0; p < 4; p++) atomicAdd(&s_hd[p][(zb >> (8 * p)) & 255u], cnt);
+            }
         }
+        const int rows_l = cnt ? r.w - r.y + 1 : 0;
+        const unsigned width = cnt ? (unsigned)(r.z - r.x + 1) : 0u;
+        const unsigned rincl = warp_inclusive_scan((unsigned)rows_l, lane);
+        const unsigned rexcl = rincl - (unsigned)rows_l;
+        const unsigned wrows = __shfl_sync(0xffffffffu, rincl, 31);
+        // the warp's first entry: the offset of its first Gaussian (lanes past n hold the total)
+        unsigned long long out = __shfl_sync(0xffffffffu, off, 0);
+        for (unsigned r0 = 0; r0 < wrows; r0 += 32) {
+            const unsigned k = r0 + (unsigned)lane;
+            int owner = 0; // lane (Gaussian) of warp row k
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(0xffffffffu, rincl, owner + step - 1) <= k) owner += step;
+            const unsigned rl = k - __shfl_sync(0xffffffffu, rexcl, owner);
+            const unsigned ow = __shfl_sync(0xffffffffu, width, owner);
+            const int oty = __shfl_sync(0xffffffffu, r.y, owner);
+            const int otx = __shfl_sync(0xffffffffu, r.x, owner);
+            const unsigned oz = __shfl_sync(0xffffffffu, zb, owner);
+            unsigned w = 0, tb = 0;
+            if (k < wrows) {
+                w = ow;
+                tb = (unsigned)(oty + (int)rl) * tiles_x + (unsigned)otx; // tile of the row's first entry
+                if (count) count_tile_digits(s_d0, s_h1, a.tile_passes, tb, w);
+            }
+            const unsigned incl = warp_inclusive_scan(w, lane);
+            const unsigned chunk = __shfl_sync(0xffffffffu, incl, 31);
+            tb -= incl - w; // entry e of the chunk, if in this row, has tile tb + e
+            for (unsigned e0 = 0; e0 < chunk; e0 += 32) {
+                const unsigned e = e0 + (unsigned)lane;
+                int pos = 0; // row (lane) of entry e
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(0xffffffffu, incl, pos + step - 1) <= e) pos += step;
+                const unsigned tile = __shfl_sync(0xffffffffu, tb, pos) + e;
+                const unsigned z = __shfl_sync(0xffffffffu, oz, pos);
+                const unsigned gl = (unsigned)__shfl_sync(0xffffffffu, owner, pos);
+                const unsigned long long dst = out + e;
+                if (e < chunk && dst < (unsigned long long)a.cap) {
+                    a.keys[dst] = ((unsigned long long)tile << 32) | z;
+                    a.vals[dst] = (unsigned)(base + (long long)(tid & ~31) + gl);
+                }
+            }
+            out += chunk;
+        }
+    }
+    if (count) {
+        __syncthreads();
+        unsigned* const H = a.hist + (size_t)(blockIdx.x % FE_HIST_COPIES) * (DUP_HIST_STRIDE * RADIX_FE);
+        for (int j = tid; j < 4 * RADIX_FE; j += EX_THREADS) {
+            const unsigned c = (&s_hd[0][0])[j];
+            if (c) atomicAdd(&H[j], c);
+        }
+        if (tid < 32) { // the tile digits: difference array -> counts, 8 digits per lane
+            unsigned c[8], run = 0;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                run += s_d0[8 * lane + j];
+                c[j] = run;
+            }
+            const unsigned incl = warp_inclusive_scan(run, lane);
+            const unsigned before = incl - run;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (c[j] + before) atomicAdd(&H[4 * RADIX_FE + 8 * lane + j], c[j] + before);
+        }
+        if (a.tile_passes > 1)
+            for (int j = tid; j < RADIX_FE; j += EX_THREADS)
+                if (s_h1[j]) atomicAdd(&H[5 * RADIX_FE + j], s_h1[j]);
+    }
 }
 
 void launch_exact_preprocess(const ExactArgs& a, cudaStream_t s)
@@ -527,7 +619,9 @@ void launch_exact_scan(const ExactArgs& a, cudaStream_t s)
 void launch_exact_duplicate(const ExactArgs& a, cudaStream_t s)
 {
     if (a.n <= 0) return;
-    k_exact_duplicate<<<(unsigned)((a.n + EX_THREADS - 1) / EX_THREADS), EX_THREADS, 0, s>>>(a);
+    const long long need = (a.n + EX_THREADS - 1) / EX_THREADS;
+    const long long cap = 8ll * device_sm_count(); // grid-stride: digit counts flushed once per block
+    k_exact_duplicate<<<(unsigned)(need < cap ? need : cap), EX_THREADS, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------

@@ -234,6 +234,16 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         a.ctr = ctr;
         a.sticky = sticky;
         RG_CK(cudaMemsetAsync(w.lb_status.p, 0, (size_t)((n + 2047) / 2048 + 1) * 8, st));
+        sa.key_bytes = 8;
+        sa.passes = (32 + F.lay.b_t + 7) / 8; // only the bits that can be non-zero
+        tile_shift = 32;
+        if (sa.passes <= 6) { // up to 2 tile-bit passes: the duplicate kernel counts every digit
+            a.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + 2 * CTRL_BYTES);
+            a.tile_passes = sa.passes - 4;
+            sa.hist_copies = a.hist;
+            sa.hist_copy_stride = 8;
+            sa.hist_pre = hist + 2 * 256; // rows 2-7 of the frame's [8][256] histograms
+        }
         if (ev) RG_CK(cudaEventRecord(E[1], st));
         {
             NvtxScope r_("rg front end");
@@ -241,9 +251,6 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
             launch_exact_scan(a, st);
             launch_exact_duplicate(a, st);
         }
-        sa.key_bytes = 8;
-        sa.passes = (32 + F.lay.b_t + 7) / 8; // only the bits that can be non-zero
-        tile_shift = 32;
     } else {
         FrontendArgs a;
         memset(&a, 0, sizeof(a));
@@ -317,6 +324,7 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
                 a.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + 2 * CTRL_BYTES);
                 a.hist_passes = sa.passes;
                 sa.hist_copies = a.hist;
+                sa.hist_copy_stride = 2;
                 sa.hist_pre = hist + 4 * 256; // rows 4-5 of the frame's [8][256] histograms
                 a.keys16 = w.keys[0].as<unsigned short>();
                 sa.key_bytes = 2;

@@ -47,8 +47,9 @@ constexpr int EV_RING = 512;
 constexpr int EV_PER_FRAME = 7; // start, depth order, front end, histogram, sort, ranges, raster
 constexpr long long MAX_CAP = (1ll << 30) - 1;
 constexpr size_t CTRL_BYTES = sizeof(Counters) + 8 * 256 * sizeof(unsigned);
-// frame counters, the per-Gaussian depth sort's, then the front end's digit-count copies
-constexpr size_t FE_HIST_BYTES = (size_t)FE_HIST_COPIES * 2 * 256 * sizeof(unsigned);
+// frame counters, the per-Gaussian depth sort's, then the producers' digit-count copies
+// ([copy][2][256] from the fused front end, [copy][8][256] from the exact duplicate)
+constexpr size_t FE_HIST_BYTES = (size_t)FE_HIST_COPIES * 8 * 256 * sizeof(unsigned);
 constexpr size_t CTRL_ALLOC = 2 * CTRL_BYTES + FE_HIST_BYTES;
 
 // Frame workspace: everything one frame in flight needs besides the scene.

@@ -513,6 +513,9 @@ struct ExactArgs {
     unsigned long long* status; // scan look-back
     Counters* ctr;
     Sticky* sticky;
+    unsigned* hist;        // [FE_HIST_COPIES][8][256] the sort's digit counts (passes 0-3: depth bits,
+                           // 4-5: tile bits), counted by the duplicate kernel, or null
+    int tile_passes;       // 1 or 2 tile-bit passes (b_t <= 16) when hist is set
 };
 void launch_exact_preprocess(const ExactArgs& a, cudaStream_t s);
 void launch_exact_scan(const ExactArgs& a, cudaStream_t s);
@@ -528,8 +531,9 @@ struct SortArgs {
     int ballot_mask;      // bit p: rank pass p with ballots instead of match_any
     unsigned* hist;       // [8][256]
     unsigned* hist_pre;   // [passes][256] digit counts from the producer of the keys, or null
-    const unsigned* hist_copies; // [FE_HIST_COPIES][2][256] the producer's partial counts (summed into
-                                 // hist_pre), or null if hist_pre is complete already
+    const unsigned* hist_copies; // [FE_HIST_COPIES][hist_copy_stride][256] the producer's partial counts
+                                 // (summed into hist_pre), or null if hist_pre is complete already
+    int hist_copy_stride;        // passes per copy of hist_copies
     unsigned* status[2];  // [max_tiles][256] look-back status per pass (alternating)
     long long max_tiles;
     Counters* ctr;

@@ -117,11 +117,12 @@ static int sm_count() { return device_sm_count(); }
 
 // The producer's digit counts cover every entry it made; they are not used when
 // entries did not fit (overflow) or its allocation gave up waiting (the error bit
-// of its look-back): the histogram kernel then counts the stored keys. Both flags
+// of its look-back, or of the exact scan's): the histogram kernel then counts the
+// stored keys. Both flags
 // are final before the sort starts.
 __device__ __forceinline__ bool recount_digits(const Counters* ctr)
 {
-    return ctr->overflow != 0u || (ctr->error & ERR_FE_LOOKBACK) != 0u;
+    return ctr->overflow != 0u || (ctr->error & (ERR_FE_LOOKBACK | ERR_SCAN_LOOKBACK)) != 0u;
 }
 
 // Digit histograms of every pass in one read of the keys (vector loads; the
@@ -133,7 +134,7 @@ template <typename K>
 __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ keys, int passes, int bit0,
                                                          unsigned* hist, unsigned* status0,
                                                          const Counters* __restrict__ ctr, unsigned* hist_pre,
-                                                         const unsigned* __restrict__ hist_copies)
+                                                         const unsigned* __restrict__ hist_copies, int copy_stride)
 {
     __shared__ unsigned s_h[8][RADIX];
     for (int j = threadIdx.x; j < 8 * RADIX; j += H_THREADS) (&s_h[0][0])[j] = 0u;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ k
         if (!hist_copies) return;
         for (long long c = gid; c < (long long)passes * RADIX; c += gsz) {
             unsigned sum = 0u;
-            for (int j = 0; j < FE_HIST_COPIES; j++) sum += hist_copies[(size_t)j * 2 * RADIX + c];
+            for (int j = 0; j < FE_HIST_COPIES; j++) sum += hist_copies[(size_t)j * copy_stride * RADIX + c];
             hist_pre[c] = sum;
         }
         return;
@@ -458,7 +459,7 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
     const K* kin = (const K*)a.keys[0];
     if (a.passes <= 0) return;
     k_sort_hist<K><<<hist_grid, H_THREADS, 0, s>>>(kin, a.passes, a.bit0, a.hist, a.status[0], a.ctr, a.hist_pre,
-                                                   a.hist_copies);
+                                                   a.hist_copies, a.hist_copy_stride > 0 ? a.hist_copy_stride : 2);
     if (ev_after_hist) cudaEventRecord(ev_after_hist, s);
     for (int p = 0; p < a.passes; p++) {
         const int src = p & 1, dst = src ^ 1;

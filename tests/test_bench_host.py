@@ -39,5 +39,10 @@ def test_roofgs_more_than_16_tile_bits_and_exact_mode():
     assert w["sort_pass"] == 16 * nd and w["hist"] == 4 * nd  # 32-bit keys, keys read for the digits
     assert w["front"] == 20 * 3_000_000 + 16 * 2_500_000 + 80 * 2_000_000 + 8 * nd
     w = bench.stage_work("exact", _stats(6), 3840, 2160)
-    assert w["sort_pass"] == 24 * nd and w["hist"] == 8 * nd and w["depth"] == 0
+    assert w["sort_pass"] == 24 * nd and w["depth"] == 0
+    # the duplicate kernel counts the digits of all 6 passes (4 depth + 2 tile digits)
+    assert w["hist"] == 1024 * ((nd + 4095) // 4096) + 17 * 6 * 256 * 4
+    assert w["front"] == 32 * 3_000_000 + 28 * 2_500_000 + 280 * 2_000_000 + 12 * nd
     assert w["ranges"] == 8 * nd + 8 * 240 * 135
+    w = bench.stage_work("exact", _stats(7, tiles_x=480, tiles_y=270), 7680, 4320)
+    assert w["hist"] == 8 * nd  # 3 tile digits: the keys are read for the digits

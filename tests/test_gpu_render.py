@@ -331,6 +331,33 @@ def test_capacity_overflow_regrows_and_is_reported():
     small.check()
 
 
+def test_exact_capacity_overflow_recounts_digits():
+    """Exact mode with too small a workspace: the entries that fit are the first ones the
+    duplicate kernel emitted (Gaussian by Gaussian, tiles ascending), and their sort must
+    not use the duplicate kernel's digit counts (which cover every entry): the clipped
+    sort equals the oracle's first entries, sorted. A checked render then regrows."""
+    sc, cams = synth.workload("tiny_256")
+    cam = cams[0]
+    ref = render(gpu_scene(sc), cam, "exact")
+    small = gpu_scene(sc)
+    small.reserve(3000)
+    small.render(cam, mode="exact")
+    torch.cuda.synchronize()
+    gk = small.inspect(binding.RG_INSPECT_KEYS).view(np.uint64)
+    gv = small.inspect(binding.RG_INSPECT_VALUES)
+    k, v, _, _ = oracle.keys(sc, cam, oracle.EXACT)
+    assert 0 < gk.size < k.size
+    emitted = np.lexsort((k, v))[: gk.size]
+    expect = emitted[np.lexsort((v[emitted], k[emitted]))]
+    assert np.array_equal(gk, k[expect]) and np.array_equal(gv, v[expect])
+    with pytest.raises(binding.RgError) as e:
+        small.check()
+    assert e.value.status == 4
+    img, st = render(small, cam, "exact", stats=True)
+    assert st["regrown"] == 1 and np.array_equal(img, ref)
+    small.check()
+
+
 def test_stage_times_and_counters(tiny):
     sc, cam, gs, _ = tiny
     for _ in range(3):
