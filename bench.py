@@ -387,7 +387,7 @@ def run_ours(a, rank, world, local_rank):
     line["clocks"] = {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if clocks else None
     line.update(extra)
     if world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a, sc, cams, budget_tiles=64)
+        line["cpu_baseline"] = cpu_baseline(a, sc, cams)
     if dist is not None:
         dist.destroy_process_group()
     return line
@@ -540,7 +540,9 @@ def run_ortho(a, sc, cams, gs, dev):
 
 def run_serve(dev, gs3, ppt=2):
     """Request loop: 4 resident scenes (0.5M, 1M, 3M, 6M), Poisson arrivals of 720p/1080p/4K requests
-    with random orbit poses; p50/p99 latency (submit -> image ready) and FPS at several request rates."""
+    with random orbit poses, swept from 100 to 3200 requests/s (past saturation). Per rate: delivered
+    FPS, p50/p99 latency to the image ready in its slot and to the image copied into the caller's
+    buffer by rg_poll."""
     import threading
 
     import numpy as np
@@ -554,11 +556,12 @@ def run_serve(dev, gs3, ppt=2):
     srv = binding.Server(scenes, 3840, 2160, mode="roofgs", max_slots=8, memory_budget=96 << 30,
                          calibration=synth.orbit_camera(0, 3840, 2160),
                          flags={1: binding.RG_FLAG_SINGLE_PIXEL, 2: 0, 4: binding.RG_FLAG_QUAD_PIXEL}[ppt])
+    slots = srv.stats()["slots"]
     pool = [torch.empty((3, 2160, 3840), device=dev) for _ in range(16)]
     rng = np.random.default_rng(11)
     results = []
-    for rate in (100.0, 200.0, 400.0):
-        n_req = int(rate * 2.0)  # about two seconds of arrivals
+    for rate in (100.0, 200.0, 400.0, 800.0, 1600.0, 3200.0):
+        n_req = max(150, min(int(rate * 1.5), 2400))  # about 1.5 s of arrivals
         gaps = rng.exponential(1.0 / rate, size=n_req)
         reqs = []
         for k in range(n_req):
@@ -566,17 +569,18 @@ def run_serve(dev, gs3, ppt=2):
             reqs.append((synth.orbit_camera(float(rng.uniform(0, 30)), w, h), int(rng.integers(4))))
         srv.reset_stats()
         tickets, lock = [], threading.Lock()
-        finished = {"n": 0}
+        span = {}
 
         def submitter():
-            t_next = time.perf_counter()
+            t_start = t_next = time.perf_counter()
             for (cam, sidx), gap in zip(reqs, gaps):
                 t_next += gap
                 while time.perf_counter() < t_next:
-                    time.sleep(0.0002)
+                    time.sleep(0.0001)
                 t = srv.submit(cam, sidx)
                 with lock:
-                    tickets.append((t, cam))
+                    tickets.append(t)
+            span["submit_s"] = time.perf_counter() - t_start
 
         th = threading.Thread(target=submitter)
         t0 = time.perf_counter()
@@ -585,32 +589,44 @@ def run_serve(dev, gs3, ppt=2):
         outstanding = []
         while done < n_req:
             with lock:
-                while tickets:
-                    outstanding.append(tickets.pop(0))
-            still = []
-            for t, cam in outstanding:
+                outstanding.extend(tickets)
+                tickets.clear()
+            # admission is first come first served: every request holding a slot is older than every
+            # queued one, so the 2 x slots oldest outstanding tickets cover all that can be ready
+            head, still = outstanding[: 2 * slots], []
+            for t in head:
                 if srv.poll(t, pool[t % len(pool)]):  # the pool buffers hold the largest image
                     done += 1
                 else:
-                    still.append((t, cam))
-            outstanding = still
-            time.sleep(0.0003)
+                    still.append(t)
+            outstanding = still + outstanding[2 * slots:]
+            time.sleep(0.0001)
         th.join()
         wall = time.perf_counter() - t0
         st = srv.stats()
-        results.append({"offered_req_per_s": rate, "requests": n_req, "fps": round(n_req / wall, 1),
+        offered = n_req / span["submit_s"]
+        results.append({"offered_req_per_s": rate, "achieved_offered_req_per_s": round(offered, 1),
+                        "requests": n_req, "fps": round(n_req / wall, 1),
                         "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                        "p50_delivered_ms": round(st["p50_delivered_ms"], 3),
+                        "p99_delivered_ms": round(st["p99_delivered_ms"], 3),
                         "max_in_flight": st["max_in_flight"]})
-    slots = srv.stats()["slots"]
     srv.close()
     for g in scenes:
         g.check()
     for g in extra:
         g.close()
+    # saturation: the first rate whose delivered FPS falls below 90 % of the achieved offered rate
+    sat = next((r for r in results if r["fps"] < 0.9 * r["achieved_offered_req_per_s"]), None)
     return {"workload": "4 resident scenes (0.5M, 1M, 3M, 6M clustered Gaussians), Poisson arrivals, "
                         "1280x720 / 1920x1080 / 3840x2160 equally likely, uniform orbit azimuth; RoofGS mode",
             "slots": slots, "rates": results,
-            "latency": "submit to image ready in the slot, host clock of the dispatcher"}
+            "saturation": None if sat is None else {
+                "offered_req_per_s": sat["offered_req_per_s"], "delivered_fps": sat["fps"],
+                "max_delivered_fps": max(r["fps"] for r in results)},
+            "latency": "p50/p99_ms: submit to image ready in its slot (dispatcher's host clock); "
+                       "p50/p99_delivered_ms: submit to image copied into the caller's buffer by rg_poll "
+                       "(includes the caller's polling delay)"}
 
 
 def rooflines(r, a, props, clocks):
@@ -672,87 +688,132 @@ def oracle_setup(sc):
     return oracle, comp
 
 
-def oracle_frame_seconds(oracle, sc, comp, cam, stride, t_bin=None):
-    """Binning of every Gaussian + FP64 blend of every `stride`-th tile, extrapolated to the frame."""
-    lay = oracle.layout(cam)
-    nt = lay["tiles_x"] * lay["tiles_y"]
+# ---------------------------------------------------------------------------
+# CPU oracle timing: whole frames on the host cores (no extrapolation)
+# ---------------------------------------------------------------------------
+_ORC = {}
+
+
+def _scene_of(spec):
+    """(scene, cameras, per-Gaussian SH scale) of a workload spec: ("bench", args) is the
+    benchmark's own workload, otherwise a named workload of synth."""
+    from paper_2608_15785_gb300 import synth
+    kind, args = spec
+    if kind == "bench":
+        sc, cams = make_inputs(args)
+        return sc, cams, True
+    sc, cams = synth.workload(kind)
+    return sc, cams, False
+
+
+def _oracle_init(spec, barrier):
+    """Worker start-up (spawn): the seeded scene and its compact attributes, once per process."""
+    import oracle
+    sc, cams, per_gauss = _scene_of(spec)
+    oracle.build()
+    _ORC.update(sc=sc, cams=cams, comp=oracle.compact(sc, per_gauss), oracle=oracle)
+    barrier.wait()
+
+
+def _oracle_part(job):
+    """The oracle's render of pose `pose`: binning of every Gaussian (one sequential pass) and the
+    FP64 blend of tiles w, w + P, w + 2P, ... (P workers together cover every tile once)."""
     import numpy as np
-    if t_bin is None:
+    pose, w, workers = job
+    o, sc, comp = _ORC["oracle"], _ORC["sc"], _ORC["comp"]
+    cam = _ORC["cams"][pose % len(_ORC["cams"])]
+    lay = o.layout(cam)
+    tiles = np.arange(w, lay["tiles_x"] * lay["tiles_y"], workers, dtype=np.int32)
+    t0 = time.perf_counter()
+    o.render(sc, cam, o.ROOFGS, comp=comp, tiles=tiles, with_diag=False)
+    return time.perf_counter() - t0, int(tiles.size)
+
+
+class OracleFrames:
+    """Whole oracle frames (RoofGS mode, exact exp) of one workload on `workers` host processes:
+    each process bins every Gaussian and blends an interleaved 1/P of the tiles; a frame's time is
+    the wall clock from dispatch until every part is back."""
+
+    def __init__(self, spec, workers):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.workers = workers
+        barrier = ctx.Barrier(workers + 1)
+        self.pool = ctx.Pool(workers, initializer=_oracle_init, initargs=(spec, barrier))
+        barrier.wait()  # every worker holds the scene
+
+    def frame(self, pose):
         t0 = time.perf_counter()
-        oracle.render(sc, cam, oracle.ROOFGS, comp=comp, tiles=np.zeros(0, np.int32), with_diag=False)
-        t_bin = time.perf_counter() - t0
-    tiles = np.arange(0, nt, stride, dtype=np.int32)
+        parts = self.pool.map(_oracle_part, [(pose, w, self.workers) for w in range(self.workers)], chunksize=1)
+        return time.perf_counter() - t0, sum(k for _, k in parts)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _single_core_frame(spec):
+    import oracle
+    sc, cams, per_gauss = _scene_of(spec)
+    oracle.build()
+    comp = oracle.compact(sc, per_gauss)
     t0 = time.perf_counter()
-    oracle.render(sc, cam, oracle.ROOFGS, comp=comp, tiles=tiles, with_diag=False)
-    t = time.perf_counter() - t0
-    return t_bin + max(t - t_bin, 0.0) * nt / len(tiles), t_bin, len(tiles), nt
+    oracle.render(sc, cams[0], oracle.ROOFGS, comp=comp, with_diag=False)
+    return time.perf_counter() - t0
 
 
-def _oracle_worker(job):
-    """One host core: the seeded scene again, the oracle's binning of every Gaussian and the FP64
-    blend of tiles w, w + P*stride, ... of pose 0 (P workers). Returns (binning s, blend s, tiles)."""
-    a, w, workers, stride = job
-    import numpy as np
-    sc, cams = make_inputs(a)
-    oracle, comp = oracle_setup(sc)
-    cam = cams[0]
-    lay = oracle.layout(cam)
-    nt = lay["tiles_x"] * lay["tiles_y"]
-    t0 = time.perf_counter()
-    oracle.render(sc, cam, oracle.ROOFGS, comp=comp, tiles=np.zeros(0, np.int32), with_diag=False)
-    t_bin = time.perf_counter() - t0
-    tiles = np.arange(w * stride, nt, workers * stride, dtype=np.int32)
-    t0 = time.perf_counter()
-    oracle.render(sc, cam, oracle.ROOFGS, comp=comp, tiles=tiles, with_diag=False)
-    return t_bin, max(time.perf_counter() - t0 - t_bin, 0.0), len(tiles)
-
-
-def cpu_baseline(a, sc, cams, budget_tiles=64):
-    """The oracle on pose 0: on one core (every 64th tile blended), and on every host core (one
-    process each, spawn context, interleaved tile samples); frame times extrapolated to all tiles."""
-    import multiprocessing as mp
-    oracle, comp = oracle_setup(sc)
-    sec, t_bin, ns, nt = oracle_frame_seconds(oracle, sc, comp, cams[0], budget_tiles)
-    single = {"value": round(1.0 / sec, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-              "sample": "pose 0: FP32 binning of all %d Gaussians (%.1f s) + FP64 blend of every %dth tile "
-                        "(%d of %d), extrapolated to the full frame" % (a.gaussians, t_bin, budget_tiles, ns, nt)}
+def cpu_baseline(a, sc, cams):
+    """The oracle timed in whole frames: the benchmark's workload (pose 0) on every host core, the
+    1920x1080 workload (500k Gaussians) on every core and on one, the 256x256 one (10k) on one."""
     workers = os.cpu_count() or 1
-    if workers <= 1:
-        return single
-    stride = 16
-    with mp.get_context("spawn").Pool(workers) as pool:
-        res = pool.map(_oracle_worker, [(a, w, workers, stride) for w in range(workers)])
-    # each core bins every Gaussian (the oracle's binning is one sequential pass) and blends 1/P of
-    # the tiles at its own measured per-tile time under full load
-    frame = max(tb + (tt / max(k, 1)) * nt / workers for tb, tt, k in res)
-    done = sum(k for _, _, k in res)
-    return {"value": round(1.0 / frame, 5), "unit": UNIT, "cores": workers, "kind": "oracle",
-            "sample": "pose 0 on %d processes: each bins all %d Gaussians and blends an interleaved 1/%d of "
-                      "every %dth tile (%d tiles in all); frame = slowest process's binning + its per-tile time x "
-                      "%d tiles / %d" % (workers, a.gaussians, workers, stride, done, nt, workers),
-            "single_core": single}
+    of = OracleFrames(("bench", a), workers)
+    sec, tiles = of.frame(0)
+    of.close()
+    out = {"value": round(1.0 / sec, 5), "unit": UNIT, "cores": workers, "kind": "oracle",
+           "sample": "one whole frame (pose 0, all %d tiles) of this workload: %d processes each bin all %d "
+                     "Gaussians and blend an interleaved 1/%d of the tiles; %.2f s wall" % (
+                         tiles, workers, a.gaussians, workers, sec)}
+    of = OracleFrames(("clustered_1080p", None), workers)
+    sec2, _ = of.frame(0)
+    of.close()
+    out["clustered_1080p_all_cores"] = {"fps": round(1.0 / sec2, 4), "s_per_frame": round(sec2, 3),
+                                        "cores": workers, "frame": "whole 1920x1080 frame, 500k Gaussians"}
+    s2 = _single_core_frame(("clustered_1080p", None))
+    out["clustered_1080p_single_core"] = {"fps": round(1.0 / s2, 4), "s_per_frame": round(s2, 3), "cores": 1}
+    s1 = _single_core_frame(("tiny_256", None))
+    out["tiny_256_single_core"] = {"fps": round(1.0 / s1, 3), "s_per_frame": round(s1, 4), "cores": 1,
+                                   "frame": "whole 256x256 frame, 10k Gaussians"}
+    return out
 
 
 def run_reference(a, rank, world):
+    """The oracle as the reference arm: whole frames of the benchmark's workload on every host core
+    (rank 0 only). Each step is one whole frame of the next orbit pose; at most 3 timed and 1 warm-up
+    frames (a frame takes seconds), so the run ends within a few minutes."""
     if rank != 0:
         return None
-    sc, cams = make_inputs(a)
-    oracle, comp = oracle_setup(sc)
-    stride = 256
-    _, t_bin, ns, nt = oracle_frame_seconds(oracle, sc, comp, cams[0], stride)
-    for k in range(a.warmup):
-        oracle_frame_seconds(oracle, sc, comp, cams[k % len(cams)], stride, t_bin)
-    secs = [oracle_frame_seconds(oracle, sc, comp, cams[k % len(cams)], stride, t_bin)[0] for k in range(a.steps)]
+    workers = os.cpu_count() or 1
+    steps, warmup = min(a.steps, 3), min(a.warmup, 1)
+    t_start = time.perf_counter()
+    of = OracleFrames(("bench", a), workers)
+    for k in range(warmup):
+        of.frame(k)
+    secs = [of.frame(warmup + k)[0] for k in range(steps)]
+    of.close()
     total = sum(secs)
-    fps = a.steps / total
-    sample = ("per step: FP32 binning of all %d Gaussians (measured once, %.1f s) + FP64 blend of every %dth tile "
-              "(%d of %d) of one orbit pose, extrapolated to the full frame" % (a.gaussians, t_bin, stride, ns, nt))
-    return {"metric": METRIC, "value": round(fps, 5), "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": round(1000 * total / a.steps, 2), "higher_is_better": True,
+    fps = steps / total
+    sample = ("whole frames of this workload (orbit poses %d-%d, every tile) on %d processes: each bins all %d "
+              "Gaussians and blends an interleaved 1/%d of the tiles" % (warmup, warmup + steps - 1, workers,
+                                                                         a.gaussians, workers))
+    return {"metric": METRIC, "value": round(fps, 5), "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": round(1000 * total / steps, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "steps_requested": a.steps, "warmup_requested": a.warmup,
+            "wall_s": round(time.perf_counter() - t_start, 2),
             "config": {"workload": workload_desc(a), "mode": "roofgs (oracle, exact exp)",
                        "n_gaussians": a.gaussians, "resolution": [a.width, a.height], "poses": a.poses},
-            "cpu_baseline": {"value": round(fps, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": round(fps, 5), "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": round(fps, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -355,6 +355,8 @@ typedef struct {
     int32_t max_in_flight; /* most requests rendering at once since the last reset */
     double p50_ms, p99_ms; /* submit -> result ready latency percentiles since the last reset */
     int64_t slot_bytes;    /* calibrated bytes per slot */
+    double p50_delivered_ms, p99_delivered_ms; /* submit -> image copied into the caller's buffer by
+                                                  rg_poll (includes the caller's polling delay) */
 } rg_server_stats_t;
 
 /* Create a server over n_scenes resident scenes (the scenes must outlive it). Synchronous. */
@@ -365,9 +367,10 @@ rg_status rg_server_destroy(rg_server* server);
 rg_status rg_submit(rg_server* server, const rg_camera* cam, int32_t scene_slot, uint64_t* ticket);
 /*
  * RG_ERR_NOT_READY while the request waits or renders. When it is done, copy its
- * image into out_chw (device [3][H][W] of the request's camera), free the slot and
- * return RG_OK (or the request's error: RG_ERR_TIMEOUT, RG_ERR_CAPACITY, ...).
- * A ticket can be collected once.
+ * image into out_chw ([3][H][W] of the request's camera, device or pinned host
+ * memory; the copy is complete when rg_poll returns), free the slot and return
+ * RG_OK (or the request's error: RG_ERR_TIMEOUT, RG_ERR_CAPACITY, ...). A ticket
+ * can be collected once.
  */
 rg_status rg_poll(rg_server* server, uint64_t ticket, float* out_chw);
 rg_status rg_server_stats(rg_server* server, rg_server_stats_t* stats);

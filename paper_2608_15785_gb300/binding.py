@@ -81,7 +81,8 @@ class RgServerConfig(C.Structure):
 
 class RgServerStats(C.Structure):
     _fields_ = [("completed", C.c_int64), ("pending", C.c_int64), ("slots", C.c_int32), ("max_in_flight", C.c_int32),
-                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("slot_bytes", C.c_int64)]
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("slot_bytes", C.c_int64),
+                ("p50_delivered_ms", C.c_double), ("p99_delivered_ms", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -324,7 +325,7 @@ class Server:
         return t.value
 
     def poll(self, ticket: int, out) -> bool:
-        """True once the image has been copied into `out` ([3, H, W] CUDA tensor); False while not ready."""
+        """True once the image has been copied into `out` ([3, H, W] CUDA or pinned host tensor); False while not ready."""
         st = lib().rg_poll(self._h, C.c_uint64(ticket), C.c_void_p(out.data_ptr()))
         if st == 7:  # RG_ERR_NOT_READY
             return False

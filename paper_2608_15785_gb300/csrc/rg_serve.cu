@@ -62,6 +62,7 @@ struct rg_server {
     bool stop = false;
     uint64_t next_ticket = 1;
     std::vector<double> latencies_ms; // submit -> result ready
+    std::vector<double> delivered_ms; // submit -> image in the caller's buffer (rg_poll)
     int max_in_flight = 0;
     int64_t completed = 0;
     std::string error;
@@ -308,13 +309,15 @@ rg_status rg_poll(rg_server* server, uint64_t ticket, float* out_chw)
     rg_status res = hit->result;
     if (res == RG_OK) {
         const size_t bytes = (size_t)3 * hit->F.cam.W * hit->F.cam.H * 4;
-        cudaError_t e = cudaMemcpyAsync(out_chw, hit->out, bytes, cudaMemcpyDeviceToDevice, hit->stream);
+        cudaError_t e = cudaMemcpyAsync(out_chw, hit->out, bytes, cudaMemcpyDefault, hit->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(hit->stream);
         if (e != cudaSuccess) res = fail(RG_ERR_CUDA, cudaGetErrorString(e));
     } else {
         fail(res, "request failed");
     }
+    const double delivered = std::chrono::duration<double, std::milli>(Clock::now() - hit->req.submitted).count();
     std::lock_guard<std::mutex> lock(server->mu);
+    if (res == RG_OK) server->delivered_ms.push_back(delivered);
     hit->state = ServeSlot::FREE;
     server->cv.notify_all();
     return res;
@@ -324,9 +327,15 @@ rg_status rg_server_stats(rg_server* server, rg_server_stats_t* st)
 {
     if (!server || !st) return fail(RG_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lock(server->mu);
-    std::vector<double> l = server->latencies_ms;
+    std::vector<double> l = server->latencies_ms, d = server->delivered_ms;
     std::sort(l.begin(), l.end());
-    auto pct = [&](double p) { return l.empty() ? 0.0 : l[std::min(l.size() - 1, (size_t)(p * (l.size() - 1) + 0.5))]; };
+    std::sort(d.begin(), d.end());
+    auto pct_of = [](const std::vector<double>& v, double p) {
+        return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))];
+    };
+    auto pct = [&](double p) { return pct_of(l, p); };
+    st->p50_delivered_ms = pct_of(d, 0.50);
+    st->p99_delivered_ms = pct_of(d, 0.99);
     st->completed = server->completed;
     st->pending = (int64_t)server->pending.size();
     st->slots = (int32_t)server->slots.size();
@@ -342,6 +351,7 @@ rg_status rg_server_reset_stats(rg_server* server)
     if (!server) return fail(RG_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lock(server->mu);
     server->latencies_ms.clear();
+    server->delivered_ms.clear();
     server->completed = 0;
     server->max_in_flight = 0;
     return RG_OK;

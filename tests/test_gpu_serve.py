@@ -68,6 +68,8 @@ def test_results_alone_equal_results_in_the_mix(scenes, mode):
     assert st["completed"] == len(reqs) and st["slots"] == 3
     assert st["max_in_flight"] >= 2  # requests overlapped on the device
     assert 0 < st["p50_ms"] <= st["p99_ms"]
+    # latency to the caller's buffer (rg_poll) is measured too and cannot be shorter
+    assert 0 < st["p50_delivered_ms"] <= st["p99_delivered_ms"] and st["p50_delivered_ms"] >= st["p50_ms"] * 0.999
     for k, (cam, s) in enumerate(reqs):
         ref = scenes[s].render(cam, mode=mode)
         torch.cuda.synchronize()
@@ -100,4 +102,16 @@ def test_slot_growth_and_admission_errors(scenes):
         srv.submit(near, 5)  # no such scene
     with pytest.raises(binding.RgError):
         srv.poll(12345, out)  # unknown ticket
+    srv.close()
+
+
+def test_result_delivered_into_pinned_host_memory(scenes):
+    """rg_poll copies the image into the caller's buffer, which may be pinned host memory."""
+    srv = binding.Server(scenes, 640, 360, mode="roofgs", max_slots=2)
+    cam, sidx = _request(3)
+    host = torch.empty((3, cam.height, cam.width), dtype=torch.float32, pin_memory=True)
+    _collect(srv, [srv.submit(cam, sidx)], [host])
+    ref = scenes[sidx].render(cam, mode="roofgs")
+    torch.cuda.synchronize()
+    assert torch.equal(host, ref.cpu())
     srv.close()
