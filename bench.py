@@ -410,28 +410,41 @@ def run_batch(a, sc3, gs3, dev):
         return [synth.orbit_camera(int(poses[r, v]), *sizes[v % 4]) for v in range(32)]
 
     scenes = [gs1, gs3]
-    t0 = time.perf_counter()
-    binding.render_batch(scenes, idx, cams(0), mode="roofgs")  # plan: size, autotune, capture
-    torch.cuda.synchronize(dev)
-    plan_s = time.perf_counter() - t0
-    # checked calls size the lanes for both pose sets; checked single renders size the scenes
-    for r in (0, 1):
-        binding.render_batch(scenes, idx, cams(r), mode="roofgs", flags=binding.RG_FLAG_BATCH_CHECKED)
-        for v, c in enumerate(cams(r)):
-            scenes[idx[v]].render(c, mode="roofgs", stats=True)
-    torch.cuda.synchronize(dev)
-    lanes, ppt, tw, th = binding.batch_plan_info(scenes, idx, cams(0), mode="roofgs")
     outs = [torch.empty((3, h, w), device=dev) for (w, h) in [sizes[v % 4] for v in range(32)]]
     reps = 6
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    binding.render_batch(scenes, idx, cams(1), mode="roofgs", outs=outs)
-    e0.record()
-    for r in range(reps):
-        binding.render_batch(scenes, idx, cams(r % 2), mode="roofgs", outs=outs)
-    e1.record()
+
+    def timed_batch(flags):
+        t0 = time.perf_counter()
+        binding.render_batch(scenes, idx, cams(0), mode="roofgs", flags=flags)  # plan: size, autotune, capture
+        torch.cuda.synchronize(dev)
+        plan_s = time.perf_counter() - t0
+        # checked calls size the plan for both pose sets
+        for r in (0, 1):
+            binding.render_batch(scenes, idx, cams(r), mode="roofgs", flags=flags | binding.RG_FLAG_BATCH_CHECKED)
+        torch.cuda.synchronize(dev)
+        lanes, ppt, tw, th, fused = binding.batch_plan_info(scenes, idx, cams(0), mode="roofgs", flags=flags,
+                                                            with_path=True)
+        binding.render_batch(scenes, idx, cams(1), mode="roofgs", outs=outs, flags=flags)
+        e0.record()
+        for r in range(reps):
+            binding.render_batch(scenes, idx, cams(r % 2), mode="roofgs", outs=outs, flags=flags)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        return ms, {"path": "fused" if fused else "lanes", "lanes": lanes, "pixels_per_thread": ppt,
+                    "tile": [tw, th], "plan_seconds": round(plan_s, 2), "views_per_s": round(32 / (ms * 1e-3), 1),
+                    "ms_per_batch": round(ms, 3)}
+
+    batch_ms, tuned = timed_batch(0)
+    fused_ms, fused_info = timed_batch(binding.RG_FLAG_BATCH_FUSED)
+    lanes_ms, lanes_info = timed_batch(binding.RG_FLAG_BATCH_LANES)
+    # checked single renders size the scenes' own workspaces, then the same 32 views one
+    # rg_render at a time
+    for r in (0, 1):
+        for v, c in enumerate(cams(r)):
+            scenes[idx[v]].render(c, mode="roofgs", stats=True)
     torch.cuda.synchronize(dev)
-    batch_ms = e0.elapsed_time(e1) / reps
-    # the same 32 views one rg_render at a time
     e0.record()
     for r in range(reps):
         for v, c in enumerate(cams(r % 2)):
@@ -446,7 +459,9 @@ def run_batch(a, sc3, gs3, dev):
                         "8 each of 1280x720, 1920x1080, 2560x1440, 3840x2160; RoofGS mode",
             "views_per_s": round(32 / (batch_ms * 1e-3), 1), "ms_per_batch": round(batch_ms, 3),
             "sequential_views_per_s": round(32 / (seq_ms * 1e-3), 1), "speedup_vs_sequential": round(seq_ms / batch_ms, 3),
-            "autotuned": {"lanes": lanes, "pixels_per_thread": ppt, "tile": [tw, th]}, "plan_seconds": round(plan_s, 2)}
+            "autotuned": tuned, "fused_path": fused_info, "lanes_path": lanes_info,
+            "fused_speedup_vs_sequential": round(seq_ms / fused_ms, 3),
+            "lanes_speedup_vs_sequential": round(seq_ms / lanes_ms, 3)}
 
 
 def run_backward(dev):

@@ -120,6 +120,10 @@ typedef struct {
 /* flags for both modes */
 #define RG_FLAG_STAGE_EVENTS (1u << 8) /* record per-stage CUDA events (rg_stage_times) */
 #define RG_FLAG_BATCH_CHECKED (1u << 9) /* rg_render_batch: synchronise, and re-size and render again on overflow */
+/* rg_render_batch: keep only the fused path (RoofGS, at most 32 views) or only the lanes (the
+ * autotuner chooses between them otherwise) */
+#define RG_FLAG_BATCH_FUSED (1u << 11)
+#define RG_FLAG_BATCH_LANES (1u << 12)
 /* test hook for the failure path: the first radix pass of the entry sort never processes its
  * first tile, so the next tile's bounded look-back wait runs out (about a second); the frame
  * is invalid, kernels finish with in-bounds writes only, and the next rg_scene_check (or this
@@ -307,25 +311,30 @@ rg_status rg_backward(rg_scene* scene, const rg_camera* cam, const rg_render_opt
  * (scenes, resolutions, mode, flags) creates a plan: lanes of stream + workspace,
  * sized by rendering every view once per candidate tile shape (synchronous), then an
  * autotuner times the captured batch with every tile shape (16 x 16, 32 x 8, 8 x 32,
- * unless opts gives one), 1, 2 and 4 lanes and 1, 2 and 4 pixels per thread (RoofGS)
- * and keeps the fastest. Every call captures each view's pipeline on its lane
- * (view v on lane v mod lanes) into one CUDA graph, updates the plan's instantiated
- * graph in place (cameras are kernel parameters) and launches it once on `stream`:
- * no host synchronisation (unless RG_FLAG_BATCH_CHECKED). Images are identical to
- * rg_render's. An entry overflow is recorded in the scene's sticky flags
- * (rg_scene_check), as for rg_render without stats. Views of one lane run in
- * order; lanes run concurrently, so scenes may repeat across views freely.
- * A plan keeps its workspaces until one of its scenes is destroyed (at most 8
- * plans are kept).
+ * unless opts gives one), every path and 1, 2 and 4 pixels per thread (RoofGS) and
+ * keeps the fastest. Paths: (a) lanes: each view's whole pipeline on its lane (view v
+ * on lane v mod lanes; 1, 2 or 4 lanes, each a stream and a workspace); (b) fused
+ * (RoofGS, at most 32 views; one workspace per view): each view's depth order on the
+ * lanes, then ONE front-end launch over the Gaussians of every view, each view's
+ * entry sort on the lanes, then ONE persistent rasterizer launch whose blocks take the
+ * (view, tile) items of every view from a work counter. Every call captures the batch
+ * into one CUDA graph, updates the plan's instantiated graph in place (cameras are
+ * kernel parameters) and launches it once on `stream`: no host synchronisation
+ * (unless RG_FLAG_BATCH_CHECKED). Images are identical to rg_render's. An entry
+ * overflow is recorded in the scene's sticky flags (rg_scene_check), as for
+ * rg_render without stats. Scenes may repeat across views freely. A plan keeps its
+ * workspaces until one of its scenes is destroyed (at most 8 plans are kept).
+ * RG_ERR_UNSUPPORTED: RG_FLAG_BATCH_FUSED with exact mode or more than 32 views.
  */
 rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
                           const rg_render_opts* opts, float* const* outs, void* stream);
 
-/* The autotuned lane count, pixels per thread and tile shape of the plan for these views
- * (lanes 0 if no plan exists yet); tile_w and tile_h may be NULL. */
+/* The autotuned lane count, pixels per thread, tile shape and path (fused 1, lanes 0) of
+ * the plan for these views (lanes 0 if no plan exists yet); tile_w, tile_h and fused may
+ * be NULL. */
 rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
                              const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread, int32_t* tile_w,
-                             int32_t* tile_h);
+                             int32_t* tile_h, int32_t* fused);
 
 /*
  * Request loop (serving; not in the paper). A server keeps its scenes resident and

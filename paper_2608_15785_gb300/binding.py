@@ -30,6 +30,8 @@ RG_FLAG_QUAD_PIXEL = 1 << 3
 RG_FLAG_STAGE_EVENTS = 1 << 8
 RG_FLAG_BATCH_CHECKED = 1 << 9
 RG_FLAG_TEST_STALL_SORT = 1 << 10
+RG_FLAG_BATCH_FUSED = 1 << 11
+RG_FLAG_BATCH_LANES = 1 << 12
 RG_INSPECT_KEYS = 1
 RG_INSPECT_VALUES = 2
 RG_INSPECT_RANGES = 3
@@ -119,7 +121,7 @@ def lib():
         L.rg_inspect.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
         L.rg_eval_fast_exp.argtypes = [P, P, C.c_int64, P]
         L.rg_render_batch.argtypes = [P, P, P, C.c_int32, C.POINTER(RgOpts), P, P]
-        L.rg_batch_plan_info.argtypes = [P, P, P, C.c_int32, C.POINTER(RgOpts), P, P]
+        L.rg_batch_plan_info.argtypes = [P, P, P, C.c_int32, C.POINTER(RgOpts), P, P, P, P, P]
         L.rg_backward.argtypes = [P, C.POINTER(RgCamera), C.POINTER(RgOpts), P, C.POINTER(RgGrads), P]
         L.rg_submit.argtypes = [P, C.POINTER(RgCamera), C.c_int32, C.POINTER(C.c_uint64)]
         L.rg_poll.argtypes = [P, C.c_uint64, P]
@@ -293,15 +295,18 @@ def render_batch(scenes, scene_idx, cams, mode="roofgs", flags: int = 0, outs=No
     return outs
 
 
-def batch_plan_info(scenes, scene_idx, cams, mode="roofgs", flags: int = 0, tile=(0, 0)):
-    """(lanes, pixels per thread, tile width, tile height) the plan of these views uses."""
+def batch_plan_info(scenes, scene_idx, cams, mode="roofgs", flags: int = 0, tile=(0, 0), with_path=False):
+    """(lanes, pixels per thread, tile width, tile height[, fused]) the plan of these views uses."""
     n = len(cams)
     hs = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
     idx = (C.c_int32 * n)(*[int(i) for i in scene_idx])
     cs = (RgCamera * n)(*[camera_struct(c) for c in cams])
     o = RgOpts(_mode(mode), int(flags), int(tile[0]), int(tile[1]))
-    lanes, ppt, tw, th = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-    check(lib().rg_batch_plan_info(hs, idx, cs, n, C.byref(o), C.byref(lanes), C.byref(ppt), C.byref(tw), C.byref(th)))
+    lanes, ppt, tw, th, fused = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    check(lib().rg_batch_plan_info(hs, idx, cs, n, C.byref(o), C.byref(lanes), C.byref(ppt), C.byref(tw),
+                                   C.byref(th), C.byref(fused)))
+    if with_path:
+        return lanes.value, ppt.value, tw.value, th.value, bool(fused.value)
     return lanes.value, ppt.value, tw.value, th.value
 
 

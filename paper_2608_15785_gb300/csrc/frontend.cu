@@ -95,9 +95,11 @@ __device__ __forceinline__ unsigned warp_inclusive_scan(unsigned x, int lane)
 // Full occupancy (64 warps per SM, 32 registers): the kernel is latency-bound on
 // its depth-ordered gathers and shuffles, and 8 blocks of 256 threads per SM
 // measured 0.41 ms at 4K against 0.52 ms at 4 blocks per SM (61 registers)
-__global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fused(FrontendArgs a)
+// One block of the fused front end: virtual block vb (blocks of a view are numbered in
+// the order they claimed work, so every predecessor of the ordered allocation is
+// running or done) of the view described by a.
+__device__ __forceinline__ void frontend_block(const FrontendArgs& a, const unsigned vb)
 {
-    __shared__ unsigned s_vb;
     __shared__ unsigned s_wsum[FE_WARPS];
     __shared__ RowTestS s_rt[FE_THREADS];   // per-row test of each thread's Gaussian
     __shared__ unsigned s_q[FE_THREADS];    // quantized depth, Eq. (9)
@@ -110,11 +112,9 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
     __shared__ unsigned s_d0[RADIX_FE + 1], s_h1[RADIX_FE];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
     if (a.hist_passes)
         for (int j = tid; j < 2 * RADIX_FE + 1; j += FE_THREADS) (j <= RADIX_FE ? s_d0[j] : s_h1[j - RADIX_FE - 1]) = 0u;
     __syncthreads();
-    const unsigned vb = s_vb;
     const long long slot = (long long)vb * FE_THREADS + tid;
     // Gaussian of this slot: slots follow depth order when an order is given, so
     // the entries come out sorted by depth and only the tile bits remain to sort
@@ -330,6 +330,36 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fuse
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fused(FrontendArgs a)
+{
+    __shared__ unsigned s_vb;
+    if (threadIdx.x == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
+    __syncthreads();
+    frontend_block(a, s_vb);
+}
+
+// Every view of a batch in one grid: a block claims the next of all views' blocks
+// (views in order, each view's blocks in order) and runs it with that view's
+// arguments, read from the kernel's parameter space.
+__global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS)
+    k_frontend_views(const __grid_constant__ FrontendViews m)
+{
+    __shared__ unsigned s_g;
+    if (threadIdx.x == 0) s_g = atomicAdd(m.claim, 1u);
+    __syncthreads();
+    const unsigned g = s_g;
+    int v = 0;
+    while (v + 1 < m.n_views && m.block_prefix[v + 1] <= g) v++;
+    frontend_block(m.views[v], g - m.block_prefix[v]);
+}
+
+void launch_frontend_views(const FrontendViews& m, cudaStream_t s)
+{
+    const unsigned blocks = m.block_prefix[m.n_views];
+    if (blocks == 0) return;
+    k_frontend_views<<<blocks, FE_THREADS, 0, s>>>(m);
 }
 
 // Grid-stride over the Gaussians; each block also counts the 8-bit digits of its

@@ -103,14 +103,14 @@ __device__ __forceinline__ unsigned warp_lower_bound(const K* __restrict__ keys,
     return lo + (unsigned)__popc(__ballot_sync(0xffffffffu, less));
 }
 
+// One tile of the RoofGS rasterizer (a block of 256 / PPT threads).
 template <bool FAST, int PPT, bool COUNT>
-__global__ void __launch_bounds__(256 / PPT) k_raster_roofgs(RasterArgs a)
+__device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
 {
     constexpr int NT = 256 / PPT; // threads per tile of 256 pixels (16 x 16, 32 x 8 or 8 x 32)
     __shared__ float4 s_c0[NT];
     __shared__ float4 s_c1[NT];
     __shared__ float s_cb[NT];
-    const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int x0 = tx * a.cam.tw, y0 = ty * a.cam.th;
     const int t = threadIdx.x;
@@ -208,6 +208,56 @@ __global__ void __launch_bounds__(256 / PPT) k_raster_roofgs(RasterArgs a)
             a.out[plane + o] = cg[i] + T[i] * a.cam.bg[1];
             a.out[2 * plane + o] = cb[i] + T[i] * a.cam.bg[2];
         }
+    }
+}
+
+template <bool FAST, int PPT, bool COUNT>
+__global__ void __launch_bounds__(256 / PPT) k_raster_roofgs(RasterArgs a)
+{
+    raster_tile<FAST, PPT, COUNT>(a, blockIdx.x);
+}
+
+// Every view of a batch in one persistent launch: each block takes (view, tile) items
+// from one work counter (views in order, tiles in order) until all are done, and
+// rasterizes the tile with that view's arguments (kernel parameter space).
+template <bool FAST, int PPT>
+__global__ void __launch_bounds__(256 / PPT) k_raster_views(const __grid_constant__ RasterViews m)
+{
+    __shared__ unsigned s_g;
+    const unsigned total = m.tile_prefix[m.n_views];
+    while (true) {
+        if (threadIdx.x == 0) s_g = atomicAdd(m.claim, 1u);
+        __syncthreads();
+        const unsigned g = s_g;
+        if (g >= total) break;
+        int v = 0;
+        while (v + 1 < m.n_views && m.tile_prefix[v + 1] <= g) v++;
+        raster_tile<FAST, PPT, false>(m.views[v], (int)(g - m.tile_prefix[v]));
+        __syncthreads(); // every thread has read s_g before it is claimed again
+    }
+}
+
+template <bool FAST, int PPT>
+static void raster_views_launch(const RasterViews& m, cudaStream_t s)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_views<FAST, PPT>, 256 / PPT, 0);
+    const unsigned total = m.tile_prefix[m.n_views];
+    unsigned grid = (unsigned)((per_sm > 0 ? per_sm : 1) * device_sm_count());
+    if (grid > total) grid = total;
+    if (grid) k_raster_views<FAST, PPT><<<grid, 256 / PPT, 0, s>>>(m);
+}
+
+void launch_raster_views(const RasterViews& m, int fast_exp, int ppt, cudaStream_t s)
+{
+    if (fast_exp) {
+        if (ppt == 1) raster_views_launch<true, 1>(m, s);
+        else if (ppt == 4) raster_views_launch<true, 4>(m, s);
+        else raster_views_launch<true, 2>(m, s);
+    } else {
+        if (ppt == 1) raster_views_launch<false, 1>(m, s);
+        else if (ppt == 4) raster_views_launch<false, 4>(m, s);
+        else raster_views_launch<false, 2>(m, s);
     }
 }
 

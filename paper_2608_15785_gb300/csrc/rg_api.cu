@@ -168,6 +168,132 @@ struct NvtxScope {
     NvtxScope& operator=(const NvtxScope&) = delete;
 };
 
+// Arguments of a RoofGS frame's front end and sorts on workspace w (nothing launched;
+// records what rg_inspect needs about the frame in w).
+void roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flags, RoofgsFrame& f)
+{
+    memset(&f, 0, sizeof(f));
+    Counters* ctr = w.ctrl.as<Counters>();
+    unsigned* hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + sizeof(Counters));
+    Sticky* sticky = s->sticky.as<Sticky>();
+    const long long n = s->n;
+    FrontendArgs& a = f.fa;
+    a.geoA = s->geoA.as<float4>();
+    a.geoB = s->geoB.as<uint4>();
+    a.shq = s->shq.as<uint4>();
+    for (int k = 0; k < 12; k++) a.band_scale[k] = (k / 3 <= s->sh_degree) ? s->band_scale[k] : 0.0f;
+    a.per_gauss_scale = s->sh_scale_mode == RG_SH_SCALE_BAND_GAUSS;
+    a.sh_degree = s->sh_degree;
+    a.n = n;
+    a.cam = F.cam;
+    a.lay = F.lay;
+    a.rec = w.rec.as<float4>();
+    a.keys = w.keys[0].as<unsigned>();
+    a.vals = w.vals[0].as<unsigned>();
+    a.cap = w.cap;
+    a.status = w.lb_status.as<unsigned long long>();
+    a.ctr = ctr;
+    a.sticky = sticky;
+    SortArgs& sa = f.sa;
+    for (int k = 0; k < 2; k++) {
+        sa.keys[k] = w.keys[k].p;
+        sa.vals[k] = w.vals[k].as<unsigned>();
+        sa.status[k] = w.sort_status[k].as<unsigned>();
+    }
+    sa.cap = w.cap;
+    sa.hist = hist;
+    sa.max_tiles = (w.cap + sort_tile_items() - 1) / sort_tile_items();
+    sa.ctr = ctr;
+    sa.sticky = sticky;
+    sa.key_bytes = 4;
+    if (flags & RG_FLAG_SORT_FULL_KEY) {
+        // the paper's scheme: entries in Gaussian order, 4 passes over the 32-bit key
+        sa.passes = 4;
+        sa.bit0 = 0;
+    } else {
+        // Gaussians sorted by quantized depth first (stable, ties by index); the
+        // entries then come out in (q_d, index) order and a stable sort of the
+        // b_t tile bits alone yields the order of the full 32-bit key
+        f.depth_order = true;
+        SortArgs& ga = f.ga;
+        for (int k = 0; k < 2; k++) {
+            ga.keys[k] = w.gkeys[k].p;
+            ga.vals[k] = w.gvals[k].as<unsigned>();
+            ga.status[k] = w.gstatus[k].as<unsigned>();
+        }
+        ga.cap = n;
+        ga.key_bytes = 4;
+        ga.passes = (F.lay.b_d + 7) / 8;
+        ga.bit0 = 0;
+        // Gaussians in index order carry scattered low depth digits: rank the first pass
+        // with ballots (measured 8 % faster on the 3 M-Gaussian depth keys)
+        ga.ballot_mask = 1;
+        ga.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + CTRL_BYTES + sizeof(Counters));
+        ga.max_tiles = (n + sort_tile_items() - 1) / sort_tile_items();
+        ga.ctr = reinterpret_cast<Counters*>(w.ctrl.as<unsigned char>() + CTRL_BYTES);
+        ga.sticky = sticky;
+        // the depth keys' digits are counted as they are written (ga.passes <= 4)
+        ga.hist_pre = ga.hist;
+        a.order = w.gvals[ga.passes & 1].as<unsigned>();
+        sa.passes = (F.lay.b_t + 7) / 8;
+        sa.bit0 = F.lay.b_d;
+        // depth-ordered entries of one Gaussian row carry consecutive tiles, so the warp
+        // holds many distinct low tile digits: rank that pass with ballots
+        sa.ballot_mask = 1;
+        // up to 2 tile-bit passes (b_t <= 16): the front end counts the digits of its
+        // entries per tile row, and the sort's histogram pass only runs on overflow;
+        // the entries carry the 16-bit tile id alone (the depth code of a 32-bit key
+        // follows from the value: entries stay in depth order within a tile)
+        if (sa.passes <= 2) {
+            a.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + 2 * CTRL_BYTES);
+            a.hist_passes = sa.passes;
+            sa.hist_copies = a.hist;
+            sa.hist_copy_stride = 2;
+            sa.hist_pre = hist + 4 * 256; // rows 4-5 of the frame's [8][256] histograms
+            a.keys16 = w.keys[0].as<unsigned short>();
+            sa.key_bytes = 2;
+            sa.bit0 = 0;
+        }
+        w.last_gfin = ga.passes & 1;
+    }
+    f.tile_shift = a.keys16 ? 0 : F.lay.b_d;
+    w.last_key16 = a.keys16 != nullptr;
+    w.last_bd = F.lay.b_d;
+    w.last_mode = RG_MODE_ROOFGS;
+    w.last_passes = sa.passes;
+    w.last_tiles = F.tiles;
+}
+
+// The per-Gaussian depth order of a RoofGS frame: quantized depth keys (with the sort's
+// digit counts), then their stable sort.
+void roofgs_depth_order(const RoofgsFrame& f, Workspace& w, cudaStream_t st)
+{
+    launch_depth_keys(f.fa, w.gkeys[0].as<unsigned>(), w.gvals[0].as<unsigned>(), f.ga.ctr, f.ga.hist, f.ga.passes, st);
+    launch_sort(f.ga, st, nullptr);
+}
+
+// The RoofGS rasterizer's arguments for a frame built by roofgs_build (non-counting).
+void roofgs_raster_args(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flags, float* out, RasterArgs& r)
+{
+    memset(&r, 0, sizeof(r));
+    const int fin = w.last_passes & 1;
+    r.ranges = w.ranges.as<uint2>();
+    r.vals = w.vals[fin].as<unsigned>();
+    r.n = s->n;
+    r.tiles_x = F.lay.tiles_x;
+    r.tiles_y = F.lay.tiles_y;
+    r.cam = F.cam;
+    r.out = out;
+    r.rec = w.rec.as<float4>();
+    if (w.last_key16) r.skeys16 = w.keys[fin].as<unsigned short>();
+    else r.skeys = w.keys[fin].as<unsigned>();
+    r.tile_shift = w.last_key16 ? 0 : F.lay.b_d;
+    r.ranges_out = w.ranges.as<uint2>();
+    r.ctr = w.ctrl.as<Counters>();
+    r.fast_exp = (flags & RG_FLAG_EXACT_EXP) ? 0 : 1;
+    r.ppt = (flags & RG_FLAG_SINGLE_PIXEL) ? 1 : ((flags & RG_FLAG_QUAD_PIXEL) ? 4 : 2);
+}
+
 // One frame on `st`; the caller has checked arguments and the workspace.
 rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode, uint32_t flags, float* out,
                       cudaStream_t st, bool count)
@@ -252,93 +378,21 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
             launch_exact_duplicate(a, st);
         }
     } else {
-        FrontendArgs a;
-        memset(&a, 0, sizeof(a));
-        a.geoA = s->geoA.as<float4>();
-        a.geoB = s->geoB.as<uint4>();
-        a.shq = s->shq.as<uint4>();
-        for (int k = 0; k < 12; k++) a.band_scale[k] = (k / 3 <= s->sh_degree) ? s->band_scale[k] : 0.0f;
-        a.per_gauss_scale = s->sh_scale_mode == RG_SH_SCALE_BAND_GAUSS;
-        a.sh_degree = s->sh_degree;
-        a.n = n;
-        a.cam = F.cam;
-        a.lay = F.lay;
-        a.rec = w.rec.as<float4>();
-        a.keys = w.keys[0].as<unsigned>();
-        a.vals = w.vals[0].as<unsigned>();
-        a.cap = w.cap;
-        a.status = w.lb_status.as<unsigned long long>();
-        a.ctr = ctr;
-        a.sticky = sticky;
+        RoofgsFrame f;
+        roofgs_build(s, w, F, flags, f);
         RG_CK(cudaMemsetAsync(w.lb_status.p, 0,
                               (size_t)((n + frontend_block_threads() - 1) / frontend_block_threads() + 1) * 8, st));
-        sa.key_bytes = 4;
-        if (flags & RG_FLAG_SORT_FULL_KEY) {
-            // the paper's scheme: entries in Gaussian order, 4 passes over the 32-bit key
-            sa.passes = 4;
-            sa.bit0 = 0;
-            if (ev) RG_CK(cudaEventRecord(E[1], st));
-        } else {
-            // Gaussians sorted by quantized depth first (stable, ties by index); the
-            // entries then come out in (q_d, index) order and a stable sort of the
-            // b_t tile bits alone yields the order of the full 32-bit key
-            SortArgs ga;
-            memset(&ga, 0, sizeof(ga));
-            for (int k = 0; k < 2; k++) {
-                ga.keys[k] = w.gkeys[k].p;
-                ga.vals[k] = w.gvals[k].as<unsigned>();
-                ga.status[k] = w.gstatus[k].as<unsigned>();
-            }
-            Counters* gctr = reinterpret_cast<Counters*>(w.ctrl.as<unsigned char>() + CTRL_BYTES);
-            ga.cap = n;
-            ga.key_bytes = 4;
-            ga.passes = (F.lay.b_d + 7) / 8;
-            ga.bit0 = 0;
-            // Gaussians in index order carry scattered low depth digits: rank the first pass
-            // with ballots (measured 8 % faster on the 3 M-Gaussian depth keys)
-            ga.ballot_mask = 1;
-            ga.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + CTRL_BYTES + sizeof(Counters));
-            ga.max_tiles = (n + sort_tile_items() - 1) / sort_tile_items();
-            ga.ctr = gctr;
-            ga.sticky = sticky;
-            {
-                NvtxScope r_("rg depth order");
-                // the depth keys' digits are counted as they are written (ga.passes <= 4)
-                ga.hist_pre = ga.hist;
-                launch_depth_keys(a, w.gkeys[0].as<unsigned>(), w.gvals[0].as<unsigned>(), gctr, ga.hist, ga.passes,
-                                  st);
-                launch_sort(ga, st, nullptr);
-            }
-            a.order = w.gvals[ga.passes & 1].as<unsigned>();
-            if (ev) RG_CK(cudaEventRecord(E[1], st));
-            sa.passes = (F.lay.b_t + 7) / 8;
-            sa.bit0 = F.lay.b_d;
-            // depth-ordered entries of one Gaussian row carry consecutive tiles, so the warp
-            // holds many distinct low tile digits: rank that pass with ballots
-            sa.ballot_mask = 1;
-            // up to 2 tile-bit passes (b_t <= 16): the front end counts the digits of its
-            // entries per tile row, and the sort's histogram pass only runs on overflow;
-            // the entries carry the 16-bit tile id alone (the depth code of a 32-bit key
-            // follows from the value: entries stay in depth order within a tile)
-            if (sa.passes <= 2) {
-                a.hist = reinterpret_cast<unsigned*>(w.ctrl.as<unsigned char>() + 2 * CTRL_BYTES);
-                a.hist_passes = sa.passes;
-                sa.hist_copies = a.hist;
-                sa.hist_copy_stride = 2;
-                sa.hist_pre = hist + 4 * 256; // rows 4-5 of the frame's [8][256] histograms
-                a.keys16 = w.keys[0].as<unsigned short>();
-                sa.key_bytes = 2;
-                sa.bit0 = 0;
-            }
-            w.last_gfin = ga.passes & 1;
+        if (f.depth_order) {
+            NvtxScope r_("rg depth order");
+            roofgs_depth_order(f, w, st);
         }
+        if (ev) RG_CK(cudaEventRecord(E[1], st));
         {
             NvtxScope r_("rg front end");
-            launch_frontend_fused(a, st);
+            launch_frontend_fused(f.fa, st);
         }
-        tile_shift = a.keys16 ? 0 : F.lay.b_d;
-        w.last_key16 = a.keys16 != nullptr;
-        w.last_bd = F.lay.b_d;
+        sa = f.sa;
+        tile_shift = f.tile_shift;
     }
     if (ev) RG_CK(cudaEventRecord(E[2], st));
     if (ev && sa.passes <= 0) RG_CK(cudaEventRecord(E[3], st));
@@ -385,14 +439,8 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         NvtxScope r_("rg raster");
         launch_raster_exact(r, st);
     } else {
-        r.rec = w.rec.as<float4>();
-        if (w.last_key16) r.skeys16 = w.keys[fin].as<unsigned short>();
-        else r.skeys = w.keys[fin].as<unsigned>();
-        r.tile_shift = tile_shift;
-        r.ranges_out = w.ranges.as<uint2>();
-        r.ctr = ctr;
-        r.fast_exp = (flags & RG_FLAG_EXACT_EXP) ? 0 : 1;
-        r.ppt = (flags & RG_FLAG_SINGLE_PIXEL) ? 1 : ((flags & RG_FLAG_QUAD_PIXEL) ? 4 : 2);
+        roofgs_raster_args(s, w, F, flags, out, r);
+        r.count = count ? ctr : nullptr;
         NvtxScope r_("rg raster");
         launch_raster_roofgs(r, st);
     }

@@ -34,7 +34,10 @@ struct BatchPlan {
     int req_tw = 0, req_th = 0; // requested tile shape (0 x 0: autotuned)
     int tw = TILE, th = TILE;   // tile shape in use
     bool tuned = false;
+    bool fused = false;         // autotuned: the fused path (RoofGS; see plan_capture_fused)
     std::unique_ptr<Workspace[]> ws{new Workspace[BATCH_MAX_LANES]};
+    std::unique_ptr<Workspace[]> vws; // fused path: one workspace per view
+    DevBuf claim;                     // fused path: work counters of the multi-view launches
     cudaStream_t streams[BATCH_MAX_LANES] = {nullptr};
     cudaEvent_t join[BATCH_MAX_LANES] = {nullptr};
     cudaEvent_t fork = nullptr;
@@ -43,6 +46,7 @@ struct BatchPlan {
     int exec_lanes = 0;
     uint32_t exec_raster = 0;
     int exec_tw = 0;
+    int exec_fused = -1;
 
     ~BatchPlan()
     {
@@ -52,6 +56,9 @@ struct BatchPlan {
             if (join[l]) cudaEventDestroy(join[l]);
             ws[l].release();
         }
+        if (vws)
+            for (size_t v = 0; v < scenes.size(); v++) vws[v].release();
+        claim.release();
         if (fork) cudaEventDestroy(fork);
         if (cap) cudaStreamDestroy(cap);
     }
@@ -71,6 +78,13 @@ rg_status plan_init(BatchPlan& P)
     return RG_OK;
 }
 
+// The fused path: RoofGS, at most MAX_BATCH_VIEWS views, no test hook.
+bool fused_possible(const BatchPlan& P)
+{
+    return P.mode == RG_MODE_ROOFGS && P.scenes.size() <= (size_t)MAX_BATCH_VIEWS &&
+           !(P.flags & (RG_FLAG_TEST_STALL_SORT | RG_FLAG_BATCH_LANES));
+}
+
 // Size every lane for every view: render each view once on lane 0's workspace with
 // the checked path, then give all lanes the largest capacity (+25 % headroom for
 // other poses). Also runs each kernel once outside capture (first-use set-up).
@@ -79,6 +93,7 @@ rg_status plan_size(BatchPlan& P, const std::vector<FrameLayout>& F, float* cons
     int64_t cap = 0;
     int max_tiles = 1;
     int64_t max_n = 1;
+    std::vector<int64_t> view_entries(F.size(), 0);
     for (size_t v = 0; v < F.size(); v++) {
         rg_scene* s = P.scenes[v];
         max_tiles = std::max(max_tiles, F[v].tiles);
@@ -93,6 +108,7 @@ rg_status plan_size(BatchPlan& P, const std::vector<FrameLayout>& F, float* cons
             RG_CK(cudaStreamSynchronize(st));
             if (c2.error) return fail(RG_ERR_TIMEOUT, "a bounded device wait gave up");
             cap = std::max<int64_t>(cap, (int64_t)c2.n_entries_total);
+            view_entries[v] = std::max<int64_t>(view_entries[v], (int64_t)c2.n_entries_total);
             if (c2.n_entries_total <= (unsigned long long)P.ws[0].cap) break;
             int64_t want = (int64_t)(c2.n_entries_total + c2.n_entries_total / 4 + 1024);
             if (want > MAX_CAP) return fail(RG_ERR_CAPACITY, "a view needs more than 2^30 - 1 entries");
@@ -104,26 +120,95 @@ rg_status plan_size(BatchPlan& P, const std::vector<FrameLayout>& F, float* cons
         for (size_t v = 0; v < F.size(); v++)
             RG_TRY(ensure_workspace(P.ws[l], P.scenes[v]->n, P.mode, max_tiles, std::max(cap, P.ws[l].cap)));
     }
+    if (fused_possible(P)) { // the fused path keeps every view's frame at once: one workspace per view
+        if (!P.vws) P.vws.reset(new Workspace[F.size()]);
+        for (size_t v = 0; v < F.size(); v++) {
+            const int64_t c = std::min<int64_t>(MAX_CAP, view_entries[v] + view_entries[v] / 4 + 1024);
+            RG_TRY(ensure_workspace(P.vws[v], P.scenes[v]->n, P.mode, F[v].tiles, std::max(c, P.vws[v].cap)));
+        }
+        RG_TRY(ensure(P.claim, 256, "batch work counters"));
+    }
     // the scenes' sticky flags of the sizing frames are not errors
     for (rg_scene* s : P.scenes) RG_CK(cudaMemsetAsync(s->sticky.p, 0, sizeof(Sticky), st));
     RG_CK(cudaStreamSynchronize(st));
     return RG_OK;
 }
 
-// Capture all views on `lanes` lanes and bring P.exec up to date.
+// The fused path's stages of every view, enqueued while P.cap is being captured: on the
+// lanes, each view's counters are cleared and its Gaussians ordered by depth; then ONE
+// front-end launch walks the Gaussians of every view (k_frontend_views); on the lanes,
+// each view's entries are sorted; then ONE persistent rasterizer launch takes the
+// (view, tile) items of every view from a work counter (k_raster_views).
+rg_status enqueue_fused(BatchPlan& P, const std::vector<FrameLayout>& F, float* const* outs, int lanes, uint32_t fl)
+{
+    const int V = (int)F.size();
+    std::unique_ptr<FrontendViews> fv(new FrontendViews());
+    std::unique_ptr<RasterViews> rv(new RasterViews());
+    std::vector<SortArgs> sorts((size_t)V);
+    unsigned blocks = 0, items = 0;
+    const int bt = frontend_block_threads();
+    for (int v = 0; v < V; v++) {
+        rg_scene* s = P.scenes[v];
+        Workspace& w = P.vws[v];
+        cudaStream_t ls = P.streams[v % lanes];
+        RoofgsFrame f;
+        roofgs_build(s, w, F[v], fl, f);
+        RG_CK(cudaMemsetAsync(w.ctrl.p, 0, CTRL_ALLOC, ls));
+        RG_CK(cudaMemsetAsync(w.lb_status.p, 0, (size_t)((s->n + bt - 1) / bt + 1) * 8, ls));
+        if (f.depth_order) roofgs_depth_order(f, w, ls);
+        fv->views[v] = f.fa;
+        fv->block_prefix[v] = blocks;
+        blocks += (unsigned)((s->n + bt - 1) / bt);
+        sorts[v] = f.sa;
+    }
+    fv->block_prefix[V] = blocks;
+    fv->n_views = V;
+    fv->claim = P.claim.as<unsigned>();
+    RG_CK(cudaMemsetAsync(P.claim.p, 0, 2 * sizeof(unsigned), P.cap));
+    for (int l = 0; l < lanes; l++) {
+        RG_CK(cudaEventRecord(P.join[l], P.streams[l]));
+        RG_CK(cudaStreamWaitEvent(P.cap, P.join[l], 0));
+    }
+    launch_frontend_views(*fv, P.cap);
+    RG_CK(cudaEventRecord(P.fork, P.cap));
+    for (int l = 0; l < lanes; l++) RG_CK(cudaStreamWaitEvent(P.streams[l], P.fork, 0));
+    for (int v = 0; v < V; v++) launch_sort(sorts[v], P.streams[v % lanes], nullptr);
+    for (int l = 0; l < lanes; l++) {
+        RG_CK(cudaEventRecord(P.join[l], P.streams[l]));
+        RG_CK(cudaStreamWaitEvent(P.cap, P.join[l], 0));
+    }
+    for (int v = 0; v < V; v++) {
+        roofgs_raster_args(P.scenes[v], P.vws[v], F[v], fl, outs[v], rv->views[v]);
+        rv->tile_prefix[v] = items;
+        items += (unsigned)F[v].tiles;
+    }
+    rv->tile_prefix[V] = items;
+    rv->n_views = V;
+    rv->claim = P.claim.as<unsigned>() + 1;
+    launch_raster_views(*rv, (fl & RG_FLAG_EXACT_EXP) ? 0 : 1, rv->views[0].ppt, P.cap);
+    RG_CK(cudaGetLastError());
+    return RG_OK;
+}
+
+// Capture all views on `lanes` lanes (the fused path if `fused`) and bring P.exec up to date.
 rg_status plan_capture(BatchPlan& P, const std::vector<FrameLayout>& F, float* const* outs, int lanes,
-                       uint32_t raster_flags)
+                       uint32_t raster_flags, bool fused)
 {
     RG_CK(cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal));
     rg_status err = RG_OK;
     cudaError_t ce = cudaEventRecord(P.fork, P.cap);
     for (int l = 0; l < lanes && ce == cudaSuccess; l++) ce = cudaStreamWaitEvent(P.streams[l], P.fork, 0);
-    const uint32_t fl = (P.flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL)) | raster_flags;
-    for (size_t v = 0; v < F.size() && ce == cudaSuccess && err == RG_OK; v++)
-        err = render_once(P.scenes[v], P.ws[v % lanes], F[v], P.mode, fl, outs[v], P.streams[v % lanes]);
-    for (int l = 0; l < lanes && ce == cudaSuccess; l++) {
-        ce = cudaEventRecord(P.join[l], P.streams[l]);
-        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(P.cap, P.join[l], 0);
+    const uint32_t fl = (P.flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL |
+                                     RG_FLAG_BATCH_FUSED | RG_FLAG_BATCH_LANES)) | raster_flags;
+    if (fused && ce == cudaSuccess) {
+        err = enqueue_fused(P, F, outs, lanes, fl);
+    } else {
+        for (size_t v = 0; v < F.size() && ce == cudaSuccess && err == RG_OK; v++)
+            err = render_once(P.scenes[v], P.ws[v % lanes], F[v], P.mode, fl, outs[v], P.streams[v % lanes]);
+        for (int l = 0; l < lanes && ce == cudaSuccess; l++) {
+            ce = cudaEventRecord(P.join[l], P.streams[l]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(P.cap, P.join[l], 0);
+        }
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(P.cap, &g);
@@ -137,7 +222,8 @@ rg_status plan_capture(BatchPlan& P, const std::vector<FrameLayout>& F, float* c
         return fail(RG_ERR_CUDA, std::string("batch capture failed: ") +
                                      cudaGetErrorString(ce != cudaSuccess ? ce : ee));
     }
-    bool fresh = !P.exec || P.exec_lanes != lanes || P.exec_raster != raster_flags || (!F.empty() && P.exec_tw != F[0].cam.tw);
+    bool fresh = !P.exec || P.exec_lanes != lanes || P.exec_raster != raster_flags ||
+                 (!F.empty() && P.exec_tw != F[0].cam.tw) || P.exec_fused != (int)fused;
     if (!fresh) {
         cudaGraphExecUpdateResultInfo info;
         if (cudaGraphExecUpdate(P.exec, g, &info) != cudaSuccess) {
@@ -157,6 +243,7 @@ rg_status plan_capture(BatchPlan& P, const std::vector<FrameLayout>& F, float* c
         P.exec_lanes = lanes;
         P.exec_raster = raster_flags;
         P.exec_tw = F.empty() ? 0 : F[0].cam.tw;
+        P.exec_fused = (int)fused;
     }
     cudaGraphDestroy(g);
     return RG_OK;
@@ -184,6 +271,13 @@ rg_status plan_tune(BatchPlan& P, const rg_camera* cams, float* const* outs, cud
     float best = 1e30f;
     int best_l = 1, best_tw = TILE, best_th = TILE;
     uint32_t best_r = 0;
+    bool best_fused = false;
+    // paths: the lanes (1, 2 or 4), and the fused path on 4 lanes; RG_FLAG_BATCH_FUSED /
+    // RG_FLAG_BATCH_LANES keep one of them
+    std::vector<std::pair<int, bool>> paths;
+    if (!(P.flags & RG_FLAG_BATCH_FUSED))
+        for (int lanes : {1, 2, 4}) paths.push_back({lanes, false});
+    if (fused_possible(P) && P.vws) paths.push_back({std::min(BATCH_MAX_LANES, std::max(1, V)), true});
     cudaEvent_t e0, e1;
     RG_CK(cudaEventCreate(&e0));
     RG_CK(cudaEventCreate(&e1));
@@ -191,12 +285,13 @@ rg_status plan_tune(BatchPlan& P, const rg_camera* cams, float* const* outs, cud
     rg_status e = RG_OK;
     for (auto shape : plan_shapes(P)) {
         e = layouts_for(cams, V, shape.first, shape.second, F);
-        for (int lanes : {1, 2, 4}) {
+        for (auto path : paths) {
+            const int lanes = path.first;
             if (e != RG_OK) break;
             if (lanes > V && lanes > 1) continue;
             for (uint32_t r : {0u, (uint32_t)RG_FLAG_SINGLE_PIXEL, (uint32_t)RG_FLAG_QUAD_PIXEL}) {
                 if (P.mode != RG_MODE_ROOFGS && r) continue;
-                e = plan_capture(P, F, outs, lanes, r);
+                e = plan_capture(P, F, outs, lanes, r, path.second);
                 if (e != RG_OK) break;
                 float ms = 0.f;
                 if (cudaGraphLaunch(P.exec, st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess ||
@@ -207,6 +302,7 @@ rg_status plan_tune(BatchPlan& P, const rg_camera* cams, float* const* outs, cud
                 }
                 if (ms < best) {
                     best = ms;
+                    best_fused = path.second;
                     best_l = lanes;
                     best_r = r;
                     best_tw = shape.first;
@@ -219,7 +315,9 @@ rg_status plan_tune(BatchPlan& P, const rg_camera* cams, float* const* outs, cud
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != RG_OK) return e;
+    if (best >= 1e30f) return fail(RG_ERR_UNSUPPORTED, "no batch path applies to these views and flags");
     P.lanes = best_l;
+    P.fused = best_fused;
     P.raster_flags = best_r;
     P.tw = best_tw;
     P.th = best_th;
@@ -276,6 +374,8 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
     std::lock_guard<std::mutex> lock(g_batch_mu);
     BatchPlan* P = nullptr;
     const uint32_t key_flags = opts->flags & ~(RG_FLAG_STAGE_EVENTS | RG_FLAG_SINGLE_PIXEL | RG_FLAG_QUAD_PIXEL | RG_FLAG_BATCH_CHECKED);
+    if ((key_flags & RG_FLAG_BATCH_FUSED) && (mode != RG_MODE_ROOFGS || n > MAX_BATCH_VIEWS))
+        return fail(RG_ERR_UNSUPPORTED, "the fused batch path renders RoofGS mode, at most 32 views");
     for (auto& p : g_plans) {
         if (p->device != dev || p->mode != mode || p->flags != key_flags || p->scenes != vs || p->req_tw != req_tw ||
             p->req_th != req_th)
@@ -312,7 +412,7 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
         P = g_plans.back().get();
     }
     RG_TRY(layouts_for(cams, n, P->tw, P->th, F));
-    RG_TRY(plan_capture(*P, F, outs, P->lanes, P->raster_flags));
+    RG_TRY(plan_capture(*P, F, outs, P->lanes, P->raster_flags, P->fused));
     RG_CK(cudaGraphLaunch(P->exec, st));
     if (opts->flags & RG_FLAG_BATCH_CHECKED) {
         // synchronous check: resize and render again if a view overflowed its lane
@@ -326,7 +426,7 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
         }
         if (over) { // grow the lanes (never shrink) for these views and render again
             RG_TRY(plan_size(*P, F, outs, st));
-            RG_TRY(plan_capture(*P, F, outs, P->lanes, P->raster_flags));
+            RG_TRY(plan_capture(*P, F, outs, P->lanes, P->raster_flags, P->fused));
             RG_CK(cudaGraphLaunch(P->exec, st));
             RG_CK(cudaStreamSynchronize(st));
         }
@@ -338,7 +438,7 @@ rg_status rg_render_batch(rg_scene* const* scenes, const int32_t* scene_idx, con
 // (0 lanes if no plan exists yet).
 rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, const rg_camera* cams, int32_t n,
                              const rg_render_opts* opts, int32_t* lanes, int32_t* pixels_per_thread, int32_t* tile_w,
-                             int32_t* tile_h)
+                             int32_t* tile_h, int32_t* fused)
 {
     if (!scenes || !scene_idx || !cams || !opts || !lanes || !pixels_per_thread || n <= 0)
         return fail(RG_ERR_INVALID_ARG, "bad arguments");
@@ -360,6 +460,7 @@ rg_status rg_batch_plan_info(rg_scene* const* scenes, const int32_t* scene_idx, 
             *pixels_per_thread = (p->raster_flags & RG_FLAG_SINGLE_PIXEL) ? 1 : ((p->raster_flags & RG_FLAG_QUAD_PIXEL) ? 4 : 2);
             if (tile_w) *tile_w = p->tw;
             if (tile_h) *tile_h = p->th;
+            if (fused) *fused = p->fused ? 1 : 0;
             return RG_OK;
         }
     }

@@ -132,6 +132,18 @@ void init_events(Workspace& w);
 // after the ranges; count selects the counting rasterizer
 rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode, uint32_t flags, float* out,
                       cudaStream_t st, bool count = false);
+// RoofGS frame in stages (rg_render runs them back to back; a batch's fused path runs every
+// view's front end in one launch and every view's rasterizer in one persistent launch)
+struct RoofgsFrame {
+    FrontendArgs fa;  // fused front end
+    SortArgs ga;      // per-Gaussian depth sort (if depth_order)
+    SortArgs sa;      // entry sort
+    bool depth_order; // Gaussians pre-sorted by quantized depth (not with RG_FLAG_SORT_FULL_KEY)
+    int tile_shift;   // sorted key >> tile_shift = tile id
+};
+void roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flags, RoofgsFrame& f);
+void roofgs_depth_order(const RoofgsFrame& f, Workspace& w, cudaStream_t st);
+void roofgs_raster_args(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flags, float* out, RasterArgs& r);
 // frees a scene and its workspace
 void destroy_scene(rg_scene* s);
 // drops the batch plans that render from scene s (rg_batch.cu)

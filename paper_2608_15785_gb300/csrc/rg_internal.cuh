@@ -482,6 +482,21 @@ struct FrontendArgs {
     int hist_passes;            // 0, 1 or 2: 8-bit digits of the tile id counted (b_t <= 16)
 };
 void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s);
+
+// Views of a batch rendered by one launch of a stage (the batch's fused path).
+constexpr int MAX_BATCH_VIEWS = 32;
+
+struct FrontendViews {
+    FrontendArgs views[MAX_BATCH_VIEWS];
+    unsigned block_prefix[MAX_BATCH_VIEWS + 1]; // first block of each view; [n_views] = all blocks
+    int n_views;
+    unsigned* claim;                            // zeroed before the launch
+};
+// kernel parameters are limited to 32,764 bytes
+static_assert(sizeof(FrontendViews) <= 32000, "the views' front-end arguments must fit the kernel parameters");
+// one grid over the Gaussians of every view: block_prefix[v] = sum over earlier views of
+// ceil(n / frontend_block_threads())
+void launch_frontend_views(const FrontendViews& m, cudaStream_t s);
 // threads per block of the fused front end (one look-back status word per block)
 int frontend_block_threads();
 // quantized depth (Eq. (9)) of every Gaussian as a sort key, Gaussian index as value;
@@ -578,6 +593,16 @@ struct RasterArgs {
     Counters* count;      // non-null: count evaluated / blended pairs (separate kernel variant)
 };
 void launch_raster_roofgs(const RasterArgs& a, cudaStream_t s);
+
+struct RasterViews {
+    RasterArgs views[MAX_BATCH_VIEWS];          // RoofGS tile-search arguments of each view
+    unsigned tile_prefix[MAX_BATCH_VIEWS + 1];  // first item of each view; [n_views] = all tiles
+    int n_views;
+    unsigned* claim;                            // zeroed before the launch
+};
+static_assert(sizeof(RasterViews) <= 32000, "the views' rasterizer arguments must fit the kernel parameters");
+// one persistent launch over the (view, tile) items of every view
+void launch_raster_views(const RasterViews& m, int fast_exp, int ppt, cudaStream_t s);
 void launch_raster_exact(const RasterArgs& a, cudaStream_t s);
 void launch_fast_exp_eval(const float* P, float* out, long long n, cudaStream_t s);
 

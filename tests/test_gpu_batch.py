@@ -59,16 +59,24 @@ def _single(scene, cam, mode, ppt, tile):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode", ["roofgs", "exact"])
-def test_batch_equals_single_views(scenes, mode):
+@pytest.mark.parametrize("mode,path", [("roofgs", "auto"), ("roofgs", "fused"), ("roofgs", "lanes"),
+                                       ("exact", "auto")])
+def test_batch_equals_single_views(scenes, mode, path):
+    """path: the autotuner's choice, or forced: the fused path (one front-end launch over every
+    view's Gaussians, one persistent rasterizer over every view's tiles) or the lanes."""
     idx = [v % 2 for v in range(len(SIZES))]
+    pf = {"auto": 0, "fused": binding.RG_FLAG_BATCH_FUSED, "lanes": binding.RG_FLAG_BATCH_LANES}[path]
     for call, k0 in enumerate((0, 7)):  # second call: new poses, same plan (graph update)
         cams = _cams(k0)
-        outs = binding.render_batch(scenes, idx, cams, mode=mode)
+        outs = binding.render_batch(scenes, idx, cams, mode=mode, flags=pf)
         torch.cuda.synchronize()
-        lanes, ppt, tw, th = binding.batch_plan_info(scenes, idx, cams, mode=mode)
+        lanes, ppt, tw, th, fused = binding.batch_plan_info(scenes, idx, cams, mode=mode, flags=pf, with_path=True)
         assert lanes in (1, 2, 4) and ppt in ((1, 2, 4) if mode == "roofgs" else (2,))
         assert (tw, th) in ((16, 16), (32, 8), (8, 32))
+        if path != "auto":
+            assert fused == (path == "fused")
+        if mode == "exact":
+            assert not fused
         for v, cam in enumerate(cams):
             img = outs[v].cpu().numpy()
             ref = _single(scenes[idx[v]], cam, mode, ppt, (tw, th))
@@ -106,3 +114,11 @@ def test_batch_with_a_fixed_tile_shape(scenes, tile):
     assert (tw, th) == tile
     for v, cam in enumerate(cams):
         assert np.array_equal(outs[v].cpu().numpy(), _single(scenes[idx[v]], cam, "roofgs", ppt, tile))
+
+
+def test_fused_path_limits(scenes):
+    """The fused path renders RoofGS mode only."""
+    cams = _cams(1)[:2]
+    with pytest.raises(binding.RgError) as e:
+        binding.render_batch(scenes, [0, 1], cams, mode="exact", flags=binding.RG_FLAG_BATCH_FUSED)
+    assert e.value.status == 8
