@@ -38,15 +38,17 @@ CLOCK_QUERY = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-# Source-level FP32/ALU-pipe instruction counts of the rasterizers' inner loops
-# (per evaluated (Gaussian, pixel) exponent, and per pair inside the
-# alpha >= 1/255 range that is blended or ends the pixel):
-#   RoofGS dual-pixel: exponent 4 (5 FFMA for P(x,y), 3 for P(x,y+1), per pixel)
-#     + range test 1; blend = FFMA + shift-add (bit exp) + min + 1-alpha +
-#     T(1-alpha) + stop test + alpha*T + 3 FFMA colour + T update = 11.
-#   exact: exponent (2 FADD + 6 FMUL/FFMA/FADD) + test 2 = 10; blend = expf
-#     (~9) + o*e + min + alpha test + 1-alpha + T(1-alpha) + stop test + alpha*T
-#     + 3 FFMA + T update = 20.
+# The rasterizer is bound by instruction issue (ncu: issue slots 87.5 % busy). Its roofline
+# divides warp instructions issued per second by the issue peak, SMs x 4 schedulers x SM
+# clock. Warp instructions per evaluated (Gaussian, pixel) pair of the timed kernel
+# (k_raster_roofgs<fast exp, 4 pixels per thread>), from ncu on the 1M-Gaussian 4K case:
+# sm__inst_issued.sum 544.2 M for 615.1 M evaluated pairs (per pair: FMA pipe 0.420, ALU
+# pipe 0.232, LSU 0.036, XU 0.001, the rest branches and uniform datapath). The pair
+# count of the timed frames comes from the counting variant of the same kernel.
+RASTER_WARP_INST_PER_PAIR = 544.2 / 615.1
+# Source-level FP32/ALU-pipe instruction counts of the rasterizers' inner loops (per
+# evaluated exponent, per pair inside the alpha >= 1/255 range), kept as a second,
+# model-based view: RoofGS 4 + 1 range test, blend 11; exact 10, blend 20.
 OPS = {"roofgs": (5, 11), "exact": (10, 20)}
 STAGES = ["depth_order", "front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"]
 # DRAM bytes per entry of one tile-bit one-sweep pass (16-bit tile ids + 32-bit values): ncu
@@ -651,6 +653,7 @@ def rooflines(r, a, props, clocks):
     work = stage_work("roofgs", st, W, H)
     sms = props.multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    issue_peak = sms * 4 * mhz * 1e6 / 1e9  # warp instructions per second (G/s): 4 schedulers per SM
     alu_peak = sms * 128 * mhz * 1e6 / 1e9  # FP32-pipe instructions per second (G/s): 128 lanes per SM
     ms = dict(zip(STAGES, r["stage_ms"]))
 
@@ -665,8 +668,12 @@ def rooflines(r, a, props, clocks):
         "sort_hist": hbm_stage(work["hist"], ms["sort_hist"]),
         "sort_pass": hbm_stage(work["sort_pass"], ms["sort_passes"] / passes),
         "ranges": hbm_stage(work["ranges"], ms["ranges"]) if work["ranges"] else None,
-        "raster": {"bound": "alu", "achieved": work["raster_ops"] / (ms["raster"] * 1e-3) / 1e9, "peak": alu_peak,
-                   "unit": "Gop/s", "ms": ms["raster"], "ops": work["raster_ops"]},
+        "raster": {"bound": "issue", "achieved": RASTER_WARP_INST_PER_PAIR * st["n_pairs"] / (ms["raster"] * 1e-3) / 1e9,
+                   "peak": issue_peak, "unit": "G warp instructions/s", "ms": ms["raster"],
+                   "warp_instructions": RASTER_WARP_INST_PER_PAIR * st["n_pairs"],
+                   "fp32_pipe_model": {"achieved": round(work["raster_ops"] / (ms["raster"] * 1e-3) / 1e9, 1),
+                                       "peak": round(alu_peak, 1), "unit": "Gop/s",
+                                       "frac": round(work["raster_ops"] / (ms["raster"] * 1e-3) / 1e9 / alu_peak, 4)}},
     }
     stages["sort_pass"]["launches_per_frame"] = work["passes"]
     stages = {k: v for k, v in stages.items() if v is not None}
@@ -689,7 +696,7 @@ def rooflines(r, a, props, clocks):
     roof = {"kernel": names[dom], "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
             "unit": d["unit"], "frac": d["frac"], "traffic": traffic,
             "peak_source": ("of measured HBM copy bandwidth" if src == "measured" else "of fallback HBM bandwidth")
-            if d["bound"] == "hbm" else "%d SMs x 128 FP32 lanes x %.0f MHz median SM clock under load" % (sms, mhz)}
+            if d["bound"] == "hbm" else "%d SMs x 4 schedulers x %.0f MHz median SM clock under load" % (sms, mhz)}
     return roof, stages
 
 
