@@ -45,6 +45,7 @@ struct SortCfg;
 template <>
 struct SortCfg<unsigned> {
     static constexpr int THREADS = RG_SORT_T32, KPT = RG_SORT_K32, MIN_BLOCKS = RG_SORT_B32;
+    static constexpr bool STAGE_VALS = false;
 };
 // 16-bit tile ids: 6-byte entries leave room in shared memory for three CTAs of
 // 256 x 24 = 6144 entries per SM (80 registers, a few spilled): measured 0.852 ms
@@ -57,10 +58,14 @@ struct SortCfg<unsigned> {
 template <> // 16-bit tile ids (a key still takes a register)
 struct SortCfg<unsigned short> {
     static constexpr int THREADS = RG_SORT_T16, KPT = RG_SORT_K16, MIN_BLOCKS = RG_SORT_B16;
+    // values staged in shared memory by cp.async instead of registers: no spills at 80
+    // registers, 72.7 KB per CTA (3 per SM still fit); 4K tile-bit passes 0.855 -> 0.835 ms
+    static constexpr bool STAGE_VALS = true;
 };
 template <>
 struct SortCfg<unsigned long long> {
     static constexpr int THREADS = 512, KPT = 8, MIN_BLOCKS = 2;
+    static constexpr bool STAGE_VALS = false; // staging measured slower for the exact-mode keys (9.14 vs 8.81 ms)
 };
 template <typename K>
 constexpr int tile_of() { return SortCfg<K>::THREADS * SortCfg<K>::KPT; }
@@ -226,11 +231,26 @@ __device__ __forceinline__ unsigned digit_exclusive_scan(unsigned v, unsigned* s
     return x - v + (warp ? s_w[warp - 1] : 0u);
 }
 
+// asynchronous global -> shared copies (cp.async): the tile's values travel to shared
+// memory while the keys are ranked, without passing through registers
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename K>
 struct SortSmem {
     static constexpr int TILE = tile_of<K>(), WARPS = SortCfg<K>::THREADS / 32;
     K keys[TILE];
     unsigned vals[TILE];
+    unsigned vin[SortCfg<K>::STAGE_VALS ? TILE : 1]; // the tile's values as loaded (element order), by cp.async
     unsigned whist[WARPS][RADIX]; // per-warp digit counters, then per-warp exclusive offsets
     unsigned goff[RADIX];         // global exclusive digit offsets of this pass
     unsigned loff[RADIX];         // tile-local exclusive digit offsets
@@ -275,16 +295,26 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
         const unsigned tile = S.tile;
         if (tile >= ntiles) break;
 
+        constexpr bool STAGE = SortCfg<K>::STAGE_VALS;
+        if constexpr (STAGE) {
+            // the tile's values go to shared memory asynchronously (16 bytes at a time; the tile
+            // starts on a 16-byte boundary of a 16-byte-aligned array); read back by the reorder
+            const unsigned base = tile * S_TILE;
+            const unsigned cnt = n - base < (unsigned)S_TILE ? n - base : (unsigned)S_TILE;
+            const unsigned full = cnt & ~3u;
+            for (unsigned c = tid; c < full / 4; c += S_THREADS) cp_async16(&S.vin[4 * c], vin + base + 4 * c);
+            for (unsigned j = full + tid; j < cnt; j += S_THREADS) cp_async4(&S.vin[j], vin + base + j);
+        }
         // load the tile warp-striped: element = tile*TILE + warp*32*KPT + i*32 + lane
         const unsigned e0 = tile * S_TILE + warp * 32 * S_KPT + lane;
         K k[S_KPT];
-        unsigned v[S_KPT];
+        unsigned v[STAGE ? 1 : S_KPT];
 #pragma unroll
         for (int i = 0; i < S_KPT; i++) {
             const unsigned e = e0 + 32 * i;
             const bool ok = e < n;
             k[i] = ok ? kin[e] : (K)~(K)0; // padding sorts last (digit 255, after the valid ones)
-            v[i] = ok ? vin[e] : 0u;
+            if constexpr (!STAGE) v[i] = ok ? vin[e] : 0u;
         }
         // stable rank of each element among the warp's elements of the same digit
         // (below 32 * KPT: two ranks share a register)
@@ -340,6 +370,7 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             }
             if (lane == 31) S.scan[warp] = incl;
         }
+        if constexpr (SortCfg<K>::STAGE_VALS) cp_async_wait_all(); // this thread's value copies, visible after C
         __syncthreads(); // C
         unsigned lo = 0;
         if (tid < RADIX) {
@@ -405,7 +436,8 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             const unsigned r = (i & 1) ? (rank2[i >> 1] >> 16) : (rank2[i >> 1] & 0xffffu);
             const unsigned pos = S.loff[d] + S.whist[warp][d] + r;
             S.keys[pos] = k[i];
-            S.vals[pos] = v[i];
+            if constexpr (SortCfg<K>::STAGE_VALS) S.vals[pos] = S.vin[warp * 32 * S_KPT + 32 * i + lane];
+            else S.vals[pos] = v[i];
         }
         __syncthreads(); // E
         const unsigned rem = n - tile * S_TILE;
