@@ -117,8 +117,20 @@ def test_batch_with_a_fixed_tile_shape(scenes, tile):
 
 
 def test_fused_path_limits(scenes):
-    """The fused path renders RoofGS mode only."""
+    """The fused path renders RoofGS mode and at most 32 views; beyond that the autotuned plan
+    takes the lanes, and its images still equal the single-view renders."""
     cams = _cams(1)[:2]
     with pytest.raises(binding.RgError) as e:
         binding.render_batch(scenes, [0, 1], cams, mode="exact", flags=binding.RG_FLAG_BATCH_FUSED)
     assert e.value.status == 8
+    many = [synth.look_at_camera((0.05 * v - 0.8, -0.2, -3.0), 64 + 4 * (v % 3), 48, zfar=4.8) for v in range(33)]
+    idx = [v % 2 for v in range(33)]
+    with pytest.raises(binding.RgError) as e:
+        binding.render_batch(scenes, idx, many, mode="roofgs", flags=binding.RG_FLAG_BATCH_FUSED)
+    assert e.value.status == 8
+    outs = binding.render_batch(scenes, idx, many, mode="roofgs")
+    torch.cuda.synchronize()
+    lanes, ppt, tw, th, fused = binding.batch_plan_info(scenes, idx, many, mode="roofgs", with_path=True)
+    assert not fused
+    for v in (0, 7, 32):
+        assert np.array_equal(outs[v].cpu().numpy(), _single(scenes[idx[v]], many[v], "roofgs", ppt, (tw, th)))
