@@ -53,8 +53,8 @@ OPS = {"roofgs": (5, 11), "exact": (10, 20)}
 STAGES = ["depth_order", "front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"]
 # DRAM bytes per entry of one tile-bit one-sweep pass (16-bit tile ids + 32-bit values): ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the tile-bit passes on the 1M-Gaussian 4K case,
-# scaled by the entries of the launch (166.9 + 133.9 MB and 166.0 + 127.3 MB for 27.03 M entries)
-SORT_PASS_TRAFFIC_PER_ENTRY = 11.0
+# scaled by the entries of the launch (167.1 + 118.5 MB and 166.0 + 113.2 MB for 27.03 M entries)
+SORT_PASS_TRAFFIC_PER_ENTRY = 10.4
 
 
 def parse():
