@@ -185,7 +185,11 @@ rg_status rg_scene_reserve(rg_scene* scene, int64_t n_entries);
  * out [channel][row][column]: device memory, or pinned host memory that the
  * device addresses (the image is then written straight to the host).
  * Pipeline (exact): preprocess -> scan -> duplicate -> 64-bit radix sort ->
- * tile ranges -> rasterizer (Sec. II-A pipeline, Sec. III).
+ * tile ranges -> rasterizer (Sec. II-A pipeline, Sec. III). The exponent of
+ * Eq. (10) is evaluated from the projected mean carried at twice single
+ * precision and the quadratic form completed in dx, so the image stays within
+ * 2e-4 per channel of an FP64 evaluation except where a pair's alpha or T lies
+ * within rounding of the 1/255 or 1e-4 thresholds.
  * Pipeline (RoofGS): Gaussians ordered by quantized depth -> fused front end ->
  * stable radix sort of the tile bits of the 32-bit keys (the order of the full
  * key; RG_FLAG_SORT_FULL_KEY sorts all 32 bits in 4 passes instead) -> fast-exp
