@@ -76,6 +76,7 @@ def parse():
     p.add_argument("--ppt", type=int, default=4, choices=(1, 2, 4),
                    help="RoofGS pixels per thread in the rasterizer (2 = the paper's dual-pixel scheme)")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-tile-sort", action="store_true")
     return p.parse_args()
 
 
@@ -346,6 +347,8 @@ def run_ours(a, rank, world, local_rank):
         extra["backward"] = run_backward(dev)
     if single and not a.no_serve:
         extra["serve"] = run_serve(dev, gs, a.ppt)
+    if single and not a.no_tile_sort:
+        extra["tile_counting_sort"] = run_tile_sort(a, gs, cams, dev, rflags)
     clocks = sampler.stop() if sampler else None
     if dist is not None:
         dist.barrier()
@@ -464,6 +467,46 @@ def run_batch(a, sc3, gs3, dev):
             "autotuned": tuned, "fused_path": fused_info, "lanes_path": lanes_info,
             "fused_speedup_vs_sequential": round(seq_ms / fused_ms, 3),
             "lanes_speedup_vs_sequential": round(seq_ms / lanes_ms, 3)}
+
+
+def run_tile_sort(a, gs, cams, dev, rflags):
+    """The per-tile counting sort (RG_FLAG_TILE_COUNTING_SORT) against the tile-bit radix passes, on
+    this workload and on the 1080p one (500k Gaussians, pose 0): frame rate and sort time."""
+    import torch
+
+    from paper_2608_15785_gb300 import binding, synth
+    out = {}
+    sc2 = synth.clustered_scene(500_000, 1)
+    g2 = binding.Scene(sc2, sh_scale_mode=binding.RG_SH_SCALE_BAND_GAUSS)
+    cases = [("%dx%d, %gM" % (a.width, a.height, a.gaussians / 1e6), gs, cams),
+             ("1920x1080, 0.5M", g2, [synth.orbit_camera(0, 1920, 1080)])]
+    for label, scene, cs in cases:
+        img = torch.empty((3, cs[0].height, cs[0].width), device=dev)
+        row = {}
+        for name, fl in (("radix", 0), ("counting", binding.RG_FLAG_TILE_COUNTING_SORT)):
+            for c in cs:
+                scene.render(c, mode="roofgs", flags=rflags | fl, out=img, stats=True)
+            steps = 60
+            for k in range(5):
+                scene.render(cs[k % len(cs)], mode="roofgs", flags=rflags | fl, out=img)
+            torch.cuda.synchronize(dev)
+            scene.stage_times()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(steps):
+                scene.render(cs[k % len(cs)], mode="roofgs", flags=rflags | fl | binding.RG_FLAG_STAGE_EVENTS, out=img)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms, frames = scene.stage_times()
+            per = [x / max(frames, 1) for x in ms]
+            row[name] = {"fps": round(steps / (e0.elapsed_time(e1) * 1e-3), 1),
+                         "sort_ms": round(per[2] + per[3], 4), "raster_ms": round(per[5], 4),
+                         "front_end_ms": round(per[1], 4)}
+        row["sort_speedup"] = round(row["radix"]["sort_ms"] / max(row["counting"]["sort_ms"], 1e-9), 3)
+        out[label] = row
+        scene.check()
+    g2.close()
+    return out
 
 
 def run_backward(dev):

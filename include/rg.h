@@ -124,6 +124,13 @@ typedef struct {
  * autotuner chooses between them otherwise) */
 #define RG_FLAG_BATCH_FUSED (1u << 11)
 #define RG_FLAG_BATCH_LANES (1u << 12)
+/* RoofGS: group the depth-ordered entries by tile with one stable counting sort (per-chunk
+ * tile counts, their prefix, one in-order scatter that also writes the tile ranges) instead
+ * of the radix passes over the tile bits; the same entries and images. Needs the depth
+ * pre-sort (not RG_FLAG_SORT_FULL_KEY), tile ids of at most 16 bits and at most 57,856
+ * tiles (one 4-byte offset per tile in a block's shared memory); RG_ERR_UNSUPPORTED
+ * otherwise. Not for rg_render_batch's fused path (its plans take the lanes). */
+#define RG_FLAG_TILE_COUNTING_SORT (1u << 13)
 /* test hook for the failure path: the first radix pass of the entry sort never processes its
  * first tile, so the next tile's bounded look-back wait runs out (about a second); the frame
  * is invalid, kernels finish with in-bounds writes only, and the next rg_scene_check (or this

@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librg.so")
-SOURCES = ["frontend.cu", "sort.cu", "raster.cu", "backward.cu", "rg_api.cu", "rg_batch.cu", "rg_serve.cu",
-           "sort_noalloc.cu"]
+SOURCES = ["frontend.cu", "sort.cu", "tilesort.cu", "raster.cu", "backward.cu", "rg_api.cu", "rg_batch.cu",
+           "rg_serve.cu", "sort_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

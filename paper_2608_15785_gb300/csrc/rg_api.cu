@@ -141,6 +141,10 @@ rg_status ensure_workspace(Workspace& w, int64_t n_gauss, int mode, int tiles, i
         RG_TRY(ensure(w.offsets, (size_t)n * 4, "offsets"));
     } else {
         RG_TRY(ensure(w.rec, (size_t)n * 32, "records"));
+        // the per-tile counting sort's count matrix (chunks x tiles, at most SMs x one block's shared
+        // memory for any tile count) and tile totals: sized for any frame, so a workspace shared by
+        // views of several resolutions never runs short
+        RG_TRY(ensure(w.tsort, tilesort_matrix_bytes_max() + (size_t)tilesort_max_tiles() * 4, "tile counting sort"));
         for (int k = 0; k < 2; k++) {
             RG_TRY(ensure(w.gkeys[k], (size_t)n * 4, "depth keys"));
             RG_TRY(ensure(w.gvals[k], (size_t)n * 4, "depth order"));
@@ -170,7 +174,7 @@ struct NvtxScope {
 
 // Arguments of a RoofGS frame's front end and sorts on workspace w (nothing launched;
 // records what rg_inspect needs about the frame in w).
-void roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flags, RoofgsFrame& f)
+rg_status roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flags, RoofgsFrame& f)
 {
     memset(&f, 0, sizeof(f));
     Counters* ctr = w.ctrl.as<Counters>();
@@ -256,12 +260,35 @@ void roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flag
         }
         w.last_gfin = ga.passes & 1;
     }
+    if (flags & RG_FLAG_TILE_COUNTING_SORT) {
+        // one stable counting sort by tile instead of the tile-bit radix passes: the front end
+        // needs no digit counts; the values land in vals[1], the ranges come with them
+        if (!f.depth_order || !a.keys16 || F.tiles > tilesort_max_tiles())
+            return fail(RG_ERR_UNSUPPORTED, "RG_FLAG_TILE_COUNTING_SORT needs the depth pre-sort, 16-bit tile ids "
+                                            "and at most 57,856 tiles");
+        f.tile_sort = true;
+        a.hist = nullptr;
+        a.hist_passes = 0;
+        TileSortArgs& t = f.ts;
+        t.keys16 = w.keys[0].as<unsigned short>();
+        t.vals = w.vals[0].as<unsigned>();
+        t.vout = w.vals[1].as<unsigned>();
+        t.T = F.tiles;
+        t.chunks = tilesort_chunks(F.tiles);
+        t.M = w.tsort.as<unsigned>();
+        t.tot = t.M + (size_t)t.chunks * F.tiles;
+        t.ranges = w.ranges.as<uint2>();
+        t.ctr = ctr;
+        sa.passes = 1; // the result's buffer: vals[1]
+    }
     f.tile_shift = a.keys16 ? 0 : F.lay.b_d;
     w.last_key16 = a.keys16 != nullptr;
+    w.last_tilesort = f.tile_sort;
     w.last_bd = F.lay.b_d;
     w.last_mode = RG_MODE_ROOFGS;
     w.last_passes = sa.passes;
     w.last_tiles = F.tiles;
+    return RG_OK;
 }
 
 // The per-Gaussian depth order of a RoofGS frame: quantized depth keys (with the sort's
@@ -285,8 +312,12 @@ void roofgs_raster_args(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_
     r.cam = F.cam;
     r.out = out;
     r.rec = w.rec.as<float4>();
-    if (w.last_key16) r.skeys16 = w.keys[fin].as<unsigned short>();
-    else r.skeys = w.keys[fin].as<unsigned>();
+    if (w.last_tilesort) { // the counting sort wrote the ranges: no search
+    } else if (w.last_key16) {
+        r.skeys16 = w.keys[fin].as<unsigned short>();
+    } else {
+        r.skeys = w.keys[fin].as<unsigned>();
+    }
     r.tile_shift = w.last_key16 ? 0 : F.lay.b_d;
     r.ranges_out = w.ranges.as<uint2>();
     r.ctr = w.ctrl.as<Counters>();
@@ -312,8 +343,10 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     }
     // RoofGS frames that rasterize find each tile's range inside the rasterizer (a search of
     // the sorted keys per tile block); the others run the ranges pass
-    const bool search_ranges = mode == RG_MODE_ROOFGS && out != nullptr;
+    const bool tile_sort = mode == RG_MODE_ROOFGS && (flags & RG_FLAG_TILE_COUNTING_SORT);
+    const bool search_ranges = mode == RG_MODE_ROOFGS && out != nullptr && !tile_sort;
     w.last_key16 = false;
+    w.last_tilesort = false;
     RG_CK(cudaMemsetAsync(w.ctrl.p, 0, CTRL_ALLOC, st));
     if (flags & RG_FLAG_TEST_STALL_SORT) { // tile 0 of the first entry-sort pass is never claimed
         k_set_word<<<1, 1, 0, st>>>(&ctr->sort_tile_ctr[0], 1u);
@@ -334,6 +367,8 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     sa.ctr = ctr;
     sa.sticky = sticky;
     int tile_shift;
+    TileSortArgs tsa;
+    memset(&tsa, 0, sizeof(tsa));
     if (mode == RG_MODE_EXACT) {
         ExactArgs a;
         memset(&a, 0, sizeof(a));
@@ -379,7 +414,7 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         }
     } else {
         RoofgsFrame f;
-        roofgs_build(s, w, F, flags, f);
+        RG_TRY(roofgs_build(s, w, F, flags, f));
         RG_CK(cudaMemsetAsync(w.lb_status.p, 0,
                               (size_t)((n + frontend_block_threads() - 1) / frontend_block_threads() + 1) * 8, st));
         if (f.depth_order) {
@@ -393,16 +428,20 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         }
         sa = f.sa;
         tile_shift = f.tile_shift;
+        tsa = f.ts;
     }
     if (ev) RG_CK(cudaEventRecord(E[2], st));
-    if (ev && sa.passes <= 0) RG_CK(cudaEventRecord(E[3], st));
-    {
+    if (ev && (sa.passes <= 0 || tile_sort)) RG_CK(cudaEventRecord(E[3], st));
+    if (tile_sort) {
+        NvtxScope r_("rg sort");
+        launch_tile_counting_sort(tsa, st);
+    } else {
         NvtxScope r_("rg sort");
         launch_sort(sa, st, ev ? E[3] : nullptr);
     }
     if (ev) RG_CK(cudaEventRecord(E[4], st));
     const int fin = sa.passes & 1;
-    if (!search_ranges) {
+    if (!search_ranges && !tile_sort) {
         RangeArgs ra;
         ra.keys = w.keys[fin].p;
         ra.key_bytes = sa.key_bytes;
@@ -417,6 +456,7 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     w.last_mode = mode;
     w.last_passes = sa.passes;
     w.last_tiles = F.tiles;
+    w.last_tilesort = tile_sort;
     if (!out) { // front end, sort and ranges only (the backward replays the blend itself)
         if (ev) RG_CK(cudaEventRecord(E[6], st));
         RG_CK(cudaGetLastError());
@@ -863,12 +903,20 @@ rg_status rg_inspect(rg_scene* s, int32_t what, void* host_dst, int64_t cap_byte
         const int fin = s->ws.last_passes & 1;
         if (what == RG_INSPECT_KEYS && s->ws.last_key16) {
             // the entries carried 16-bit tile ids: each 32-bit key (tile << b_d | q_d) is rebuilt
-            // from the tile and the depth code of its Gaussian (the per-Gaussian depth sort's result)
+            // from the tile and the depth code of its Gaussian (the per-Gaussian depth sort's result);
+            // after the per-tile counting sort the tile of each slot follows from the ranges
             const size_t ne = c.n_entries, ng = (size_t)n;
             std::vector<uint16_t> t16(ne);
             std::vector<uint32_t> val(ne), gq(ng), gi(ng), q(ng, 0u);
             if (ne) {
-                RG_CK(cudaMemcpy(t16.data(), s->ws.keys[fin].p, ne * 2, cudaMemcpyDeviceToHost));
+                if (s->ws.last_tilesort) {
+                    std::vector<uint2> rr((size_t)s->ws.last_tiles);
+                    RG_CK(cudaMemcpy(rr.data(), s->ws.ranges.p, rr.size() * 8, cudaMemcpyDeviceToHost));
+                    for (size_t t = 0; t < rr.size(); t++)
+                        for (uint32_t j = rr[t].x; j < rr[t].y && j < ne; j++) t16[j] = (uint16_t)t;
+                } else {
+                    RG_CK(cudaMemcpy(t16.data(), s->ws.keys[fin].p, ne * 2, cudaMemcpyDeviceToHost));
+                }
                 RG_CK(cudaMemcpy(val.data(), s->ws.vals[fin].p, ne * 4, cudaMemcpyDeviceToHost));
             }
             if (ng) {

@@ -82,7 +82,7 @@ rg_status plan_init(BatchPlan& P)
 bool fused_possible(const BatchPlan& P)
 {
     return P.mode == RG_MODE_ROOFGS && P.scenes.size() <= (size_t)MAX_BATCH_VIEWS &&
-           !(P.flags & (RG_FLAG_TEST_STALL_SORT | RG_FLAG_BATCH_LANES));
+           !(P.flags & (RG_FLAG_TEST_STALL_SORT | RG_FLAG_BATCH_LANES | RG_FLAG_TILE_COUNTING_SORT));
 }
 
 // Size every lane for every view: render each view once on lane 0's workspace with
@@ -152,7 +152,7 @@ rg_status enqueue_fused(BatchPlan& P, const std::vector<FrameLayout>& F, float* 
         Workspace& w = P.vws[v];
         cudaStream_t ls = P.streams[v % lanes];
         RoofgsFrame f;
-        roofgs_build(s, w, F[v], fl, f);
+        RG_TRY(roofgs_build(s, w, F[v], fl, f));
         RG_CK(cudaMemsetAsync(w.ctrl.p, 0, CTRL_ALLOC, ls));
         RG_CK(cudaMemsetAsync(w.lb_status.p, 0, (size_t)((s->n + bt - 1) / bt + 1) * 8, ls));
         if (f.depth_order) roofgs_depth_order(f, w, ls);

@@ -65,11 +65,13 @@ struct Workspace {
     DevBuf rec;                                           // RoofGS raster records
     DevBuf gkeys[2], gvals[2], gstatus[2];                // RoofGS per-Gaussian depth sort
     DevBuf gbuf;                                          // backward: image-space gradients [n][9]
+    DevBuf tsort;                                         // RoofGS per-tile counting sort: matrix + tile totals
     // last frame
     int last_mode = -1;
     int last_passes = 0;
     int last_tiles = 0;
     bool last_key16 = false; // entries carried 16-bit tile ids (the 32-bit keys are rebuilt on inspection)
+    bool last_tilesort = false; // the entries were grouped by the per-tile counting sort (keys rebuilt from ranges)
     int last_bd = 0;         // b_d of the last RoofGS frame
     int last_gfin = 0;       // buffer of the per-Gaussian depth sort's result
     // stage events
@@ -82,7 +84,7 @@ struct Workspace {
     {
         DevBuf* bufs[] = {&keys[0], &keys[1], &vals[0], &vals[1], &ranges, &ctrl, &lb_status, &sort_status[0],
                           &sort_status[1], &mean2, &depth, &quad, &rgb, &rect, &touched, &offsets, &rec, &gkeys[0],
-                          &gkeys[1], &gvals[0], &gvals[1], &gstatus[0], &gstatus[1], &gbuf};
+                          &gkeys[1], &gvals[0], &gvals[1], &gstatus[0], &gstatus[1], &gbuf, &tsort};
         for (DevBuf* b : bufs) b->release();
         if (ev_init)
             for (int f = 0; f < EV_RING; f++)
@@ -139,9 +141,12 @@ struct RoofgsFrame {
     SortArgs ga;      // per-Gaussian depth sort (if depth_order)
     SortArgs sa;      // entry sort
     bool depth_order; // Gaussians pre-sorted by quantized depth (not with RG_FLAG_SORT_FULL_KEY)
+    bool tile_sort;   // RG_FLAG_TILE_COUNTING_SORT: ts replaces the radix passes sa
+    TileSortArgs ts;
     int tile_shift;   // sorted key >> tile_shift = tile id
 };
-void roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flags, RoofgsFrame& f);
+// RG_ERR_UNSUPPORTED if the flags ask for what the frame cannot do
+rg_status roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flags, RoofgsFrame& f);
 void roofgs_depth_order(const RoofgsFrame& f, Workspace& w, cudaStream_t st);
 void roofgs_raster_args(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t flags, float* out, RasterArgs& r);
 // frees a scene and its workspace

@@ -606,6 +606,27 @@ void launch_raster_views(const RasterViews& m, int fast_exp, int ppt, cudaStream
 void launch_raster_exact(const RasterArgs& a, cudaStream_t s);
 void launch_fast_exp_eval(const float* P, float* out, long long n, cudaStream_t s);
 
+// Per-tile counting sort of 16-bit-tile-id entries (tilesort.cu): stable, one scatter.
+struct TileSortArgs {
+    const unsigned short* keys16; // [n] tile ids, entries in (depth code, Gaussian) order
+    const unsigned* vals;         // [n]
+    unsigned* vout;               // [n] the values grouped by tile, order kept within a tile
+    unsigned* M;                  // [chunks][T] per-chunk tile counts, then their column prefix
+    unsigned* tot;                // [T] tile totals, then each tile's first slot
+    uint2* ranges;                // [T] [first, end) of every tile, [0, 0) if empty
+    int T;                        // tiles of the frame
+    int chunks;                   // tilesort_chunks(T)
+    const Counters* ctr;          // n_entries
+};
+// tiles the shared-memory offsets allow (one 4-byte offset per tile in a block)
+int tilesort_max_tiles();
+// chunks (blocks) for T tiles: SMs x the blocks per SM the shared memory allows; 0 if T is too large
+int tilesort_chunks(int T);
+// bytes of the C x T count matrix, and their maximum over every T
+size_t tilesort_matrix_bytes(int T);
+size_t tilesort_matrix_bytes_max();
+void launch_tile_counting_sort(const TileSortArgs& a, cudaStream_t s);
+
 struct BackwardArgs {
     // forward state of the frame (exact mode)
     const uint2* ranges;

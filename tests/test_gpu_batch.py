@@ -134,3 +134,19 @@ def test_fused_path_limits(scenes):
     assert not fused
     for v in (0, 7, 32):
         assert np.array_equal(outs[v].cpu().numpy(), _single(scenes[idx[v]], many[v], "roofgs", ppt, (tw, th)))
+
+
+@pytest.mark.parametrize("path", ["fused", "lanes"])
+def test_batch_with_an_empty_view(scenes, path):
+    """A view that sees no Gaussian (camera turned away: every Gaussian behind it) renders the
+    background in both paths, beside ordinary views, and the others are unaffected."""
+    pf = binding.RG_FLAG_BATCH_FUSED if path == "fused" else binding.RG_FLAG_BATCH_LANES
+    away = synth.look_at_camera((0.0, 0.0, -3.0), 96, 64, zfar=4.8, target=(0.0, 0.0, -6.0), bg=(0.2, 0.4, 0.6))
+    cams = [_cams(2)[0], away, _cams(2)[3]]
+    idx = [0, 0, 1]
+    outs = binding.render_batch(scenes, idx, cams, mode="roofgs", flags=pf)
+    torch.cuda.synchronize()
+    lanes, ppt, tw, th = binding.batch_plan_info(scenes, idx, cams, mode="roofgs", flags=pf)
+    assert np.allclose(outs[1].cpu().numpy(), np.array([0.2, 0.4, 0.6])[:, None, None])
+    for v, cam in enumerate(cams):
+        assert np.array_equal(outs[v].cpu().numpy(), _single(scenes[idx[v]], cam, "roofgs", ppt, (tw, th))), v

@@ -358,6 +358,58 @@ def test_exact_capacity_overflow_recounts_digits():
     small.check()
 
 
+@pytest.mark.parametrize("name", ["tiny_256", "clustered_1080p", "clustered_4k"])
+def test_tile_counting_sort_matches_the_radix_passes(name):
+    """RG_FLAG_TILE_COUNTING_SORT groups the depth-ordered entries by tile with one stable
+    counting sort: keys, values and ranges bit-exact against the oracle, the image bit-identical
+    to the radix path's (2 and 4 pixels per thread)."""
+    sc, cams = synth.workload(name)
+    cam = cams[0] if name != "clustered_4k" else cams[7]
+    per_gauss = name == "clustered_4k"
+    gs = gpu_scene(sc, per_gauss)
+    comp = oracle.compact(sc, per_gauss)
+    for ppt in (0, binding.RG_FLAG_QUAD_PIXEL):
+        ref, st = render(gs, cam, "roofgs", flags=ppt, stats=True)
+        img, st2 = render(gs, cam, "roofgs", flags=ppt | binding.RG_FLAG_TILE_COUNTING_SORT, stats=True)
+        assert st2["n_entries"] == st["n_entries"]
+        assert np.array_equal(img, ref)
+        assert st2["n_entries"] == _keys_equal(gs, sc, cam, oracle.ROOFGS, comp)
+        # the timed (unchecked) launch gives the same image
+        assert np.array_equal(render(gs, cam, "roofgs", flags=ppt | binding.RG_FLAG_TILE_COUNTING_SORT), ref)
+    gs.check()
+
+
+def test_tile_counting_sort_limits_and_overflow():
+    """The counting sort needs the depth pre-sort and 16-bit tile ids (RG_ERR_UNSUPPORTED
+    otherwise); an overflowed frame sorts exactly its first emitted entries."""
+    sc, cams = synth.workload("tiny_256")
+    cam = cams[0]
+    gs = gpu_scene(sc)
+    with pytest.raises(binding.RgError) as e:
+        gs.render(cam, flags=binding.RG_FLAG_TILE_COUNTING_SORT | binding.RG_FLAG_SORT_FULL_KEY)
+    assert e.value.status == 8
+    with pytest.raises(binding.RgError) as e:  # 7680 x 4320: 17 tile bits
+        gs.render(synth.orbit_camera(0, 7680, 4320), flags=binding.RG_FLAG_TILE_COUNTING_SORT)
+    assert e.value.status == 8
+    small = gpu_scene(sc)
+    small.reserve(1000)
+    small.render(cam, flags=binding.RG_FLAG_TILE_COUNTING_SORT)
+    torch.cuda.synchronize()
+    gk = small.inspect(binding.RG_INSPECT_KEYS).view(np.uint32).astype(np.uint64)
+    gv = small.inspect(binding.RG_INSPECT_VALUES)
+    k, v, _, _ = oracle.keys(sc, cam, oracle.ROOFGS, comp=oracle.compact(sc))
+    b_d = np.uint64(oracle.layout(cam)["b_d"])
+    assert 0 < gk.size < k.size
+    emitted = np.lexsort((k >> b_d, v, k & ((np.uint64(1) << b_d) - np.uint64(1))))[: gk.size]
+    expect = emitted[np.lexsort((v[emitted], k[emitted]))]
+    assert np.array_equal(gk, k[expect]) and np.array_equal(gv, v[expect])
+    with pytest.raises(binding.RgError):
+        small.check()
+    img, st = render(small, cam, "roofgs", flags=binding.RG_FLAG_TILE_COUNTING_SORT, stats=True)
+    assert st["regrown"] == 1 and np.array_equal(img, render(gs, cam, "roofgs"))
+    small.check()
+
+
 def test_stage_times_and_counters(tiny):
     sc, cam, gs, _ = tiny
     for _ in range(3):
