@@ -65,6 +65,38 @@ __device__ __forceinline__ void blend(float P, float r, float g, float b, float&
     }
 }
 
+// Two pixels of a thread blended together with packed FP32x2 arithmetic (FFMA2 / FMUL2:
+// one instruction for both pixels). Per pixel the operations and roundings of
+// blend<true, false>, written with -alpha (the shift-add of Eq. (24) without its + 2^31
+// is -exp^(P): that addition only sets the sign bit) and with the negated colours nr, ng,
+// nb: T + T (-alpha) = T (1 - alpha) and c + (-r)(-alpha T) = c + r (alpha T) round to the
+// same values. A pixel that is finished or below -ln 255 takes -alpha = 0, which leaves
+// its T and colour unchanged.
+__device__ __forceinline__ void blend_pair_fast(float Pa, float Pb, float2 nr, float2 ng, float2 nb, float2& T, float2& cr,
+                                                float2& cg, float2& cb, bool& da, bool& db)
+{
+    const bool ua = !da && Pa >= -LN255F, ub = !db && Pb >= -LN255F;
+    if (ua || ub) {
+        const float2 w = __ffma2_rn(make_float2(Pa, Pb), make_float2(1.44269502f, 1.44269502f),
+                                    make_float2(126.954323f, 126.954323f));
+        const float ea = __uint_as_float(__float_as_uint(w.x) << 6); // -exp^(P)
+        const float eb = __uint_as_float(__float_as_uint(w.y) << 6);
+        const float2 na = make_float2(ua ? fmaxf(-0.99f, ea) : 0.0f, ub ? fmaxf(-0.99f, eb) : 0.0f);
+        const float2 Tn = __ffma2_rn(T, na, T);
+        const bool sa = Tn.x < 1e-4f, sb = Tn.y < 1e-4f; // only for a blended pixel
+        float2 nw = __fmul2_rn(na, T);                    // -alpha T
+        nw.x = sa ? 0.0f : nw.x;
+        nw.y = sb ? 0.0f : nw.y;
+        cr = __ffma2_rn(nr, nw, cr);
+        cg = __ffma2_rn(ng, nw, cg);
+        cb = __ffma2_rn(nb, nw, cb);
+        T.x = sa ? T.x : Tn.x;
+        T.y = sb ? T.y : Tn.y;
+        da = da || sa;
+        db = db || sb;
+    }
+}
+
 // sums the per-thread work counters of a counting launch into the frame counters
 __device__ __forceinline__ void flush_counts(Counters* c, unsigned n_eval, unsigned n_blend)
 {
@@ -108,9 +140,10 @@ template <bool FAST, int PPT, bool COUNT>
 __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
 {
     constexpr int NT = 256 / PPT; // threads per tile of 256 pixels (16 x 16, 32 x 8 or 8 x 32)
-    __shared__ float4 s_c0[NT];
-    __shared__ float4 s_c1[NT];
-    __shared__ float s_cb[NT];
+    constexpr int NH = (PPT + 1) / 2; // pixel pairs of a thread (one pixel of the last pair unused at PPT 1)
+    __shared__ float4 s_c0[NT];       // C1, C2, C3, C4
+    __shared__ float4 s_c1[NT];       // C5, C6, -b, -b
+    __shared__ float4 s_cn[NT];       // -r, -r, -g, -g (pairs for the packed blend)
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int x0 = tx * a.cam.tw, y0 = ty * a.cam.th;
     const int t = threadIdx.x;
@@ -120,13 +153,15 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
     const int px = x0 + lx, py = y0 + ly;
     const int W = a.cam.W, H = a.cam.H;
     bool done[PPT];
-    float T[PPT], cr[PPT], cg[PPT], cb[PPT];
+    // transmittance and colour of pixel i in component i & 1 of pair i / 2
+    float2 T2[NH], R2[NH], G2[NH], B2[NH];
 #pragma unroll
-    for (int i = 0; i < PPT; i++) {
-        done[i] = !(px < W && py + i < H);
-        T[i] = 1.0f;
-        cr[i] = cg[i] = cb[i] = 0.0f;
+    for (int h = 0; h < NH; h++) {
+        T2[h] = make_float2(1.0f, 1.0f);
+        R2[h] = G2[h] = B2[h] = make_float2(0.0f, 0.0f);
     }
+#pragma unroll
+    for (int i = 0; i < PPT; i++) done[i] = !(px < W && py + i < H);
     // hoisted pixel terms (tile-local)
     const float x = (float)lx, y = (float)ly;
     const float xx = x * x, xy = x * y, yy = y * y, y2p1 = 2.0f * y + 1.0f;
@@ -171,8 +206,8 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
             const float fg = __half2float(__ushort_as_half((unsigned short)(rg >> 16)));
             const float fb = __half2float(__ushort_as_half((unsigned short)(bb & 0xffffu)));
             s_c0[t] = make_float4(C1, C2, C3, C4);
-            s_c1[t] = make_float4(C5, C6, fr, fg);
-            s_cb[t] = fb;
+            s_c1[t] = make_float4(C5, C6, -fb, -fb);
+            s_cn[t] = make_float4(-fr, -fr, -fg, -fg);
         }
         __syncthreads();
         const int cnt = min((unsigned)NT, range.y - start);
@@ -180,10 +215,10 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
             for (int k = 0; k < cnt; k++) {
                 const float4 c0 = s_c0[k];
                 const float4 c1 = s_c1[k];
-                const float fb = s_cb[k];
+                const float4 cn = s_cn[k];
                 // Eq. (16): P(x, y) = C1 x^2 + C2 xy + C3 y^2 + C4 x + C5 y + C6
-                float P = fmaf(c0.x, xx, fmaf(c0.y, xy, fmaf(c0.z, yy, fmaf(c0.w, x, fmaf(c1.x, y, c1.y)))));
-                blend<FAST, COUNT>(P, c1.z, c1.w, fb, T[0], cr[0], cg[0], cb[0], done[0], n_eval, n_blend);
+                float P[PPT];
+                P[0] = fmaf(c0.x, xx, fmaf(c0.y, xy, fmaf(c0.z, yy, fmaf(c0.w, x, fmaf(c1.x, y, c1.y)))));
                 if (PPT >= 2) {
                     // Eq. (20): P(x, y+1) = P(x, y) + C2 x + C3 (2y + 1) + C5; the step to the next
                     // row grows by 2 C3 per row
@@ -191,8 +226,22 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
 #pragma unroll
                     for (int i = 1; i < PPT; i++) {
                         if (i > 1) d = fmaf(2.0f, c0.z, d);
-                        P = P + d;
-                        blend<FAST, COUNT>(P, c1.z, c1.w, fb, T[i], cr[i], cg[i], cb[i], done[i], n_eval, n_blend);
+                        P[i] = P[i - 1] + d;
+                    }
+                }
+                if (FAST && !COUNT && PPT >= 2) {
+#pragma unroll
+                    for (int h = 0; h < NH; h++)
+                        blend_pair_fast(P[2 * h], P[2 * h + 1], make_float2(cn.x, cn.y), make_float2(cn.z, cn.w),
+                                        make_float2(c1.z, c1.w), T2[h], R2[h], G2[h], B2[h], done[2 * h], done[2 * h + 1]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < PPT; i++) {
+                        float& Ti = (i & 1) ? T2[i >> 1].y : T2[i >> 1].x;
+                        float& Ri = (i & 1) ? R2[i >> 1].y : R2[i >> 1].x;
+                        float& Gi = (i & 1) ? G2[i >> 1].y : G2[i >> 1].x;
+                        float& Bi = (i & 1) ? B2[i >> 1].y : B2[i >> 1].x;
+                        blend<FAST, COUNT>(P[i], -cn.x, -cn.z, -c1.z, Ti, Ri, Gi, Bi, done[i], n_eval, n_blend);
                     }
                 }
             }
@@ -204,9 +253,10 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
     for (int i = 0; i < PPT; i++) {
         if (px < W && py + i < H) {
             const size_t o = (size_t)(py + i) * W + px;
-            a.out[o] = cr[i] + T[i] * a.cam.bg[0];
-            a.out[plane + o] = cg[i] + T[i] * a.cam.bg[1];
-            a.out[2 * plane + o] = cb[i] + T[i] * a.cam.bg[2];
+            const float Ti = (i & 1) ? T2[i >> 1].y : T2[i >> 1].x;
+            a.out[o] = ((i & 1) ? R2[i >> 1].y : R2[i >> 1].x) + Ti * a.cam.bg[0];
+            a.out[plane + o] = ((i & 1) ? G2[i >> 1].y : G2[i >> 1].x) + Ti * a.cam.bg[1];
+            a.out[2 * plane + o] = ((i & 1) ? B2[i >> 1].y : B2[i >> 1].x) + Ti * a.cam.bg[2];
         }
     }
 }

@@ -14,8 +14,10 @@
 // if entries overflowed). Each pass is then ONE kernel over tiles of 6144
 // (16- and 32-bit keys) or 4096 (64-bit keys) entries (one-sweep scheme): a
 // persistent grid takes tiles
-// in order from an atomic counter, ranks the tile's digits per warp (match_any,
-// or one ballot per digit bit where warps hold many distinct digits; stable),
+// in order from an atomic counter, ranks the tile's digits per warp (stable; per
+// pass one of: match_any, where a warp holds few distinct digits; a bit mask per
+// digit in shared memory that every lane ORs its bit into, where it holds many;
+// one ballot per digit bit),
 // publishes its per-digit counts, obtains the counts of all earlier tiles by
 // decoupled look-back (bounded waits), reorders the tile in shared memory by
 // digit and writes each digit run to its global position (runs of consecutive
@@ -23,6 +25,7 @@
 // of entries is read on the device: no host round trip. k_ranges finds the
 // per-tile [start, end) of a sorted array (exact mode; RoofGS frames find their
 // ranges inside the rasterizer).
+#include <algorithm>
 #include <mutex>
 
 #include "rg_internal.cuh"
@@ -259,10 +262,10 @@ struct SortSmem {
     unsigned tile;
 };
 
-template <typename K>
+template <typename K, int RM>
 __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k_onesweep(const K* __restrict__ kin, const unsigned* __restrict__ vin,
                                                         K* __restrict__ kout, unsigned* __restrict__ vout, int pass,
-                                                        int bit0, int ballot_rank, const unsigned* __restrict__ hist,
+                                                        int bit0, const unsigned* __restrict__ hist,
                                                         const unsigned* __restrict__ hist_pre, unsigned* status,
                                                         unsigned* status_next, Counters* ctr, Sticky* sticky)
 {
@@ -272,7 +275,11 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
     static_assert(S_THREADS >= RADIX && S_THREADS % 32 == 0, "sort tile needs one thread per digit");
     constexpr int S_WARPS = S_THREADS / 32;
     SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
+    static_assert(S_WARPS * RADIX <= S_TILE, "the peer masks live in the reorder buffer's values");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // SORT_RANK_PEERS: this warp's bit mask per digit, in the reorder buffer's values (free until
+    // barrier B; all zero whenever a tile's ranking starts)
+    unsigned* const pmask = S.vals + warp * RADIX;
     const int shift = bit0 + 8 * pass;
     // entry counts stay below 2^30 (workspace limit): 32-bit indices throughout
     const unsigned n = ctr->n_entries;
@@ -288,7 +295,10 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
     // counters cleared, during the write-out of the tile before it. Five
     // barriers per tile: after ranking (B), after the digit scan (C), after the
     // local offsets (D), after the reorder (E) and after the write-out (A).
-    for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) (&S.whist[0][0])[j] = 0u;
+    for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) {
+        (&S.whist[0][0])[j] = 0u;
+        if (RM == SORT_RANK_PEERS) S.vals[j] = 0u;
+    }
     if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
     __syncthreads();
     while (true) {
@@ -323,7 +333,7 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
         for (int i = 0; i < S_KPT; i++) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
             unsigned peers;
-            if (ballot_rank) { // lanes with the same digit: one ballot per digit bit (constant cost)
+            if (RM == SORT_RANK_BALLOT) { // lanes with the same digit: one ballot per digit bit (constant cost)
                 peers = 0xffffffffu;
 #pragma unroll
                 for (int bit = 0; bit < 8; bit++) {
@@ -331,13 +341,28 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
                     const unsigned bal = __ballot_sync(0xffffffffu, on);
                     peers &= on ? bal : ~bal;
                 }
+            } else if (RM == SORT_RANK_PEERS) { // every lane sets its bit in its digit's mask
+                atomicOr(&pmask[d], 1u << lane);
+                __syncwarp();
+                peers = pmask[d];
             } else { // hardware match: fast when the warp holds few distinct digits
                 peers = __match_any_sync(0xffffffffu, d);
             }
             const int leader = __ffs(peers) - 1;
             unsigned b = 0;
-            if (lane == leader) b = atomicAdd(&S.whist[warp][d], (unsigned)__popc(peers)); // one lane per digit
-            b = __shfl_sync(0xffffffffu, b, leader);
+            if (RM == SORT_RANK_PEERS) {
+                // one lane per digit: read and advance the warp's count, clear the mask once every
+                // lane has read it (after the shuffle)
+                if (lane == leader) b = S.whist[warp][d];
+                b = __shfl_sync(0xffffffffu, b, leader);
+                if (lane == leader) {
+                    S.whist[warp][d] = b + (unsigned)__popc(peers);
+                    pmask[d] = 0u;
+                }
+            } else {
+                if (lane == leader) b = atomicAdd(&S.whist[warp][d], (unsigned)__popc(peers)); // one lane per digit
+                b = __shfl_sync(0xffffffffu, b, leader);
+            }
             const unsigned r = b + __popc(peers & lt_mask);
             if (i & 1) rank2[i >> 1] |= r << 16;
             else rank2[i >> 1] = r;
@@ -462,10 +487,24 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
                 }
             }
         }
-        for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) (&S.whist[0][0])[j] = 0u;
+        // slot j of the reorder buffer is read above by thread j mod THREADS only: that thread
+        // clears the peer masks it aliases
+        for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) {
+            (&S.whist[0][0])[j] = 0u;
+            if (RM == SORT_RANK_PEERS) S.vals[j] = 0u;
+        }
         if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
         __syncthreads(); // A
     }
+}
+
+template <typename K, int RM>
+static int onesweep_blocks_per_sm(size_t smem)
+{
+    cudaFuncSetAttribute(k_onesweep<K, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, RM>, SortCfg<K>::THREADS, smem);
+    return per_sm;
 }
 
 template <typename K>
@@ -480,9 +519,12 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
         std::lock_guard<std::mutex> lock(g_shape_mu);
         int& g = g_shape[dev].onesweep_grid[kind];
         if (g == 0) { // once per device and key width, with the device current
-            cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K>, SortCfg<K>::THREADS, smem);
+            // the three rankings share the tile shape and the launch bounds: the smallest
+            // residency of the three sizes the persistent grid
+            const int r[3] = {onesweep_blocks_per_sm<K, SORT_RANK_MATCH>(smem),
+                              onesweep_blocks_per_sm<K, SORT_RANK_BALLOT>(smem),
+                              onesweep_blocks_per_sm<K, SORT_RANK_PEERS>(smem)};
+            const int per_sm = std::min(r[0], std::min(r[1], r[2]));
             g = (per_sm > 0 ? per_sm : 1) * sms;
         }
         grid = g;
@@ -496,10 +538,11 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
     for (int p = 0; p < a.passes; p++) {
         const int src = p & 1, dst = src ^ 1;
         unsigned* nxt = (p + 1 < a.passes) ? a.status[(p + 1) & 1] : nullptr;
-        k_onesweep<K><<<grid, SortCfg<K>::THREADS, smem, s>>>((const K*)a.keys[src], a.vals[src], (K*)a.keys[dst], a.vals[dst], p,
-                                                    a.bit0, (a.ballot_mask >> p) & 1, a.hist, a.hist_pre,
-                                                    a.status[p & 1], nxt,
-                                                    a.ctr, a.sticky);
+        const int rm = (int)((a.rank_modes >> (2 * p)) & 3u);
+        auto kern = rm == SORT_RANK_BALLOT ? k_onesweep<K, SORT_RANK_BALLOT>
+                                           : (rm == SORT_RANK_PEERS ? k_onesweep<K, SORT_RANK_PEERS> : k_onesweep<K, SORT_RANK_MATCH>);
+        kern<<<grid, SortCfg<K>::THREADS, smem, s>>>((const K*)a.keys[src], a.vals[src], (K*)a.keys[dst], a.vals[dst], p, a.bit0,
+                                                     a.hist, a.hist_pre, a.status[p & 1], nxt, a.ctr, a.sticky);
     }
 }
 
