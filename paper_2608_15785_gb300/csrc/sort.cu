@@ -304,6 +304,21 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
     while (true) {
         const unsigned tile = S.tile;
         if (tile >= ntiles) break;
+        if (tid == 0) {
+            // tiles are claimed in order, one per block at a time: the tile half a grid ahead is
+            // claimed by some block about half a tile's time from now. Its keys and values go to
+            // L2 by one bulk prefetch each (16-byte multiples inside the tile), so that block's
+            // key loads hit L2 (4K tile-bit passes 0.778 -> 0.742 ms; the keys alone 0.748 ms,
+            // the values alone 0.785 ms; a quarter grid ahead as good, one grid ahead 0.744 ms)
+            const unsigned nx = tile + gridDim.x / 2;
+            if (nx < ntiles) {
+                const unsigned b = nx * S_TILE;
+                const unsigned c = n - b < (unsigned)S_TILE ? n - b : (unsigned)S_TILE;
+                const unsigned kb = (c * (unsigned)sizeof(K)) & ~15u, vb = (c * 4u) & ~15u;
+                if (kb) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(kin + b), "r"(kb) : "memory");
+                if (vb) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(vin + b), "r"(vb) : "memory");
+            }
+        }
 
         constexpr bool STAGE = SortCfg<K>::STAGE_VALS;
         if constexpr (STAGE) {
