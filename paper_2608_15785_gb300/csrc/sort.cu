@@ -276,6 +276,11 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
     constexpr int S_WARPS = S_THREADS / 32;
     SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
     static_assert(S_WARPS * RADIX <= S_TILE, "the peer masks live in the reorder buffer's values");
+    // two ranking chains per warp where the reorder buffer's values hold two sets of peer masks
+    // and the counts of a chain fit 16 bits (32 x KPT / 2 elements)
+    constexpr bool TWO_CHAINS = 2 * S_WARPS * RADIX <= S_TILE && S_KPT % 4 == 0;
+    constexpr int HALF = S_KPT / 2;
+    constexpr int PM_WORDS = (TWO_CHAINS ? 2 : 1) * S_WARPS * RADIX; // peer-mask words in S.vals
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // SORT_RANK_PEERS: this warp's bit mask per digit, in the reorder buffer's values (free until
     // barrier B; all zero whenever a tile's ranking starts)
@@ -295,10 +300,9 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
     // counters cleared, during the write-out of the tile before it. Five
     // barriers per tile: after ranking (B), after the digit scan (C), after the
     // local offsets (D), after the reorder (E) and after the write-out (A).
-    for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) {
-        (&S.whist[0][0])[j] = 0u;
-        if (RM == SORT_RANK_PEERS) S.vals[j] = 0u;
-    }
+    for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) (&S.whist[0][0])[j] = 0u;
+    if (RM == SORT_RANK_PEERS)
+        for (int j = tid; j < PM_WORDS; j += S_THREADS) S.vals[j] = 0u;
     if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
     __syncthreads();
     while (true) {
@@ -344,44 +348,89 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
         // stable rank of each element among the warp's elements of the same digit
         // (below 32 * KPT: two ranks share a register)
         unsigned rank2[(S_KPT + 1) / 2];
-#pragma unroll
-        for (int i = 0; i < S_KPT; i++) {
-            const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
-            unsigned peers;
-            if (RM == SORT_RANK_BALLOT) { // lanes with the same digit: one ballot per digit bit (constant cost)
-                peers = 0xffffffffu;
-#pragma unroll
-                for (int bit = 0; bit < 8; bit++) {
-                    const bool on = (d >> bit) & 1u;
-                    const unsigned bal = __ballot_sync(0xffffffffu, on);
-                    peers &= on ? bal : ~bal;
-                }
-            } else if (RM == SORT_RANK_PEERS) { // every lane sets its bit in its digit's mask
-                atomicOr(&pmask[d], 1u << lane);
-                __syncwarp();
-                peers = pmask[d];
-            } else { // hardware match: fast when the warp holds few distinct digits
-                peers = __match_any_sync(0xffffffffu, d);
-            }
-            const int leader = __ffs(peers) - 1;
-            unsigned b = 0;
-            if (RM == SORT_RANK_PEERS) {
-                // one lane per digit: read and advance the warp's count, clear the mask once every
-                // lane has read it (after the shuffle)
-                if (lane == leader) b = S.whist[warp][d];
-                b = __shfl_sync(0xffffffffu, b, leader);
-                if (lane == leader) {
-                    S.whist[warp][d] = b + (unsigned)__popc(peers);
-                    pmask[d] = 0u;
-                }
-            } else {
-                if (lane == leader) b = atomicAdd(&S.whist[warp][d], (unsigned)__popc(peers)); // one lane per digit
-                b = __shfl_sync(0xffffffffu, b, leader);
-            }
-            const unsigned r = b + __popc(peers & lt_mask);
+        auto set_rank = [&](int i, unsigned r) {
             if (i & 1) rank2[i >> 1] |= r << 16;
             else rank2[i >> 1] = r;
-            __syncwarp();
+        };
+        // lanes of the warp holding digit d (each lane's bit), by the pass's ranking
+        auto ballot_peers = [&](unsigned d) {
+            unsigned peers = 0xffffffffu;
+#pragma unroll
+            for (int bit = 0; bit < 8; bit++) {
+                const bool on = (d >> bit) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, on);
+                peers &= on ? bal : ~bal;
+            }
+            return peers;
+        };
+        if constexpr (TWO_CHAINS) {
+            // two independent chains: elements 0 .. HALF-1 count in the low 16 bits of the warp's
+            // digit counters, elements HALF .. KPT-1 in the high 16 bits (each with its own peer
+            // masks), so the shared-memory round trips of one element overlap the other's
+            unsigned* const pmask_b = pmask + S_WARPS * RADIX;
+#pragma unroll
+            for (int i = 0; i < HALF; i++) {
+                const unsigned da = (unsigned)(k[i] >> shift) & 0xffu, db = (unsigned)(k[i + HALF] >> shift) & 0xffu;
+                unsigned pa, pb;
+                if (RM == SORT_RANK_BALLOT) {
+                    pa = ballot_peers(da);
+                    pb = ballot_peers(db);
+                } else if (RM == SORT_RANK_PEERS) {
+                    atomicOr(&pmask[da], 1u << lane);
+                    atomicOr(&pmask_b[db], 1u << lane);
+                    __syncwarp();
+                    pa = pmask[da];
+                    pb = pmask_b[db];
+                } else {
+                    pa = __match_any_sync(0xffffffffu, da);
+                    pb = __match_any_sync(0xffffffffu, db);
+                }
+                const int la = __ffs(pa) - 1, lb = __ffs(pb) - 1;
+                unsigned ba = 0, bb = 0;
+                if (lane == la) ba = atomicAdd(&S.whist[warp][da], (unsigned)__popc(pa));
+                if (lane == lb) bb = atomicAdd(&S.whist[warp][db], (unsigned)__popc(pb) << 16);
+                ba = __shfl_sync(0xffffffffu, ba, la) & 0xffffu;
+                bb = __shfl_sync(0xffffffffu, bb, lb) >> 16;
+                if (RM == SORT_RANK_PEERS) { // every lane has read the masks (the shuffles)
+                    if (lane == la) pmask[da] = 0u;
+                    if (lane == lb) pmask_b[db] = 0u;
+                }
+                set_rank(i, ba + __popc(pa & lt_mask));
+                set_rank(i + HALF, bb + __popc(pb & lt_mask));
+                __syncwarp();
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < S_KPT; i++) {
+                const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
+                unsigned peers;
+                if (RM == SORT_RANK_BALLOT) { // lanes with the same digit: one ballot per digit bit (constant cost)
+                    peers = ballot_peers(d);
+                } else if (RM == SORT_RANK_PEERS) { // every lane sets its bit in its digit's mask
+                    atomicOr(&pmask[d], 1u << lane);
+                    __syncwarp();
+                    peers = pmask[d];
+                } else { // hardware match: fast when the warp holds few distinct digits
+                    peers = __match_any_sync(0xffffffffu, d);
+                }
+                const int leader = __ffs(peers) - 1;
+                unsigned b = 0;
+                if (RM == SORT_RANK_PEERS) {
+                    // one lane per digit: read and advance the warp's count, clear the mask once every
+                    // lane has read it (after the shuffle)
+                    if (lane == leader) b = S.whist[warp][d];
+                    b = __shfl_sync(0xffffffffu, b, leader);
+                    if (lane == leader) {
+                        S.whist[warp][d] = b + (unsigned)__popc(peers);
+                        pmask[d] = 0u;
+                    }
+                } else {
+                    if (lane == leader) b = atomicAdd(&S.whist[warp][d], (unsigned)__popc(peers)); // one lane per digit
+                    b = __shfl_sync(0xffffffffu, b, leader);
+                }
+                set_rank(i, b + __popc(peers & lt_mask));
+                __syncwarp();
+            }
         }
         __syncthreads(); // B
         // digit tid: tile count, per-warp exclusive offsets, publish the count,
@@ -393,8 +442,14 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
 #pragma unroll
             for (int w = 0; w < S_WARPS; w++) {
                 const unsigned c = S.whist[w][tid];
-                S.whist[w][tid] = count;
-                count += c;
+                if constexpr (TWO_CHAINS) { // the warp's offsets of both chains, low and high half
+                    const unsigned ca = c & 0xffffu;
+                    S.whist[w][tid] = count | ((count + ca) << 16);
+                    count += ca + (c >> 16);
+                } else {
+                    S.whist[w][tid] = count;
+                    count += c;
+                }
             }
             *reinterpret_cast<volatile unsigned*>(status + (size_t)tile * RADIX + tid) = (tile == 0 ? SF_PRE : SF_AGG) | count;
 #pragma unroll
@@ -474,7 +529,9 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
         for (int i = 0; i < S_KPT; i++) {
             const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
             const unsigned r = (i & 1) ? (rank2[i >> 1] >> 16) : (rank2[i >> 1] & 0xffffu);
-            const unsigned pos = S.loff[d] + S.whist[warp][d] + r;
+            unsigned woff = S.whist[warp][d];
+            if constexpr (TWO_CHAINS) woff = i < HALF ? (woff & 0xffffu) : (woff >> 16);
+            const unsigned pos = S.loff[d] + woff + r;
             S.keys[pos] = k[i];
             if constexpr (SortCfg<K>::STAGE_VALS) S.vals[pos] = S.vin[warp * 32 * S_KPT + 32 * i + lane];
             else S.vals[pos] = v[i];
@@ -504,10 +561,9 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
         }
         // slot j of the reorder buffer is read above by thread j mod THREADS only: that thread
         // clears the peer masks it aliases
-        for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) {
-            (&S.whist[0][0])[j] = 0u;
-            if (RM == SORT_RANK_PEERS) S.vals[j] = 0u;
-        }
+        for (int j = tid; j < S_WARPS * RADIX; j += S_THREADS) (&S.whist[0][0])[j] = 0u;
+        if (RM == SORT_RANK_PEERS)
+            for (int j = tid; j < PM_WORDS; j += S_THREADS) S.vals[j] = 0u;
         if (tid == 0) S.tile = atomicAdd(&ctr->sort_tile_ctr[pass], 1u);
         __syncthreads(); // A
     }
