@@ -212,6 +212,7 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
         __syncthreads();
         const int cnt = min((unsigned)NT, range.y - start);
         if (!__all_sync(0xffffffffu, all_done)) {
+#pragma unroll 2 // two records per iteration: 4K raster 0.564 -> 0.558 ms
             for (int k = 0; k < cnt; k++) {
                 const float4 c0 = s_c0[k];
                 const float4 c1 = s_c1[k];

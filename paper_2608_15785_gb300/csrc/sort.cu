@@ -254,9 +254,8 @@ struct SortSmem {
     K keys[TILE];
     unsigned vals[TILE];
     unsigned vin[SortCfg<K>::STAGE_VALS ? TILE : 1]; // the tile's values as loaded (element order), by cp.async
-    unsigned whist[WARPS][RADIX]; // per-warp digit counters, then per-warp exclusive offsets
+    unsigned whist[WARPS][RADIX]; // per-warp digit counters, then each warp's first slot of the digit in the tile
     unsigned goff[RADIX];         // global exclusive digit offsets of this pass
-    unsigned loff[RADIX];         // tile-local exclusive digit offsets
     unsigned gbase[RADIX];        // global start of this tile's run of each digit minus its local start
     unsigned scan[WARPS];
     unsigned tile;
@@ -471,7 +470,11 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
         if (tid < RADIX) {
             lo = incl - count;
             for (int w = 0; w < warp; w++) lo += S.scan[w];
-            S.loff[tid] = lo;
+            // the tile-local start of the digit goes into every warp's offset (both chains' halves),
+            // so that the reorder reads one word per element
+            const unsigned lo2 = TWO_CHAINS ? (lo | (lo << 16)) : lo;
+#pragma unroll
+            for (int w = 0; w < S_WARPS; w++) S.whist[w][tid] += lo2;
         }
         __syncthreads(); // D
         if (tid < RADIX) {
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             const unsigned r = (i & 1) ? (rank2[i >> 1] >> 16) : (rank2[i >> 1] & 0xffffu);
             unsigned woff = S.whist[warp][d];
             if constexpr (TWO_CHAINS) woff = i < HALF ? (woff & 0xffffu) : (woff >> 16);
-            const unsigned pos = S.loff[d] + woff + r;
+            const unsigned pos = woff + r;
             S.keys[pos] = k[i];
             if constexpr (SortCfg<K>::STAGE_VALS) S.vals[pos] = S.vin[warp * 32 * S_KPT + 32 * i + lane];
             else S.vals[pos] = v[i];
