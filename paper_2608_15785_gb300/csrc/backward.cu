@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(B_THREADS) k_raster_backward(BackwardArgs a)
     __shared__ unsigned s_id[B_THREADS];
     __shared__ float4 s_xy[B_THREADS];
     __shared__ float4 s_co[B_THREADS];
+    grid_dependency_wait();
     __shared__ float4 s_rgb[B_THREADS];
     __shared__ int s_last;
     const int tile = blockIdx.x;
@@ -210,6 +211,7 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float g
 
 __global__ void __launch_bounds__(128) k_preprocess_backward(BackwardArgs a)
 {
+    grid_dependency_wait();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     float* dm = a.dmeans + 3 * i;
@@ -342,13 +344,13 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(BackwardArgs a)
 void launch_raster_backward(const BackwardArgs& a, cudaStream_t s)
 {
     const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
-    k_raster_backward<<<tiles, B_THREADS, 0, s>>>(a);
+    launch_dependent(k_raster_backward, dim3(tiles), dim3(B_THREADS), 0, s, a);
 }
 
 void launch_preprocess_backward(const BackwardArgs& a, cudaStream_t s)
 {
     if (a.n <= 0) return;
-    k_preprocess_backward<<<(unsigned)((a.n + 127) / 128), 128, 0, s>>>(a);
+    launch_dependent(k_preprocess_backward, dim3((unsigned)((a.n + 127) / 128)), dim3(128), 0, s, a);
 }
 
 } // namespace rg

@@ -335,6 +335,7 @@ __device__ __forceinline__ void frontend_block(const FrontendArgs& a, const unsi
 __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fused(FrontendArgs a)
 {
     __shared__ unsigned s_vb;
+    grid_dependency_wait();
     if (threadIdx.x == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
     __syncthreads();
     frontend_block(a, s_vb);
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS)
     k_frontend_views(const __grid_constant__ FrontendViews m)
 {
     __shared__ unsigned s_g;
+    grid_dependency_wait();
     if (threadIdx.x == 0) s_g = atomicAdd(m.claim, 1u);
     __syncthreads();
     const unsigned g = s_g;
@@ -359,7 +361,7 @@ void launch_frontend_views(const FrontendViews& m, cudaStream_t s)
 {
     const unsigned blocks = m.block_prefix[m.n_views];
     if (blocks == 0) return;
-    k_frontend_views<<<blocks, FE_THREADS, 0, s>>>(m);
+    launch_dependent(k_frontend_views, dim3(blocks), dim3(FE_THREADS), 0, s, m);
 }
 
 // Grid-stride over the Gaussians; each block also counts the 8-bit digits of its
@@ -369,6 +371,7 @@ __global__ void __launch_bounds__(256) k_depth_keys(FrontendArgs a, unsigned* ke
                                                     unsigned* hist, int passes)
 {
     __shared__ unsigned s_h[4][256];
+    grid_dependency_wait();
     for (int j = threadIdx.x; j < 4 * 256; j += 256) (&s_h[0][0])[j] = 0u;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_entries = (unsigned)a.n;
@@ -394,7 +397,7 @@ void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Co
     const int grid_cap = 8 * device_sm_count();
     const long long need = (a.n + 255) / 256;
     const unsigned blocks = (unsigned)(need < 1 ? 1 : (need < grid_cap ? need : grid_cap));
-    k_depth_keys<<<blocks, 256, 0, s>>>(a, keys, vals, ctr, hist, passes);
+    launch_dependent(k_depth_keys, dim3(blocks), dim3(256), 0, s, a, keys, vals, ctr, hist, passes);
 }
 
 int frontend_block_threads() { return FE_THREADS; }
@@ -403,7 +406,7 @@ void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s)
 {
     if (a.n <= 0) return;
     const unsigned blocks = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
-    k_frontend_fused<<<blocks, FE_THREADS, 0, s>>>(a);
+    launch_dependent(k_frontend_fused, dim3(blocks), dim3(FE_THREADS), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -413,6 +416,7 @@ constexpr int EX_THREADS = 256;
 
 __global__ void __launch_bounds__(EX_THREADS) k_exact_preprocess(ExactArgs a)
 {
+    grid_dependency_wait();
     const long long i = (long long)blockIdx.x * EX_THREADS + threadIdx.x;
     if (i >= a.n) return;
     a.touched[i] = 0;
@@ -470,6 +474,7 @@ __global__ void __launch_bounds__(EX_THREADS) k_exact_scan(ExactArgs a)
 {
     __shared__ unsigned s_vb;
     __shared__ unsigned long long s_wsum[EX_THREADS / 32];
+    grid_dependency_wait();
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
@@ -542,6 +547,7 @@ __global__ void __launch_bounds__(EX_THREADS) k_exact_duplicate(ExactArgs a)
 {
     __shared__ unsigned s_hd[4][RADIX_FE];             // depth digits (key bits 0..31)
     __shared__ unsigned s_d0[RADIX_FE + 1], s_h1[RADIX_FE]; // tile digits (key bits 32..47)
+    grid_dependency_wait();
     const int tid = threadIdx.x, lane = tid & 31;
     const bool count = a.hist != nullptr;
     if (count) {
@@ -639,19 +645,19 @@ __global__ void __launch_bounds__(EX_THREADS) k_exact_duplicate(ExactArgs a)
 void launch_exact_preprocess(const ExactArgs& a, cudaStream_t s)
 {
     if (a.n <= 0) return;
-    k_exact_preprocess<<<(unsigned)((a.n + EX_THREADS - 1) / EX_THREADS), EX_THREADS, 0, s>>>(a);
+    launch_dependent(k_exact_preprocess, dim3((unsigned)((a.n + EX_THREADS - 1) / EX_THREADS)), dim3(EX_THREADS), 0, s, a);
 }
 void launch_exact_scan(const ExactArgs& a, cudaStream_t s)
 {
     if (a.n <= 0) return;
-    k_exact_scan<<<(unsigned)((a.n + SCAN_TILE - 1) / SCAN_TILE), EX_THREADS, 0, s>>>(a);
+    launch_dependent(k_exact_scan, dim3((unsigned)((a.n + SCAN_TILE - 1) / SCAN_TILE)), dim3(EX_THREADS), 0, s, a);
 }
 void launch_exact_duplicate(const ExactArgs& a, cudaStream_t s)
 {
     if (a.n <= 0) return;
     const long long need = (a.n + EX_THREADS - 1) / EX_THREADS;
     const long long cap = 8ll * device_sm_count(); // grid-stride: digit counts flushed once per block
-    k_exact_duplicate<<<(unsigned)(need < cap ? need : cap), EX_THREADS, 0, s>>>(a);
+    launch_dependent(k_exact_duplicate, dim3((unsigned)(need < cap ? need : cap)), dim3(EX_THREADS), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------

@@ -265,6 +265,7 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
 template <bool FAST, int PPT, bool COUNT>
 __global__ void __launch_bounds__(256 / PPT) k_raster_roofgs(RasterArgs a)
 {
+    grid_dependency_wait();
     raster_tile<FAST, PPT, COUNT>(a, blockIdx.x);
 }
 
@@ -275,6 +276,7 @@ template <bool FAST, int PPT>
 __global__ void __launch_bounds__(256 / PPT) k_raster_views(const __grid_constant__ RasterViews m)
 {
     __shared__ unsigned s_g;
+    grid_dependency_wait();
     const unsigned total = m.tile_prefix[m.n_views];
     while (true) {
         if (threadIdx.x == 0) s_g = atomicAdd(m.claim, 1u);
@@ -296,7 +298,7 @@ static void raster_views_launch(const RasterViews& m, cudaStream_t s)
     const unsigned total = m.tile_prefix[m.n_views];
     unsigned grid = (unsigned)((per_sm > 0 ? per_sm : 1) * device_sm_count());
     if (grid > total) grid = total;
-    if (grid) k_raster_views<FAST, PPT><<<grid, 256 / PPT, 0, s>>>(m);
+    if (grid) launch_dependent(k_raster_views<FAST, PPT>, dim3(grid), dim3(256 / PPT), 0, s, m);
 }
 
 void launch_raster_views(const RasterViews& m, int fast_exp, int ppt, cudaStream_t s)
@@ -317,13 +319,13 @@ static void raster_roofgs_variant(const RasterArgs& a, cudaStream_t s)
 {
     const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
     if (a.fast_exp) {
-        if (a.ppt == 1) k_raster_roofgs<true, 1, COUNT><<<tiles, 256, 0, s>>>(a);
-        else if (a.ppt == 4) k_raster_roofgs<true, 4, COUNT><<<tiles, 64, 0, s>>>(a);
-        else k_raster_roofgs<true, 2, COUNT><<<tiles, 128, 0, s>>>(a);
+        if (a.ppt == 1) launch_dependent(k_raster_roofgs<true, 1, COUNT>, dim3(tiles), dim3(256), 0, s, a);
+        else if (a.ppt == 4) launch_dependent(k_raster_roofgs<true, 4, COUNT>, dim3(tiles), dim3(64), 0, s, a);
+        else launch_dependent(k_raster_roofgs<true, 2, COUNT>, dim3(tiles), dim3(128), 0, s, a);
     } else {
-        if (a.ppt == 1) k_raster_roofgs<false, 1, COUNT><<<tiles, 256, 0, s>>>(a);
-        else if (a.ppt == 4) k_raster_roofgs<false, 4, COUNT><<<tiles, 64, 0, s>>>(a);
-        else k_raster_roofgs<false, 2, COUNT><<<tiles, 128, 0, s>>>(a);
+        if (a.ppt == 1) launch_dependent(k_raster_roofgs<false, 1, COUNT>, dim3(tiles), dim3(256), 0, s, a);
+        else if (a.ppt == 4) launch_dependent(k_raster_roofgs<false, 4, COUNT>, dim3(tiles), dim3(64), 0, s, a);
+        else launch_dependent(k_raster_roofgs<false, 2, COUNT>, dim3(tiles), dim3(128), 0, s, a);
     }
 }
 
@@ -344,6 +346,7 @@ __global__ void __launch_bounds__(E_THREADS) k_raster_exact(RasterArgs a)
     __shared__ float4 s_m[E_THREADS];
     __shared__ float4 s_q[E_THREADS];
     __shared__ float4 s_rgb[E_THREADS];
+    grid_dependency_wait();
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int x0 = tx * a.cam.tw, y0 = ty * a.cam.th;
@@ -401,8 +404,8 @@ __global__ void __launch_bounds__(E_THREADS) k_raster_exact(RasterArgs a)
 void launch_raster_exact(const RasterArgs& a, cudaStream_t s)
 {
     const unsigned tiles = (unsigned)(a.tiles_x * a.tiles_y);
-    if (a.count) k_raster_exact<true><<<tiles, E_THREADS, 0, s>>>(a);
-    else k_raster_exact<false><<<tiles, E_THREADS, 0, s>>>(a);
+    if (a.count) launch_dependent(k_raster_exact<true>, dim3(tiles), dim3(E_THREADS), 0, s, a);
+    else launch_dependent(k_raster_exact<false>, dim3(tiles), dim3(E_THREADS), 0, s, a);
 }
 
 void launch_fast_exp_eval(const float* P, float* out, long long n, cudaStream_t s)

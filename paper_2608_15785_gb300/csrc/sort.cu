@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(H_THREADS) k_sort_hist(const K* __restrict__ k
                                                          const unsigned* __restrict__ hist_copies, int copy_stride)
 {
     __shared__ unsigned s_h[8][RADIX];
+    grid_dependency_wait();
     for (int j = threadIdx.x; j < 8 * RADIX; j += H_THREADS) (&s_h[0][0])[j] = 0u;
     __syncthreads();
     const long long n = ctr->n_entries;
@@ -269,6 +270,7 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
                                                         unsigned* status_next, Counters* ctr, Sticky* sticky)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    grid_dependency_wait();
     constexpr int S_THREADS = SortCfg<K>::THREADS, S_KPT = SortCfg<K>::KPT, S_TILE = tile_of<K>();
     // threads 0..255 each own one digit (scan, offsets, look-back): at least RADIX threads
     static_assert(S_THREADS >= RADIX && S_THREADS % 32 == 0, "sort tile needs one thread per digit");
@@ -612,8 +614,8 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
     const int hist_grid = 8 * sms;
     const K* kin = (const K*)a.keys[0];
     if (a.passes <= 0) return;
-    k_sort_hist<K><<<hist_grid, H_THREADS, 0, s>>>(kin, a.passes, a.bit0, a.hist, a.status[0], a.ctr, a.hist_pre,
-                                                   a.hist_copies, a.hist_copy_stride > 0 ? a.hist_copy_stride : 2);
+    launch_dependent(k_sort_hist<K>, dim3(hist_grid), dim3(H_THREADS), 0, s, kin, a.passes, a.bit0, a.hist, a.status[0],
+                     a.ctr, a.hist_pre, a.hist_copies, a.hist_copy_stride > 0 ? a.hist_copy_stride : 2);
     if (ev_after_hist) cudaEventRecord(ev_after_hist, s);
     for (int p = 0; p < a.passes; p++) {
         const int src = p & 1, dst = src ^ 1;
@@ -621,8 +623,9 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
         const int rm = (int)((a.rank_modes >> (2 * p)) & 3u);
         auto kern = rm == SORT_RANK_BALLOT ? k_onesweep<K, SORT_RANK_BALLOT>
                                            : (rm == SORT_RANK_PEERS ? k_onesweep<K, SORT_RANK_PEERS> : k_onesweep<K, SORT_RANK_MATCH>);
-        kern<<<grid, SortCfg<K>::THREADS, smem, s>>>((const K*)a.keys[src], a.vals[src], (K*)a.keys[dst], a.vals[dst], p, a.bit0,
-                                                     a.hist, a.hist_pre, a.status[p & 1], nxt, a.ctr, a.sticky);
+        launch_dependent(kern, dim3(grid), dim3(SortCfg<K>::THREADS), smem, s, (const K*)a.keys[src], a.vals[src],
+                         (K*)a.keys[dst], a.vals[dst], p, a.bit0, (const unsigned*)a.hist, (const unsigned*)a.hist_pre,
+                         a.status[p & 1], nxt, a.ctr, a.sticky);
     }
 }
 
@@ -650,6 +653,7 @@ template <typename K>
 __global__ void k_ranges(const K* __restrict__ keys, int tile_shift, long long ntiles, uint2* ranges,
                          const Counters* __restrict__ ctr)
 {
+    grid_dependency_wait();
     constexpr int V = 16 / sizeof(K);
     const long long n = ctr->n_entries;
     const long long nv = (n + V - 1) / V;
@@ -678,13 +682,14 @@ void launch_ranges(const RangeArgs& a, cudaStream_t s)
 {
     const int grid = 8 * sm_count();
     if (a.key_bytes == 2)
-        k_ranges<unsigned short><<<grid, 256, 0, s>>>((const unsigned short*)a.keys, a.tile_shift, a.ntiles, a.ranges,
-                                                      a.ctr);
+        launch_dependent(k_ranges<unsigned short>, dim3(grid), dim3(256), 0, s, (const unsigned short*)a.keys, a.tile_shift,
+                         a.ntiles, a.ranges, (const Counters*)a.ctr);
     else if (a.key_bytes == 4)
-        k_ranges<unsigned><<<grid, 256, 0, s>>>((const unsigned*)a.keys, a.tile_shift, a.ntiles, a.ranges, a.ctr);
+        launch_dependent(k_ranges<unsigned>, dim3(grid), dim3(256), 0, s, (const unsigned*)a.keys, a.tile_shift, a.ntiles,
+                         a.ranges, (const Counters*)a.ctr);
     else
-        k_ranges<unsigned long long><<<grid, 256, 0, s>>>((const unsigned long long*)a.keys, a.tile_shift, a.ntiles,
-                                                          a.ranges, a.ctr);
+        launch_dependent(k_ranges<unsigned long long>, dim3(grid), dim3(256), 0, s, (const unsigned long long*)a.keys,
+                         a.tile_shift, a.ntiles, a.ranges, (const Counters*)a.ctr);
 }
 
 } // namespace rg

@@ -36,6 +36,7 @@ constexpr unsigned TC_NONE = 0xFFFFu;                  // no entry (past the chu
 __global__ void __launch_bounds__(TC_THREADS) k_tc_count(TileSortArgs a)
 {
     extern __shared__ unsigned s_cnt[];
+    grid_dependency_wait();
     for (int t = threadIdx.x; t < a.T; t += TC_THREADS) s_cnt[t] = 0u;
     __syncthreads();
     const unsigned n = a.ctr->n_entries;
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_count(TileSortArgs a)
 // one thread per tile: column prefix over the chunks (coalesced across threads)
 __global__ void __launch_bounds__(256) k_tc_colscan(TileSortArgs a)
 {
+    grid_dependency_wait();
     const int t = blockIdx.x * 256 + threadIdx.x;
     if (t >= a.T) return;
     unsigned run = 0u;
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(256) k_tc_colscan(TileSortArgs a)
 __global__ void __launch_bounds__(1024) k_tc_tilescan(TileSortArgs a)
 {
     __shared__ unsigned s_w[32];
+    grid_dependency_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (a.T + 1023) / 1024;
     const int t0 = tid * per;
@@ -109,6 +112,7 @@ __global__ void __launch_bounds__(1024) k_tc_tilescan(TileSortArgs a)
 __global__ void __launch_bounds__(TC_THREADS) k_tc_scatter(TileSortArgs a)
 {
     extern __shared__ unsigned s_off[];
+    grid_dependency_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned* const row = a.M + (size_t)blockIdx.x * a.T;
     for (int t = tid; t < a.T; t += TC_THREADS) s_off[t] = row[t] + a.tot[t];
@@ -195,10 +199,10 @@ void launch_tile_counting_sort(const TileSortArgs& a, cudaStream_t s)
             g_tc_attr[dev] = (int)smem;
         }
     }
-    k_tc_count<<<a.chunks, TC_THREADS, smem, s>>>(a);
-    k_tc_colscan<<<(a.T + 255) / 256, 256, 0, s>>>(a);
-    k_tc_tilescan<<<1, 1024, 0, s>>>(a);
-    k_tc_scatter<<<a.chunks, TC_THREADS, smem, s>>>(a);
+    launch_dependent(k_tc_count, dim3(a.chunks), dim3(TC_THREADS), smem, s, a);
+    launch_dependent(k_tc_colscan, dim3((a.T + 255) / 256), dim3(256), 0, s, a);
+    launch_dependent(k_tc_tilescan, dim3(1), dim3(1024), 0, s, a);
+    launch_dependent(k_tc_scatter, dim3(a.chunks), dim3(TC_THREADS), smem, s, a);
 }
 
 } // namespace rg
