@@ -281,11 +281,18 @@ def run_ours(a, rank, world, local_rank):
         steps = a.steps if mode == "roofgs" else max(10, a.steps // 2)
         if sampler and mode == "roofgs":
             sampler.mark("timed_start")
-        ms = timed(mode, steps, binding.RG_FLAG_STAGE_EVENTS)
+        # the headline: plain frames (no events between the stages: they cost about 1.5 % at 4K and 5 %
+        # at 1080p, and they break the programmatic dependent launches between the kernels)
+        ms = timed(mode, steps, 0)
         if sampler and mode == "roofgs":
             sampler.mark("timed_end")
-        stage_ms, frames = gs.stage_times()
         gs.check()  # no overflow, no timed-out wait in the timed frames
+        # stage times and the kernels' rooflines: the same frames again with CUDA events between
+        # the stages, on the render stream
+        gs.stage_times()  # discard
+        timed(mode, min(steps, 100), binding.RG_FLAG_STAGE_EVENTS)
+        stage_ms, frames = gs.stage_times()
+        gs.check()
         poses_used = sorted({rank_pose(rank, world, k, len(cams)) for k in range(steps)})
         results[mode] = {"ms": ms, "steps": steps, "stats": mean_stats(stats, poses_used),
                          "stage_ms": [x / max(frames, 1) for x in stage_ms], "frames_timed_by_events": frames}
@@ -370,7 +377,9 @@ def run_ours(a, rank, world, local_rank):
            "entries_per_frame": round(r["stats"]["n_entries"]),
            "visible_per_frame": round(r["stats"]["n_visible"]),
            "pairs_per_frame": round(r["stats"]["n_pairs"]), "blends_per_frame": round(r["stats"]["n_blends"]),
-           "stage_ms": dict(zip(STAGES, [round(x, 4) for x in r["stage_ms"]]))}
+           "stage_ms": dict(zip(STAGES, [round(x, 4) for x in r["stage_ms"]])),
+           "stage_timing": "CUDA events between the stages on the render stream, over a second run of %d of the "
+                           "same frames (the headline frames run without them)" % r["frames_timed_by_events"]}
     if "exact" in results:
         ex = results["exact"]
         ex_fps = job_fps(ex["steps"], world, ex["ms"])
