@@ -178,7 +178,7 @@ struct NvtxScope {
 #define RG_DEPTH_RANK_MODES sort_rank_modes(SORT_RANK_PEERS, SORT_RANK_PEERS, SORT_RANK_PEERS, SORT_RANK_PEERS)
 #endif
 #ifndef RG_TILE_RANK_MODES
-#define RG_TILE_RANK_MODES sort_rank_modes(SORT_RANK_PEERS, SORT_RANK_MATCH)
+#define RG_TILE_RANK_MODES sort_rank_modes(SORT_RANK_PEERS, SORT_RANK_PEERS)
 #endif
 #ifndef RG_EXACT_RANK_MODES
 #define RG_EXACT_RANK_MODES sort_rank_modes(SORT_RANK_MATCH, SORT_RANK_MATCH, SORT_RANK_MATCH, SORT_RANK_MATCH) | \
@@ -256,8 +256,10 @@ rg_status roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t
         sa.passes = (F.lay.b_t + 7) / 8;
         sa.bit0 = F.lay.b_d;
         // depth-ordered entries of one Gaussian row carry consecutive tiles, so the warp
-        // holds many distinct low tile digits: rank that pass with the peer masks (4K tile-bit
-        // passes 0.832 -> 0.778 ms against ballots), the high digits with match_any
+        // holds many distinct low tile digits, and after that pass the high digits of
+        // neighbouring entries are scattered too: both passes rank with the peer masks (4K
+        // tile-bit passes 0.832 -> 0.778 ms against ballots on pass 0; with two ranking chains
+        // per warp 0.682 -> 0.656 ms against match_any on pass 1)
         sa.rank_modes = RG_TILE_RANK_MODES;
         // up to 2 tile-bit passes (b_t <= 16): the front end counts the digits of its
         // entries per tile row, and the sort's histogram pass only runs on overflow;
