@@ -562,9 +562,9 @@ void launch_exact_scan(const ExactArgs& a, cudaStream_t s);
 void launch_exact_duplicate(const ExactArgs& a, cudaStream_t s);
 
 // How a warp finds the lanes that hold the same digit (the ranking of a one-sweep pass):
-// match_any (few distinct digits per warp), one ballot per digit bit (constant cost),
-// or a per-warp bit mask per digit in shared memory that every lane ORs its bit into.
-enum { SORT_RANK_MATCH = 0, SORT_RANK_BALLOT = 1, SORT_RANK_PEERS = 2 };
+// match_any (few distinct digits per warp), or a per-warp bit mask per digit in shared
+// memory that every lane ORs its bit into (many distinct digits).
+enum { SORT_RANK_MATCH = 0, SORT_RANK_PEERS = 1 };
 constexpr unsigned sort_rank_modes(int m0, int m1 = 0, int m2 = 0, int m3 = 0)
 {
     return (unsigned)m0 | ((unsigned)m1 << 2) | ((unsigned)m2 << 4) | ((unsigned)m3 << 6);
@@ -578,7 +578,7 @@ struct SortArgs {
     int passes;           // 8-bit digits
     int bit0;             // lowest key bit sorted (digit p = bits bit0 + 8p ..)
     unsigned rank_modes;  // 2 bits per pass p (bits 2p, 2p+1): how warps rank the digits of pass p,
-                          // SORT_RANK_MATCH, SORT_RANK_BALLOT or SORT_RANK_PEERS
+                          // SORT_RANK_MATCH or SORT_RANK_PEERS
     unsigned* hist;       // [8][256]
     unsigned* hist_pre;   // [passes][256] digit counts from the producer of the keys, or null
     const unsigned* hist_copies; // [FE_HIST_COPIES][hist_copy_stride][256] the producer's partial counts

@@ -16,8 +16,7 @@
 // persistent grid takes tiles
 // in order from an atomic counter, ranks the tile's digits per warp (stable; per
 // pass one of: match_any, where a warp holds few distinct digits; a bit mask per
-// digit in shared memory that every lane ORs its bit into, where it holds many;
-// one ballot per digit bit),
+// digit in shared memory that every lane ORs its bit into, where it holds many),
 // publishes its per-digit counts, obtains the counts of all earlier tiles by
 // decoupled look-back (bounded waits), reorders the tile in shared memory by
 // digit and writes each digit run to its global position (runs of consecutive
@@ -353,17 +352,6 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             if (i & 1) rank2[i >> 1] |= r << 16;
             else rank2[i >> 1] = r;
         };
-        // lanes of the warp holding digit d (each lane's bit), by the pass's ranking
-        auto ballot_peers = [&](unsigned d) {
-            unsigned peers = 0xffffffffu;
-#pragma unroll
-            for (int bit = 0; bit < 8; bit++) {
-                const bool on = (d >> bit) & 1u;
-                const unsigned bal = __ballot_sync(0xffffffffu, on);
-                peers &= on ? bal : ~bal;
-            }
-            return peers;
-        };
         if constexpr (TWO_CHAINS) {
             // two independent chains: elements 0 .. HALF-1 count in the low 16 bits of the warp's
             // digit counters, elements HALF .. KPT-1 in the high 16 bits (each with its own peer
@@ -373,10 +361,7 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             for (int i = 0; i < HALF; i++) {
                 const unsigned da = (unsigned)(k[i] >> shift) & 0xffu, db = (unsigned)(k[i + HALF] >> shift) & 0xffu;
                 unsigned pa, pb;
-                if (RM == SORT_RANK_BALLOT) {
-                    pa = ballot_peers(da);
-                    pb = ballot_peers(db);
-                } else if (RM == SORT_RANK_PEERS) {
+                if (RM == SORT_RANK_PEERS) {
                     atomicOr(&pmask[da], 1u << lane);
                     atomicOr(&pmask_b[db], 1u << lane);
                     __syncwarp();
@@ -405,9 +390,7 @@ __global__ void __launch_bounds__(SortCfg<K>::THREADS, SortCfg<K>::MIN_BLOCKS) k
             for (int i = 0; i < S_KPT; i++) {
                 const unsigned d = (unsigned)(k[i] >> shift) & 0xffu;
                 unsigned peers;
-                if (RM == SORT_RANK_BALLOT) { // lanes with the same digit: one ballot per digit bit (constant cost)
-                    peers = ballot_peers(d);
-                } else if (RM == SORT_RANK_PEERS) { // every lane sets its bit in its digit's mask
+                if (RM == SORT_RANK_PEERS) { // every lane sets its bit in its digit's mask
                     atomicOr(&pmask[d], 1u << lane);
                     __syncwarp();
                     peers = pmask[d];
@@ -601,12 +584,10 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
         std::lock_guard<std::mutex> lock(g_shape_mu);
         int& g = g_shape[dev].onesweep_grid[kind];
         if (g == 0) { // once per device and key width, with the device current
-            // the three rankings share the tile shape and the launch bounds: the smallest
-            // residency of the three sizes the persistent grid
-            const int r[3] = {onesweep_blocks_per_sm<K, SORT_RANK_MATCH>(smem),
-                              onesweep_blocks_per_sm<K, SORT_RANK_BALLOT>(smem),
-                              onesweep_blocks_per_sm<K, SORT_RANK_PEERS>(smem)};
-            const int per_sm = std::min(r[0], std::min(r[1], r[2]));
+            // the two rankings share the tile shape and the launch bounds: the smaller
+            // residency of the two sizes the persistent grid
+            const int per_sm = std::min(onesweep_blocks_per_sm<K, SORT_RANK_MATCH>(smem),
+                                        onesweep_blocks_per_sm<K, SORT_RANK_PEERS>(smem));
             g = (per_sm > 0 ? per_sm : 1) * sms;
         }
         grid = g;
@@ -621,8 +602,7 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
         const int src = p & 1, dst = src ^ 1;
         unsigned* nxt = (p + 1 < a.passes) ? a.status[(p + 1) & 1] : nullptr;
         const int rm = (int)((a.rank_modes >> (2 * p)) & 3u);
-        auto kern = rm == SORT_RANK_BALLOT ? k_onesweep<K, SORT_RANK_BALLOT>
-                                           : (rm == SORT_RANK_PEERS ? k_onesweep<K, SORT_RANK_PEERS> : k_onesweep<K, SORT_RANK_MATCH>);
+        auto kern = rm == SORT_RANK_PEERS ? k_onesweep<K, SORT_RANK_PEERS> : k_onesweep<K, SORT_RANK_MATCH>;
         launch_dependent(kern, dim3(grid), dim3(SortCfg<K>::THREADS), smem, s, (const K*)a.keys[src], a.vals[src],
                          (K*)a.keys[dst], a.vals[dst], p, a.bit0, (const unsigned*)a.hist, (const unsigned*)a.hist_pre,
                          a.status[p & 1], nxt, a.ctr, a.sticky);

@@ -111,6 +111,8 @@ extern "C" rg_status rg_sort_pairs_noalloc(uint32_t* keys, uint32_t* vals, int64
     a.cap = NA_MAX;
     a.key_bytes = 4;
     a.passes = key_bits / 8;
+    // arbitrary keys hold many distinct digits per warp: every pass ranks with the peer masks
+    a.rank_modes = sort_rank_modes(SORT_RANK_PEERS, SORT_RANK_PEERS, SORT_RANK_PEERS, SORT_RANK_PEERS);
     a.hist = reinterpret_cast<unsigned*>(base + OFF_CTRL + sizeof(Counters));
     a.status[0] = reinterpret_cast<unsigned*>(base + OFF_STATUS0);
     a.status[1] = reinterpret_cast<unsigned*>(base + OFF_STATUS1);
