@@ -14,16 +14,18 @@
 // if entries overflowed). Each pass is then ONE kernel over tiles of 6144
 // (16- and 32-bit keys) or 4096 (64-bit keys) entries (one-sweep scheme): a
 // persistent grid takes tiles
-// in order from an atomic counter, ranks the tile's digits per warp (stable; per
-// pass one of: match_any, where a warp holds few distinct digits; a bit mask per
-// digit in shared memory that every lane ORs its bit into, where it holds many),
-// publishes its per-digit counts, obtains the counts of all earlier tiles by
-// decoupled look-back (bounded waits), reorders the tile in shared memory by
-// digit and writes each digit run to its global position (runs of consecutive
-// addresses). Per pass every entry is read once and written once. The number
-// of entries is read on the device: no host round trip. k_ranges finds the
-// per-tile [start, end) of a sorted array (exact mode; RoofGS frames find their
-// ranges inside the rasterizer).
+// in order from an atomic counter (and prefetches the tile half a grid ahead into
+// L2), ranks the tile's digits per warp (stable; per pass one of: match_any,
+// where a warp holds few distinct digits; a bit mask per digit in shared memory
+// that every lane ORs its bit into, where it holds many; where shared memory
+// allows, each warp's elements as two interleaved chains), publishes its
+// per-digit counts, obtains the counts of all earlier tiles by decoupled
+// look-back (bounded waits), reorders the tile in shared memory by digit and
+// writes each digit run to its global position (runs of consecutive addresses).
+// Per pass every entry is read once and written once. The number of entries is
+// read on the device: no host round trip. k_ranges finds the per-tile
+// [start, end) of a sorted array (exact mode; RoofGS frames find their ranges
+// inside the rasterizer).
 #include <algorithm>
 #include <mutex>
 
@@ -61,7 +63,7 @@ template <> // 16-bit tile ids (a key still takes a register)
 struct SortCfg<unsigned short> {
     static constexpr int THREADS = RG_SORT_T16, KPT = RG_SORT_K16, MIN_BLOCKS = RG_SORT_B16;
     // values staged in shared memory by cp.async instead of registers: no spills at 80
-    // registers, 72.7 KB per CTA (3 per SM still fit); 4K tile-bit passes 0.855 -> 0.835 ms
+    // registers, 71.7 KB per CTA (3 per SM still fit); 4K tile-bit passes 0.855 -> 0.835 ms
     static constexpr bool STAGE_VALS = true;
 };
 template <>
