@@ -389,10 +389,11 @@ def run_ours(a, rank, world, local_rank):
         cfg["exact_entries_per_frame"] = round(ex["stats"]["n_entries"])
     line["config"] = cfg
     line["roofline"], line["stages"] = rooflines(r, a, props, clocks)
-    # per frame: depth keys, depth-sort histogram + passes, fused front end, entry histogram +
-    # tile-bit passes, rasterizer (which finds the tile ranges itself)
+    # per frame: depth keys (which also clear the depth sort's look-back status), depth-sort
+    # passes, fused front end, entry histogram + tile-bit passes, rasterizer (which finds the
+    # tile ranges itself)
     gp = (int(r["stats"]["b_d"]) + 7) // 8
-    line["gpu_launches"] = r["steps"] * (1 + 1 + gp + 1 + 1 + int(r["stats"]["sort_passes"]) + 1)
+    line["gpu_launches"] = r["steps"] * (1 + gp + 1 + 1 + int(r["stats"]["sort_passes"]) + 1)
     line["e2e"] = {"value": round(job_fps(e2e_steps, world, e2e_ms), 2), "unit": UNIT,
                    "h2d_bytes_per_step": 100,  # the rg_camera struct, passed by value per call
                    "d2h_bytes_per_step": 3 * a.width * a.height * 4,

@@ -368,11 +368,15 @@ void launch_frontend_views(const FrontendViews& m, cudaStream_t s)
 // keys for the depth sort's passes in shared memory and adds them to `hist`
 // ([passes][256], zeroed beforehand) once at the end.
 __global__ void __launch_bounds__(256) k_depth_keys(FrontendArgs a, unsigned* keys, unsigned* vals, Counters* ctr,
-                                                    unsigned* hist, int passes)
+                                                    unsigned* hist, int passes, unsigned* status0,
+                                                    long long status_words)
 {
     __shared__ unsigned s_h[4][256];
     grid_dependency_wait();
     for (int j = threadIdx.x; j < 4 * 256; j += 256) (&s_h[0][0])[j] = 0u;
+    // the look-back status of the depth sort's first pass (no histogram kernel runs before it)
+    for (long long j = (long long)blockIdx.x * 256 + threadIdx.x; j < status_words; j += (long long)gridDim.x * 256)
+        status0[j] = 0u;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_entries = (unsigned)a.n;
     for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < a.n; i += (long long)gridDim.x * 256) {
@@ -392,12 +396,13 @@ __global__ void __launch_bounds__(256) k_depth_keys(FrontendArgs a, unsigned* ke
 }
 
 void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, unsigned* hist,
-                       int passes, cudaStream_t s)
+                       int passes, unsigned* status0, cudaStream_t s)
 {
     const int grid_cap = 8 * device_sm_count();
     const long long need = (a.n + 255) / 256;
     const unsigned blocks = (unsigned)(need < 1 ? 1 : (need < grid_cap ? need : grid_cap));
-    launch_dependent(k_depth_keys, dim3(blocks), dim3(256), 0, s, a, keys, vals, ctr, hist, passes);
+    launch_dependent(k_depth_keys, dim3(blocks), dim3(256), 0, s, a, keys, vals, ctr, hist, passes, status0,
+                     sort_status_words(4, a.n));
 }
 
 int frontend_block_threads() { return FE_THREADS; }

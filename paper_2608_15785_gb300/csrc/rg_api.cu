@@ -250,8 +250,10 @@ rg_status roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t
         ga.max_tiles = (n + sort_tile_items() - 1) / sort_tile_items();
         ga.ctr = reinterpret_cast<Counters*>(w.ctrl.as<unsigned char>() + CTRL_BYTES);
         ga.sticky = sticky;
-        // the depth keys' digits are counted as they are written (ga.passes <= 4)
+        // the depth keys' digits are counted as they are written (ga.passes <= 4), and the
+        // depth-key kernel clears the first pass's look-back status: no histogram kernel
         ga.hist_pre = ga.hist;
+        ga.hist_done = 1;
         a.order = w.gvals[ga.passes & 1].as<unsigned>();
         sa.passes = (F.lay.b_t + 7) / 8;
         sa.bit0 = F.lay.b_d;
@@ -312,7 +314,8 @@ rg_status roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t
 // digit counts), then their stable sort.
 void roofgs_depth_order(const RoofgsFrame& f, Workspace& w, cudaStream_t st)
 {
-    launch_depth_keys(f.fa, w.gkeys[0].as<unsigned>(), w.gvals[0].as<unsigned>(), f.ga.ctr, f.ga.hist, f.ga.passes, st);
+    launch_depth_keys(f.fa, w.gkeys[0].as<unsigned>(), w.gvals[0].as<unsigned>(), f.ga.ctr, f.ga.hist, f.ga.passes,
+                      f.ga.status[0], st);
     launch_sort(f.ga, st, nullptr);
 }
 

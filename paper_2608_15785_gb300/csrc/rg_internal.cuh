@@ -527,8 +527,11 @@ int frontend_block_threads();
 // quantized depth (Eq. (9)) of every Gaussian as a sort key, Gaussian index as value;
 // culled Gaussians get 2^b_d - 1 (the fused front end skips them); writes n to ctr and
 // adds the keys' 8-bit digit counts of `passes` (<= 4) passes to hist [passes][256]
+// look-back status words of a one-sweep pass over n keys of key_bytes bytes (256 per sort tile)
+long long sort_status_words(int key_bytes, long long n);
+// quantized depth keys and their digit counts; also clears status0[0 .. sort_status_words(4, n))
 void launch_depth_keys(const FrontendArgs& a, unsigned* keys, unsigned* vals, Counters* ctr, unsigned* hist,
-                       int passes, cudaStream_t s);
+                       int passes, unsigned* status0, cudaStream_t s);
 
 struct ExactArgs {
     const float* means;
@@ -586,6 +589,8 @@ struct SortArgs {
     int hist_copy_stride;        // passes per copy of hist_copies
     unsigned* status[2];  // [max_tiles][256] look-back status per pass (alternating)
     long long max_tiles;
+    int hist_done;        // 1: hist_pre is complete and status[0] clear when the sort starts (the
+                          // producer of the keys did both): no histogram kernel
     Counters* ctr;
     Sticky* sticky;
 };

@@ -79,6 +79,12 @@ constexpr int LB_WINDOW = 8; // predecessors inspected per round trip of the loo
 constexpr unsigned SF_AGG = 1u << 30, SF_PRE = 2u << 30, SF_VAL = (1u << 30) - 1u;
 constexpr int H_THREADS = 256;
 
+long long sort_status_words(int key_bytes, long long n)
+{
+    const long long t = key_bytes == 2 ? tile_of<unsigned short>() : (key_bytes == 4 ? tile_of<unsigned>() : tile_of<unsigned long long>());
+    return (n + t - 1) / t * RADIX;
+}
+
 // smallest tile of any key width: sizes the per-tile look-back status arrays
 int sort_tile_items()
 {
@@ -597,8 +603,10 @@ static void sort_impl(const SortArgs& a, cudaStream_t s, cudaEvent_t ev_after_hi
     const int hist_grid = 8 * sms;
     const K* kin = (const K*)a.keys[0];
     if (a.passes <= 0) return;
-    launch_dependent(k_sort_hist<K>, dim3(hist_grid), dim3(H_THREADS), 0, s, kin, a.passes, a.bit0, a.hist, a.status[0],
-                     a.ctr, a.hist_pre, a.hist_copies, a.hist_copy_stride > 0 ? a.hist_copy_stride : 2);
+    if (!a.hist_done)
+        launch_dependent(k_sort_hist<K>, dim3(hist_grid), dim3(H_THREADS), 0, s, kin, a.passes, a.bit0, a.hist,
+                         a.status[0], a.ctr, a.hist_pre, a.hist_copies,
+                         a.hist_copy_stride > 0 ? a.hist_copy_stride : 2);
     if (ev_after_hist) cudaEventRecord(ev_after_hist, s);
     for (int p = 0; p < a.passes; p++) {
         const int src = p & 1, dst = src ^ 1;
