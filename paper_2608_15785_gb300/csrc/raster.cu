@@ -17,8 +17,10 @@
 // y^2, x, y, each next one follows from Eq. (20) (two additions per extra
 // row). Pairs with P < -ln 255 are skipped before any exponential (Eq. (23));
 // alpha = min(0.99, exp^(P)) with the bit-level exponential of Eq. (24)
-// (Eq. (25)). A warp whose pixels are all finished skips the batch (vote); the
-// block leaves once every pixel is finished.
+// (Eq. (25)). With 2 or 4 pixels per thread the timed kernel blends the thread's
+// pixels in pairs with packed FP32x2 FMAs (the same roundings as one at a time). A
+// warp whose pixels are all finished skips the batch (vote); the block leaves once
+// every pixel is finished.
 #include "rg_internal.cuh"
 
 namespace rg {
