@@ -78,6 +78,8 @@ def parse():
                    help="RoofGS pixels per thread in the rasterizer (2 = the paper's dual-pixel scheme)")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-tile-sort", action="store_true")
+    p.add_argument("--no-per-pose", action="store_true",
+                   help="skip the per-pose median frame times (100 frames per pose in RoofGS mode)")
     return p.parse_args()
 
 
@@ -263,6 +265,26 @@ def run_ours(a, rank, world, local_rank):
         barrier()
         return slowest_ms(e0.elapsed_time(e1), dist, dev)
 
+    def per_pose(mode, frames):
+        # the timing protocol of the workload's definition: for every pose, `frames` frames of that
+        # pose with a CUDA event between consecutive frames; the median frame time per pose, and the
+        # frame rate averaged over the poses
+        med = []
+        for cam in cams:
+            for _ in range(3):
+                gs.render(cam, mode=mode, flags=rflags, out=out)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(frames + 1)]
+            ev[0].record(stream)
+            for k in range(frames):
+                gs.render(cam, mode=mode, flags=rflags, out=out)
+                ev[k + 1].record(stream)
+            torch.cuda.synchronize(dev)
+            t = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(frames))
+            med.append(t[frames // 2] if frames % 2 else 0.5 * (t[frames // 2 - 1] + t[frames // 2]))
+        gs.check()
+        return {"frames_per_pose": frames, "median_ms_per_pose": [round(m, 4) for m in med],
+                "fps_mean_over_poses_of_median": round(sum(1000.0 / m for m in med) / len(med), 2)}
+
     # RoofGS ingredient flag for the rasterizer's pixels per thread (ignored in exact mode)
     rflags = {1: binding.RG_FLAG_SINGLE_PIXEL, 2: 0, 4: binding.RG_FLAG_QUAD_PIXEL}[a.ppt]
     results = {}
@@ -296,6 +318,8 @@ def run_ours(a, rank, world, local_rank):
         poses_used = sorted({rank_pose(rank, world, k, len(cams)) for k in range(steps)})
         results[mode] = {"ms": ms, "steps": steps, "stats": mean_stats(stats, poses_used),
                          "stage_ms": [x / max(frames, 1) for x in stage_ms], "frames_timed_by_events": frames}
+        if world == 1 and not a.no_per_pose:
+            results[mode]["per_pose"] = per_pose(mode, 100 if mode == "roofgs" else 10)
     # end-to-end through the public API: every frame rendered by rg_render and delivered to pinned
     # host memory inside the timed region, three ways. Serial copy: render, copy, render, ... on one
     # stream. Pipelined copy: two image buffers; frame k's device->host copy runs on a copy stream
@@ -380,6 +404,8 @@ def run_ours(a, rank, world, local_rank):
            "stage_ms": dict(zip(STAGES, [round(x, 4) for x in r["stage_ms"]])),
            "stage_timing": "CUDA events between the stages on the render stream, over a second run of %d of the "
                            "same frames (the headline frames run without them)" % r["frames_timed_by_events"]}
+    if "per_pose" in r:
+        cfg["per_pose"] = r["per_pose"]
     if "exact" in results:
         ex = results["exact"]
         ex_fps = job_fps(ex["steps"], world, ex["ms"])
@@ -387,6 +413,8 @@ def run_ours(a, rank, world, local_rank):
         cfg["speedup_vs_exact"] = round(fps / ex_fps, 3)
         cfg["exact_stage_ms"] = dict(zip(STAGES, [round(x, 4) for x in ex["stage_ms"]]))
         cfg["exact_entries_per_frame"] = round(ex["stats"]["n_entries"])
+        if "per_pose" in ex:
+            cfg["exact_per_pose"] = ex["per_pose"]
     line["config"] = cfg
     line["roofline"], line["stages"] = rooflines(r, a, props, clocks)
     # per frame: depth keys (which also clear the depth sort's look-back status), depth-sort
