@@ -73,7 +73,8 @@ __device__ __forceinline__ void blend(float P, float r, float g, float b, float&
 // is -exp^(P): that addition only sets the sign bit) and with the negated colours nr, ng,
 // nb: T + T (-alpha) = T (1 - alpha) and c + (-r)(-alpha T) = c + r (alpha T) round to the
 // same values. A pixel that is finished or below -ln 255 takes -alpha = 0, which leaves
-// its T and colour unchanged.
+// its T and colour unchanged. The stop below 1e-4 (once per pixel at most) is a branch
+// around the common path rather than selects in it (4K raster 0.558 -> 0.500 ms).
 __device__ __forceinline__ void blend_pair_fast(float Pa, float Pb, float2 nr, float2 ng, float2 nb, float2& T, float2& cr,
                                                 float2& cg, float2& cb, bool& da, bool& db)
 {
@@ -84,18 +85,26 @@ __device__ __forceinline__ void blend_pair_fast(float Pa, float Pb, float2 nr, f
         const float ea = __uint_as_float(__float_as_uint(w.x) << 6); // -exp^(P)
         const float eb = __uint_as_float(__float_as_uint(w.y) << 6);
         const float2 na = make_float2(ua ? fmaxf(-0.99f, ea) : 0.0f, ub ? fmaxf(-0.99f, eb) : 0.0f);
-        const float2 Tn = __ffma2_rn(T, na, T);
-        const bool sa = Tn.x < 1e-4f, sb = Tn.y < 1e-4f; // only for a blended pixel
-        float2 nw = __fmul2_rn(na, T);                    // -alpha T
-        nw.x = sa ? 0.0f : nw.x;
-        nw.y = sb ? 0.0f : nw.y;
+        float2 Tn = __ffma2_rn(T, na, T);
+        float2 nw = __fmul2_rn(na, T); // -alpha T
+        if (Tn.x < 1e-4f || Tn.y < 1e-4f) {
+            // once per pixel at most: the pair that would take T below 1e-4 stops the pixel and
+            // adds nothing (weight 0; T kept). Only a blended pixel can get here (T >= 1e-4 else)
+            if (Tn.x < 1e-4f) {
+                nw.x = 0.0f;
+                Tn.x = T.x;
+                da = true;
+            }
+            if (Tn.y < 1e-4f) {
+                nw.y = 0.0f;
+                Tn.y = T.y;
+                db = true;
+            }
+        }
         cr = __ffma2_rn(nr, nw, cr);
         cg = __ffma2_rn(ng, nw, cg);
         cb = __ffma2_rn(nb, nw, cb);
-        T.x = sa ? T.x : Tn.x;
-        T.y = sb ? T.y : Tn.y;
-        da = da || sa;
-        db = db || sb;
+        T = Tn;
     }
 }
 
