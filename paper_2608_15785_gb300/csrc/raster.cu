@@ -76,9 +76,10 @@ __device__ __forceinline__ void blend(float P, float r, float g, float b, float&
 // its T and colour unchanged. The stop below 1e-4 (once per pixel at most) is a branch
 // around the common path rather than selects in it (4K raster 0.558 -> 0.500 ms).
 __device__ __forceinline__ void blend_pair_fast(float Pa, float Pb, float2 nr, float2 ng, float2 nb, float2& T, float2& cr,
-                                                float2& cg, float2& cb, bool& da, bool& db)
+                                                float2& cg, float2& cb, float& ta, float& tb)
 {
-    const bool ua = !da && Pa >= -LN255F, ub = !db && Pb >= -LN255F;
+    // ta, tb: the pixels' skip thresholds, -ln 255 while blending, +inf once finished
+    const bool ua = Pa >= ta, ub = Pb >= tb;
     if (ua || ub) {
         const float2 w = __ffma2_rn(make_float2(Pa, Pb), make_float2(1.44269502f, 1.44269502f),
                                     make_float2(126.954323f, 126.954323f));
@@ -93,12 +94,12 @@ __device__ __forceinline__ void blend_pair_fast(float Pa, float Pb, float2 nr, f
             if (Tn.x < 1e-4f) {
                 nw.x = 0.0f;
                 Tn.x = T.x;
-                da = true;
+                ta = __int_as_float(0x7f800000); // +inf: finished
             }
             if (Tn.y < 1e-4f) {
                 nw.y = 0.0f;
                 Tn.y = T.y;
-                db = true;
+                tb = __int_as_float(0x7f800000);
             }
         }
         cr = __ffma2_rn(nr, nw, cr);
@@ -164,6 +165,10 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
     const int px = x0 + lx, py = y0 + ly;
     const int W = a.cam.W, H = a.cam.H;
     bool done[PPT];
+    // the packed pair blend keeps a pixel's state as its skip threshold instead: -ln 255 while it
+    // blends, +inf once finished (one compare per pixel and Gaussian instead of two tests)
+    constexpr bool PAIRS = FAST && !COUNT && PPT >= 2;
+    float thr[PPT];
     // transmittance and colour of pixel i in component i & 1 of pair i / 2
     float2 T2[NH], R2[NH], G2[NH], B2[NH];
 #pragma unroll
@@ -172,7 +177,10 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
         R2[h] = G2[h] = B2[h] = make_float2(0.0f, 0.0f);
     }
 #pragma unroll
-    for (int i = 0; i < PPT; i++) done[i] = !(px < W && py + i < H);
+    for (int i = 0; i < PPT; i++) {
+        done[i] = !(px < W && py + i < H);
+        thr[i] = done[i] ? __int_as_float(0x7f800000) : -LN255F;
+    }
     // hoisted pixel terms (tile-local)
     const float x = (float)lx, y = (float)ly;
     const float xx = x * x, xy = x * y, yy = y * y, y2p1 = 2.0f * y + 1.0f;
@@ -196,7 +204,7 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
     for (unsigned start = range.x; start < range.y; start += NT) {
         bool all_done = true;
 #pragma unroll
-        for (int i = 0; i < PPT; i++) all_done = all_done && done[i];
+        for (int i = 0; i < PPT; i++) all_done = all_done && (PAIRS ? thr[i] == __int_as_float(0x7f800000) : done[i]);
         if (__syncthreads_count(!all_done) == 0) break;
         const unsigned j = start + t;
         if (j < range.y) {
@@ -241,11 +249,11 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
                         P[i] = P[i - 1] + d;
                     }
                 }
-                if (FAST && !COUNT && PPT >= 2) {
+                if (PAIRS) {
 #pragma unroll
                     for (int h = 0; h < NH; h++)
                         blend_pair_fast(P[2 * h], P[2 * h + 1], make_float2(cn.x, cn.y), make_float2(cn.z, cn.w),
-                                        make_float2(c1.z, c1.w), T2[h], R2[h], G2[h], B2[h], done[2 * h], done[2 * h + 1]);
+                                        make_float2(c1.z, c1.w), T2[h], R2[h], G2[h], B2[h], thr[2 * h], thr[2 * h + 1]);
                 } else {
 #pragma unroll
                     for (int i = 0; i < PPT; i++) {
