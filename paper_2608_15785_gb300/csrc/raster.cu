@@ -67,45 +67,65 @@ __device__ __forceinline__ void blend(float P, float r, float g, float b, float&
     }
 }
 
-// Two pixels of a thread blended together with packed FP32x2 arithmetic (FFMA2 / FMUL2:
-// one instruction for both pixels). Per pixel the operations and roundings of
+// A thread's pixels blended in pairs with packed FP32x2 arithmetic (FFMA2 / FMUL2: one
+// instruction for both pixels of a pair). Per pixel the operations and roundings of
 // blend<true, false>, written with -alpha (the shift-add of Eq. (24) without its + 2^31
 // is -exp^(P): that addition only sets the sign bit) and with the negated colours nr, ng,
 // nb: T + T (-alpha) = T (1 - alpha) and c + (-r)(-alpha T) = c + r (alpha T) round to the
-// same values. A pixel that is finished or below -ln 255 takes -alpha = 0, which leaves
-// its T and colour unchanged. The stop below 1e-4 (once per pixel at most) is a branch
-// around the common path rather than selects in it (4K raster 0.558 -> 0.500 ms).
-__device__ __forceinline__ void blend_pair_fast(float Pa, float Pb, float2 nr, float2 ng, float2 nb, float2& T, float2& cr,
-                                                float2& cg, float2& cb, float& ta, float& tb)
+// same values. A pixel's state is its skip threshold thr: -ln 255 while it blends, +inf
+// once finished; a pixel below its threshold takes -alpha = 0, which leaves its T and
+// colour unchanged. One branch skips the Gaussian when no pixel of the thread needs it;
+// the stop below 1e-4 (at most once in a pixel's life) is a branch around the common path
+// (4K raster 0.558 -> 0.476 ms against selects on every pair and a finished flag beside
+// the threshold test; 0.476 -> 0.453 ms with the branches taken once for all of the
+// thread's pairs instead of once per pair).
+template <int NH>
+__device__ __forceinline__ void blend_pairs_fast(const float (&P)[2 * NH], float2 nr, float2 ng, float2 nb,
+                                                 float2 (&T)[NH], float2 (&cr)[NH], float2 (&cg)[NH],
+                                                 float2 (&cb)[NH], float (&thr)[2 * NH])
 {
-    // ta, tb: the pixels' skip thresholds, -ln 255 while blending, +inf once finished
-    const bool ua = Pa >= ta, ub = Pb >= tb;
-    if (ua || ub) {
-        const float2 w = __ffma2_rn(make_float2(Pa, Pb), make_float2(1.44269502f, 1.44269502f),
+    bool u[2 * NH];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < 2 * NH; i++) {
+        u[i] = P[i] >= thr[i];
+        any = any || u[i];
+    }
+    if (!any) return;
+    float2 Tn[NH], nw[NH];
+    bool stop = false;
+#pragma unroll
+    for (int h = 0; h < NH; h++) {
+        const float2 w = __ffma2_rn(make_float2(P[2 * h], P[2 * h + 1]), make_float2(1.44269502f, 1.44269502f),
                                     make_float2(126.954323f, 126.954323f));
         const float ea = __uint_as_float(__float_as_uint(w.x) << 6); // -exp^(P)
         const float eb = __uint_as_float(__float_as_uint(w.y) << 6);
-        const float2 na = make_float2(ua ? fmaxf(-0.99f, ea) : 0.0f, ub ? fmaxf(-0.99f, eb) : 0.0f);
-        float2 Tn = __ffma2_rn(T, na, T);
-        float2 nw = __fmul2_rn(na, T); // -alpha T
-        if (Tn.x < 1e-4f || Tn.y < 1e-4f) {
-            // once per pixel at most: the pair that would take T below 1e-4 stops the pixel and
-            // adds nothing (weight 0; T kept). Only a blended pixel can get here (T >= 1e-4 else)
-            if (Tn.x < 1e-4f) {
-                nw.x = 0.0f;
-                Tn.x = T.x;
-                ta = __int_as_float(0x7f800000); // +inf: finished
+        const float2 na = make_float2(u[2 * h] ? fmaxf(-0.99f, ea) : 0.0f, u[2 * h + 1] ? fmaxf(-0.99f, eb) : 0.0f);
+        Tn[h] = __ffma2_rn(T[h], na, T[h]);
+        nw[h] = __fmul2_rn(na, T[h]); // -alpha T
+        stop = stop || Tn[h].x < 1e-4f || Tn[h].y < 1e-4f;
+    }
+    if (stop) { // a pixel that would fall below 1e-4 adds nothing (weight 0, T kept) and finishes
+#pragma unroll
+        for (int h = 0; h < NH; h++) {
+            if (Tn[h].x < 1e-4f) {
+                nw[h].x = 0.0f;
+                Tn[h].x = T[h].x;
+                thr[2 * h] = __int_as_float(0x7f800000); // +inf: finished
             }
-            if (Tn.y < 1e-4f) {
-                nw.y = 0.0f;
-                Tn.y = T.y;
-                tb = __int_as_float(0x7f800000);
+            if (Tn[h].y < 1e-4f) {
+                nw[h].y = 0.0f;
+                Tn[h].y = T[h].y;
+                thr[2 * h + 1] = __int_as_float(0x7f800000);
             }
         }
-        cr = __ffma2_rn(nr, nw, cr);
-        cg = __ffma2_rn(ng, nw, cg);
-        cb = __ffma2_rn(nb, nw, cb);
-        T = Tn;
+    }
+#pragma unroll
+    for (int h = 0; h < NH; h++) {
+        cr[h] = __ffma2_rn(nr, nw[h], cr[h]);
+        cg[h] = __ffma2_rn(ng, nw[h], cg[h]);
+        cb[h] = __ffma2_rn(nb, nw[h], cb[h]);
+        T[h] = Tn[h];
     }
 }
 
@@ -249,11 +269,9 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
                         P[i] = P[i - 1] + d;
                     }
                 }
-                if (PAIRS) {
-#pragma unroll
-                    for (int h = 0; h < NH; h++)
-                        blend_pair_fast(P[2 * h], P[2 * h + 1], make_float2(cn.x, cn.y), make_float2(cn.z, cn.w),
-                                        make_float2(c1.z, c1.w), T2[h], R2[h], G2[h], B2[h], thr[2 * h], thr[2 * h + 1]);
+                if constexpr (PAIRS) {
+                    blend_pairs_fast<NH>(P, make_float2(cn.x, cn.y), make_float2(cn.z, cn.w), make_float2(c1.z, c1.w),
+                                         T2, R2, G2, B2, thr);
                 } else {
 #pragma unroll
                     for (int i = 0; i < PPT; i++) {
