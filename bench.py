@@ -38,15 +38,16 @@ CLOCK_QUERY = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-# The rasterizer is bound by instruction issue (ncu: issue slots 78 % busy). Its roofline
+# The rasterizer is bound by instruction issue (ncu: issue slots 79 % busy). Its roofline
 # divides warp instructions issued per second by the issue peak, SMs x 4 schedulers x SM
 # clock. Warp instructions per evaluated (Gaussian, pixel) pair of the timed kernel
-# (k_raster_roofgs<fast exp, 4 pixels per thread>, pixel pairs blended with packed FP32x2
-# FMAs, two records per loop iteration), from ncu on the 1M-Gaussian 4K case:
-# sm__inst_issued.sum 472.3 M for 615.1 M evaluated pairs (per pair: FMA pipe 0.286, ALU
-# pipe 0.340, LSU 0.036, XU 0.001, the rest branches and uniform datapath). The pair count
-# of the timed frames comes from the counting variant of the same kernel.
-RASTER_WARP_INST_PER_PAIR = 472.3 / 615.1
+# (k_raster_roofgs<fast exp, 4 pixels per thread>: pixel pairs blended with packed FP32x2
+# FMAs, skip thresholds, one skip and one stop branch per thread and Gaussian, two records
+# per loop iteration), from ncu on the 1M-Gaussian 4K case: sm__inst_issued.sum 388.1 M for
+# 615.1 M evaluated pairs (per pair: FMA pipe 0.302, ALU pipe 0.188, LSU 0.033, XU 0.001,
+# the rest branches and uniform datapath). The pair count of the timed frames comes from the
+# counting variant of the same kernel.
+RASTER_WARP_INST_PER_PAIR = 388.1 / 615.1
 # Source-level FP32/ALU-pipe instruction counts of the rasterizers' inner loops (per
 # evaluated exponent, per pair inside the alpha >= 1/255 range), kept as a second,
 # model-based view: RoofGS 4 + 1 range test, blend 11; exact 10, blend 20.
