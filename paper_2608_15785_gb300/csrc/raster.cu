@@ -129,6 +129,27 @@ __device__ __forceinline__ void blend_pairs_fast(const float (&P)[2 * NH], float
     }
 }
 
+// The same blend for a thread with one pixel: the skip threshold as its state, the stop
+// below 1e-4 a branch around the common path (bit-identical to blend<true, false>).
+__device__ __forceinline__ void blend_one_fast(float P, float nr, float ng, float nb, float& T, float& cr, float& cg,
+                                               float& cb, float& thr)
+{
+    if (!(P >= thr)) return;
+    const float w = fmaf(P, 1.44269502f, 126.954323f);
+    const float na = fmaxf(-0.99f, __uint_as_float(__float_as_uint(w) << 6)); // -alpha
+    float Tn = fmaf(T, na, T);
+    float nw = na * T; // -alpha T
+    if (Tn < 1e-4f) { // once in the pixel's life: adds nothing, T kept, finished
+        nw = 0.0f;
+        Tn = T;
+        thr = __int_as_float(0x7f800000);
+    }
+    cr = fmaf(nr, nw, cr);
+    cg = fmaf(ng, nw, cg);
+    cb = fmaf(nb, nw, cb);
+    T = Tn;
+}
+
 // sums the per-thread work counters of a counting launch into the frame counters
 __device__ __forceinline__ void flush_counts(Counters* c, unsigned n_eval, unsigned n_blend)
 {
@@ -174,8 +195,10 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
     constexpr int NT = 256 / PPT; // threads per tile of 256 pixels (16 x 16, 32 x 8 or 8 x 32)
     constexpr int NH = (PPT + 1) / 2; // pixel pairs of a thread (one pixel of the last pair unused at PPT 1)
     __shared__ float4 s_c0[NT];       // C1, C2, C3, C4
-    __shared__ float4 s_c1[NT];       // C5, C6, -b, -b
-    __shared__ float4 s_cn[NT];       // -r, -r, -g, -g (pairs for the packed blend)
+    __shared__ float4 s_c1[NT];       // C5, C6, -b, -b (1 pixel per thread: C5, C6, -r, -g)
+    // -r, -r, -g, -g (pairs for the packed blend; 1 pixel per thread: -b in .x)
+    __shared__ float4 s_cn[PPT == 1 ? 1 : NT];
+    __shared__ float s_cb[PPT == 1 ? NT : 1];
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int x0 = tx * a.cam.tw, y0 = ty * a.cam.th;
     const int t = threadIdx.x;
@@ -188,6 +211,7 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
     // the packed pair blend keeps a pixel's state as its skip threshold instead: -ln 255 while it
     // blends, +inf once finished (one compare per pixel and Gaussian instead of two tests)
     constexpr bool PAIRS = FAST && !COUNT && PPT >= 2;
+    constexpr bool ONE = FAST && !COUNT && PPT == 1;
     float thr[PPT];
     // transmittance and colour of pixel i in component i & 1 of pair i / 2
     float2 T2[NH], R2[NH], G2[NH], B2[NH];
@@ -224,7 +248,8 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
     for (unsigned start = range.x; start < range.y; start += NT) {
         bool all_done = true;
 #pragma unroll
-        for (int i = 0; i < PPT; i++) all_done = all_done && (PAIRS ? thr[i] == __int_as_float(0x7f800000) : done[i]);
+        for (int i = 0; i < PPT; i++)
+            all_done = all_done && ((PAIRS || ONE) ? thr[i] == __int_as_float(0x7f800000) : done[i]);
         if (__syncthreads_count(!all_done) == 0) break;
         const unsigned j = start + t;
         if (j < range.y) {
@@ -245,17 +270,34 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
             const float fg = __half2float(__ushort_as_half((unsigned short)(rg >> 16)));
             const float fb = __half2float(__ushort_as_half((unsigned short)(bb & 0xffffu)));
             s_c0[t] = make_float4(C1, C2, C3, C4);
-            s_c1[t] = make_float4(C5, C6, -fb, -fb);
-            s_cn[t] = make_float4(-fr, -fr, -fg, -fg);
+            if constexpr (PPT == 1) {
+                s_c1[t] = make_float4(C5, C6, -fr, -fg);
+                s_cb[t] = -fb;
+            } else {
+                s_c1[t] = make_float4(C5, C6, -fb, -fb);
+                s_cn[t] = make_float4(-fr, -fr, -fg, -fg);
+            }
         }
         __syncthreads();
         const int cnt = min((unsigned)NT, range.y - start);
         if (!__all_sync(0xffffffffu, all_done)) {
-#pragma unroll 2 // two records per iteration: 4K raster 0.564 -> 0.558 ms
+#pragma unroll(PPT == 1 ? 4 : 2) // records per iteration: 4K raster 0.564 -> 0.558 ms at 4 pixels (2), 1.059 -> 0.900 ms at 1 (4)
             for (int k = 0; k < cnt; k++) {
                 const float4 c0 = s_c0[k];
                 const float4 c1 = s_c1[k];
-                const float4 cn = s_cn[k];
+                // negated colours, from the pairs' layout or the one-pixel layout
+                float nr, ng, nb;
+                float4 cn = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if constexpr (PPT == 1) {
+                    nr = c1.z;
+                    ng = c1.w;
+                    nb = s_cb[k];
+                } else {
+                    cn = s_cn[k];
+                    nr = cn.x;
+                    ng = cn.z;
+                    nb = c1.z;
+                }
                 // Eq. (16): P(x, y) = C1 x^2 + C2 xy + C3 y^2 + C4 x + C5 y + C6
                 float P[PPT];
                 P[0] = fmaf(c0.x, xx, fmaf(c0.y, xy, fmaf(c0.z, yy, fmaf(c0.w, x, fmaf(c1.x, y, c1.y)))));
@@ -272,6 +314,8 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
                 if constexpr (PAIRS) {
                     blend_pairs_fast<NH>(P, make_float2(cn.x, cn.y), make_float2(cn.z, cn.w), make_float2(c1.z, c1.w),
                                          T2, R2, G2, B2, thr);
+                } else if constexpr (ONE) {
+                    blend_one_fast(P[0], nr, ng, nb, T2[0].x, R2[0].x, G2[0].x, B2[0].x, thr[0]);
                 } else {
 #pragma unroll
                     for (int i = 0; i < PPT; i++) {
@@ -279,7 +323,7 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
                         float& Ri = (i & 1) ? R2[i >> 1].y : R2[i >> 1].x;
                         float& Gi = (i & 1) ? G2[i >> 1].y : G2[i >> 1].x;
                         float& Bi = (i & 1) ? B2[i >> 1].y : B2[i >> 1].x;
-                        blend<FAST, COUNT>(P[i], -cn.x, -cn.z, -c1.z, Ti, Ri, Gi, Bi, done[i], n_eval, n_blend);
+                        blend<FAST, COUNT>(P[i], -nr, -ng, -nb, Ti, Ri, Gi, Bi, done[i], n_eval, n_blend);
                     }
                 }
             }
