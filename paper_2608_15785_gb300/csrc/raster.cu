@@ -281,7 +281,7 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
         __syncthreads();
         const int cnt = min((unsigned)NT, range.y - start);
         if (!__all_sync(0xffffffffu, all_done)) {
-#pragma unroll(PPT == 1 ? 4 : 2) // records per iteration: 4K raster 0.564 -> 0.558 ms at 4 pixels (2), 1.059 -> 0.900 ms at 1 (4)
+#pragma unroll(PPT == 4 ? 2 : 4) // records per iteration, 4K raster: 4 pixels 0.564 -> 0.558 ms (2), 2 pixels 0.549 -> 0.540 ms and 1 pixel 1.059 -> 0.900 ms (4)
             for (int k = 0; k < cnt; k++) {
                 const float4 c0 = s_c0[k];
                 const float4 c1 = s_c1[k];
