@@ -55,7 +55,7 @@ OPS = {"roofgs": (5, 11), "exact": (10, 20)}
 STAGES = ["depth_order", "front_end", "sort_hist", "sort_passes", "ranges", "raster", "frame"]
 # DRAM bytes per entry of one tile-bit one-sweep pass (16-bit tile ids + 32-bit values): ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the tile-bit passes on the 1M-Gaussian 4K case,
-# scaled by the entries of the launch (165.6 + 118.7 MB and 165.4 + 114.1 MB for 27.03 M entries)
+# scaled by the entries of the launch (165.3 + 118.8 MB and 165.0 + 114.3 MB for 27.03 M entries)
 SORT_PASS_TRAFFIC_PER_ENTRY = 10.4
 
 
