@@ -81,6 +81,9 @@ def parse():
     p.add_argument("--no-tile-sort", action="store_true")
     p.add_argument("--no-per-pose", action="store_true",
                    help="skip the per-pose median frame times (100 frames per pose in RoofGS mode)")
+    p.add_argument("--ordered-front-end", action="store_true",
+                   help="RoofGS: the fused front end with the ordered allocation and two tile-bit passes "
+                        "instead of the row-bucketed front end")
     return p.parse_args()
 
 
@@ -154,7 +157,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # algorithmic work per stage (bytes for the HBM-bound stages, ops for raster)
 # ---------------------------------------------------------------------------
-def stage_work(mode, st, W, H):
+def row_buckets(st, ordered):
+    """Whether a RoofGS frame with an image ran the row-bucketed front end: the default with the
+    depth pre-sort, 16-bit tile ids and at most 256 x 256 tiles."""
+    return not ordered and st["b_t"] <= 16 and st["tiles_x"] <= 256 and st["tiles_y"] <= 256
+
+
+def stage_work(mode, st, W, H, rows=False):
     N, nf, nv, nd = st["n_gaussians"], st["n_front"], st["n_visible"], st["n_entries"]
     tiles = st["tiles_x"] * st["tiles_y"]
     passes = st["sort_passes"]
@@ -169,12 +178,17 @@ def stage_work(mode, st, W, H):
         # fused front end: 4 B order + 16 B mean+log o per Gaussian, 16 B FP16 geometry if inside the
         # depth/opacity range, 48 B INT8 SH + 32 B record if visible, one entry per entry
         front = 20 * N + 16 * nf + 80 * nv + entry * nd
+        if rows:
+            # row-bucketed front end, besides: 4 B of rows per slot written and read back, a 48 B row
+            # test per visible Gaussian written and read back with its 4 B order entry, 4 B per tile
+            # row and block counted, scanned (read and written) and read by the scatter
+            front += 8 * N + 100 * nv + 16 * st["tiles_y"] * ((N + 255) // 256)
         sort_pass = 2 * entry * nd  # one pass: each entry read once and written once
         if passes <= 2:
             # the front end counted the tile digits: the histogram kernel clears the first pass's
             # look-back status (1 KB per 6144-entry tile) and sums the front end's 16 copies of the
-            # [2][256] counts
-            hist = 1024 * ((nd + 6143) // 6144) + (16 + 1) * 512 * 4
+            # [passes][256] counts
+            hist = 1024 * ((nd + 6143) // 6144) + (16 + 1) * passes * 256 * 4
         else:
             hist = 4 * nd
         ranges = 0  # no ranges pass: every rasterizer block searches its tile's range in the sorted keys
@@ -221,7 +235,7 @@ def job_fps(frames_per_rank, world, ms):
 
 def mean_stats(stats, poses_used):
     keys = ["n_gaussians", "n_front", "n_visible", "n_entries", "n_pairs", "n_blends", "tiles_x", "tiles_y",
-            "sort_passes", "b_d"]
+            "sort_passes", "b_d", "b_t"]
     return {k: sum(stats[p][k] for p in poses_used) / len(poses_used) for k in keys}
 
 
@@ -288,6 +302,8 @@ def run_ours(a, rank, world, local_rank):
 
     # RoofGS ingredient flag for the rasterizer's pixels per thread (ignored in exact mode)
     rflags = {1: binding.RG_FLAG_SINGLE_PIXEL, 2: 0, 4: binding.RG_FLAG_QUAD_PIXEL}[a.ppt]
+    if a.ordered_front_end:
+        rflags |= binding.RG_FLAG_ORDERED_FRONT_END
     results = {}
     sampler = ClockSampler(bus_id) if rank == 0 else None
     modes = ["roofgs"] if a.no_exact else ["roofgs", "exact"]
@@ -381,7 +397,7 @@ def run_ours(a, rank, world, local_rank):
     if single and not a.no_serve:
         extra["serve"] = run_serve(dev, gs, a.ppt)
     if single and not a.no_tile_sort:
-        extra["tile_counting_sort"] = run_tile_sort(a, gs, cams, dev, rflags)
+        extra["tile_grouping"] = run_tile_sort(a, gs, cams, dev, rflags)
     clocks = sampler.stop() if sampler else None
     if dist is not None:
         dist.barrier()
@@ -419,10 +435,12 @@ def run_ours(a, rank, world, local_rank):
     line["config"] = cfg
     line["roofline"], line["stages"] = rooflines(r, a, props, clocks)
     # per frame: depth keys (which also clear the depth sort's look-back status), depth-sort
-    # passes, fused front end, entry histogram + tile-bit passes, rasterizer (which finds the
-    # tile ranges itself)
+    # passes, the front end (row-bucketed: count, row scan, scatter; else the fused kernel),
+    # entry histogram + tile-bit passes, rasterizer (which finds the tile ranges itself)
     gp = (int(r["stats"]["b_d"]) + 7) // 8
-    line["gpu_launches"] = r["steps"] * (1 + gp + 1 + 1 + int(r["stats"]["sort_passes"]) + 1)
+    fe = 3 if row_buckets(r["stats"], a.ordered_front_end) else 1
+    cfg["front_end"] = "row-bucketed (count, row scan, scatter)" if fe == 3 else "fused, ordered allocation"
+    line["gpu_launches"] = r["steps"] * (1 + gp + fe + 1 + int(r["stats"]["sort_passes"]) + 1)
     line["e2e"] = {"value": round(job_fps(e2e_steps, world, e2e_ms), 2), "unit": UNIT,
                    "h2d_bytes_per_step": 100,  # the rg_camera struct, passed by value per call
                    "d2h_bytes_per_step": 3 * a.width * a.height * 4,
@@ -510,8 +528,11 @@ def run_batch(a, sc3, gs3, dev):
 
 
 def run_tile_sort(a, gs, cams, dev, rflags):
-    """The per-tile counting sort (RG_FLAG_TILE_COUNTING_SORT) against the tile-bit radix passes, on
-    this workload and on the 1080p one (500k Gaussians, pose 0): frame rate and sort time."""
+    """The ways of grouping the entries by tile, on this workload and on the 1080p one (500k
+    Gaussians, pose 0): frame rate and stage times of the row-bucketed front end with its one
+    column pass (the default), the fused front end with two tile-bit radix passes
+    (RG_FLAG_ORDERED_FRONT_END) and the fused front end with the per-tile counting sort
+    (RG_FLAG_TILE_COUNTING_SORT)."""
     import torch
 
     from paper_2608_15785_gb300 import binding, synth
@@ -523,18 +544,20 @@ def run_tile_sort(a, gs, cams, dev, rflags):
     for label, scene, cs in cases:
         img = torch.empty((3, cs[0].height, cs[0].width), device=dev)
         row = {}
-        for name, fl in (("radix", 0), ("counting", binding.RG_FLAG_TILE_COUNTING_SORT)):
+        rf = rflags & ~binding.RG_FLAG_ORDERED_FRONT_END
+        for name, fl in (("row_buckets", 0), ("ordered_radix", binding.RG_FLAG_ORDERED_FRONT_END),
+                         ("counting", binding.RG_FLAG_TILE_COUNTING_SORT)):
             for c in cs:
-                scene.render(c, mode="roofgs", flags=rflags | fl, out=img, stats=True)
+                scene.render(c, mode="roofgs", flags=rf | fl, out=img, stats=True)
             steps = 60
             for k in range(5):
-                scene.render(cs[k % len(cs)], mode="roofgs", flags=rflags | fl, out=img)
+                scene.render(cs[k % len(cs)], mode="roofgs", flags=rf | fl, out=img)
             torch.cuda.synchronize(dev)
             scene.stage_times()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for k in range(steps):
-                scene.render(cs[k % len(cs)], mode="roofgs", flags=rflags | fl | binding.RG_FLAG_STAGE_EVENTS, out=img)
+                scene.render(cs[k % len(cs)], mode="roofgs", flags=rf | fl | binding.RG_FLAG_STAGE_EVENTS, out=img)
             e1.record()
             torch.cuda.synchronize(dev)
             ms, frames = scene.stage_times()
@@ -542,7 +565,9 @@ def run_tile_sort(a, gs, cams, dev, rflags):
             row[name] = {"fps": round(steps / (e0.elapsed_time(e1) * 1e-3), 1),
                          "sort_ms": round(per[2] + per[3], 4), "raster_ms": round(per[5], 4),
                          "front_end_ms": round(per[1], 4)}
-        row["sort_speedup"] = round(row["radix"]["sort_ms"] / max(row["counting"]["sort_ms"], 1e-9), 3)
+        row["counting_sort_speedup_vs_radix"] = round(row["ordered_radix"]["sort_ms"] /
+                                                      max(row["counting"]["sort_ms"], 1e-9), 3)
+        row["row_buckets_frame_speedup"] = round(row["row_buckets"]["fps"] / max(row["ordered_radix"]["fps"], 1e-9), 3)
         out[label] = row
         scene.check()
     g2.close()
@@ -733,7 +758,8 @@ def rooflines(r, a, props, clocks):
     hbm, src = measured_peaks()
     W, H = a.width, a.height
     st = r["stats"]
-    work = stage_work("roofgs", st, W, H)
+    rows = row_buckets(st, a.ordered_front_end)
+    work = stage_work("roofgs", st, W, H, rows)
     sms = props.multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     issue_peak = sms * 4 * mhz * 1e6 / 1e9  # warp instructions per second (G/s): 4 schedulers per SM
@@ -751,7 +777,7 @@ def rooflines(r, a, props, clocks):
         "sort_hist": hbm_stage(work["hist"], ms["sort_hist"]),
         "sort_pass": hbm_stage(work["sort_pass"], ms["sort_passes"] / passes),
         "ranges": hbm_stage(work["ranges"], ms["ranges"]) if work["ranges"] else None,
-        "raster": {"bound": "issue", "achieved": RASTER_WARP_INST_PER_PAIR * st["n_pairs"] / (ms["raster"] * 1e-3) / 1e9,
+        "raster": {"bound": "alu", "achieved": RASTER_WARP_INST_PER_PAIR * st["n_pairs"] / (ms["raster"] * 1e-3) / 1e9,
                    "peak": issue_peak, "unit": "G warp instructions/s", "ms": ms["raster"],
                    "warp_instructions": RASTER_WARP_INST_PER_PAIR * st["n_pairs"],
                    "fp32_pipe_model": {"achieved": round(work["raster_ops"] / (ms["raster"] * 1e-3) / 1e9, 1),
@@ -759,14 +785,16 @@ def rooflines(r, a, props, clocks):
                                        "frac": round(work["raster_ops"] / (ms["raster"] * 1e-3) / 1e9 / alu_peak, 4)}},
     }
     stages["sort_pass"]["launches_per_frame"] = work["passes"]
+    stages["depth_order"]["kernels"] = 1 + (st["b_d"] + 7) // 8
+    stages["front_end"]["kernels"] = 3 if rows else 1
     stages = {k: v for k, v in stages.items() if v is not None}
     for v in stages.values():
         v["frac"] = round(v["achieved"] / v["peak"], 4)
         v["achieved"] = round(v["achieved"], 1)
         v["peak"] = round(v["peak"], 1)
         v["ms"] = round(v["ms"], 4)
-    # dominant kernel: largest device time per frame (launches x duration)
-    share = {k: v["ms"] * v.get("launches_per_frame", 1) for k, v in stages.items()}
+    # dominant kernel: largest device time per frame (launches x duration) of the one-kernel stages
+    share = {k: v["ms"] * v.get("launches_per_frame", 1) for k, v in stages.items() if v.get("kernels", 1) == 1}
     dom = max(share, key=share.get)
     d = stages[dom]
     traffic = None
@@ -774,12 +802,13 @@ def rooflines(r, a, props, clocks):
         traffic = round(SORT_PASS_TRAFFIC_PER_ENTRY * st["n_entries"])
     names = {"sort_pass": "k_onesweep<uint16 tile id> (one tile-bit pass)",
              "raster": "k_raster_roofgs<fast exp, %d pixels per thread>" % a.ppt,
-             "front_end": "k_frontend_fused", "depth_order": "k_depth_keys + per-Gaussian sort",
+             "front_end": "k_frontend_count + k_row_scan + k_frontend_scatter" if rows else "k_frontend_fused",
+             "depth_order": "k_depth_keys + per-Gaussian sort",
              "sort_hist": "k_sort_hist<uint32>", "ranges": "k_ranges<uint32>"}
     roof = {"kernel": names[dom], "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
             "unit": d["unit"], "frac": d["frac"], "traffic": traffic,
             "peak_source": ("of measured HBM copy bandwidth" if src == "measured" else "of fallback HBM bandwidth")
-            if d["bound"] == "hbm" else "%d SMs x 4 schedulers x %.0f MHz median SM clock under load" % (sms, mhz)}
+            if d["bound"] == "hbm" else "issue: %d SMs x 4 schedulers x %.0f MHz median SM clock under load" % (sms, mhz)}
     return roof, stages
 
 

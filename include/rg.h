@@ -131,6 +131,17 @@ typedef struct {
  * tiles (one 4-byte offset per tile in a block's shared memory); RG_ERR_UNSUPPORTED
  * otherwise. Not for rg_render_batch's fused path (its plans take the lanes). */
 #define RG_FLAG_TILE_COUNTING_SORT (1u << 13)
+/* RoofGS: the fused front end with the ordered allocation (one contiguous run of entries
+ * per block, 16-bit tile ids) and the two 8-bit radix passes over the tile id, instead of the
+ * default row-bucketed front end. The row-bucketed front end (frames with an image, the
+ * depth pre-sort and at most 256 x 256 tiles) runs a count kernel (the fused front end's
+ * work without the emission), a per-tile-row scan of its block counts and a scatter kernel
+ * that writes each Gaussian's tile-row runs straight into their tile row's part of the
+ * entry array under the column-major key tx << 8 | ty; one 8-bit pass over the column then
+ * groups the entries by tile. Both give the same entries per tile in the same order, hence
+ * the same images; rg_inspect returns the entries in tile-id order either way. Other frames
+ * always take the fused front end. */
+#define RG_FLAG_ORDERED_FRONT_END (1u << 14)
 /* test hook for the failure path: the first radix pass of the entry sort never processes its
  * first tile, so the next tile's bounded look-back wait runs out (about a second); the frame
  * is invalid, kernels finish with in-bounds writes only, and the next rg_scene_check (or this

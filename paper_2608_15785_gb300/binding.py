@@ -33,6 +33,7 @@ RG_FLAG_TEST_STALL_SORT = 1 << 10
 RG_FLAG_BATCH_FUSED = 1 << 11
 RG_FLAG_BATCH_LANES = 1 << 12
 RG_FLAG_TILE_COUNTING_SORT = 1 << 13
+RG_FLAG_ORDERED_FRONT_END = 1 << 14
 RG_INSPECT_KEYS = 1
 RG_INSPECT_VALUES = 2
 RG_INSPECT_RANGES = 3

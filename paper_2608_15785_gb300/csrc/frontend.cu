@@ -15,6 +15,12 @@
 //    array go to global memory, besides the digit counts of the entry sort
 //    (each tile row is a run of consecutive tile ids; counted per block in
 //    shared memory, added to one of a few global copies).
+//  * k_frontend_count -> k_row_scan -> k_frontend_scatter: the row-bucketed front
+//    end (the renderer's default where it applies): the fused kernel's work without
+//    the allocation and emission, a per-tile-row prefix of the block counts, and a
+//    scatter of each Gaussian's tile-row runs into their tile row's part of the entry
+//    array under the column-major key tx << 8 | ty, so one 8-bit pass over the tile
+//    column is left to the sort.
 //  * k_depth_keys: quantized depth and index of every Gaussian, the input of
 //    the per-Gaussian depth sort, and the digit counts of that sort.
 //  * k_exact_*: the plain 3DGS front end (preprocess -> scan -> duplicate,
@@ -92,12 +98,13 @@ __device__ __forceinline__ unsigned warp_inclusive_scan(unsigned x, int lane)
     return x;
 }
 
-// Full occupancy (64 warps per SM, 32 registers): the kernel is latency-bound on
-// its depth-ordered gathers and shuffles, and 8 blocks of 256 threads per SM
-// measured 0.41 ms at 4K against 0.52 ms at 4 blocks per SM (61 registers)
 // One block of the fused front end: virtual block vb (blocks of a view are numbered in
 // the order they claimed work, so every predecessor of the ordered allocation is
 // running or done) of the view described by a.
+// ROWS: the count kernel of the row-bucketed front end instead (launch_frontend_rows):
+// the same per-Gaussian work and entry counts, but no allocation and no emission; the
+// block stores each slot's row test, its entries per tile row and the column digits.
+template <bool ROWS>
 __device__ __forceinline__ void frontend_block(const FrontendArgs& a, const unsigned vb)
 {
     __shared__ unsigned s_wsum[FE_WARPS];
@@ -108,7 +115,8 @@ __device__ __forceinline__ void frontend_block(const FrontendArgs& a, const unsi
     __shared__ unsigned long long s_base;
     // digit counts of the block's entries for the entry sort (8-bit digits of the
     // tile id): pass 0 as a difference array over the digits (tile rows are runs of
-    // consecutive tiles), pass 1 as plain counts
+    // consecutive tiles), pass 1 as plain counts. ROWS: s_d0 over the tile columns,
+    // s_h1 the entries of each tile row.
     __shared__ unsigned s_d0[RADIX_FE + 1], s_h1[RADIX_FE];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -136,6 +144,14 @@ __device__ __forceinline__ void frontend_block(const FrontendArgs& a, const unsi
             if (project_bin(a.cam, ga.x, ga.y, ga.z, pz, h_lo(gb.x), h_hi(gb.x), h_lo(gb.y), h_hi(gb.y), h_lo(gb.z),
                             h_hi(gb.z), h_lo(gb.w), true, ga.w, b)) {
                 rt = row_test(b);
+                if constexpr (ROWS) { // the row test for the scatter kernel, stored before the SH work
+                    s_rt[tid] = shared_row_test(rt);
+                    if (rt.ty1 >= rt.ty0) { // three coalesced planes
+                        a.row_rt[slot] = make_float4(rt.u, rt.v, rt.tt, rt.isc);
+                        a.row_rt[a.n + slot] = make_float4(rt.ys, rt.cc, rt.kk, rt.xl);
+                        a.row_rt[2 * a.n + slot] = make_float4(rt.xh, rt.yl, rt.yh, __int_as_float(rt.ty0));
+                    }
+                }
                 qd = quantize_depth(pz, a.cam.zn, a.lay);
                 // conic in the paper's (a, b, c) of Eq. (10): b multiplies dx*dy
                 const float inv = 1.0f / b.det;
@@ -178,9 +194,10 @@ __device__ __forceinline__ void frontend_block(const FrontendArgs& a, const unsi
             }
         }
     }
-    s_rt[tid] = shared_row_test(rt);
+    if constexpr (!ROWS) s_rt[tid] = shared_row_test(rt); // (ROWS: stored above; read only for rows > 0)
     s_q[tid] = qd;
     s_id[tid] = (unsigned)i;
+    if (ROWS && slot < a.n) a.row_n[slot] = rt.ty1 >= rt.ty0 ? (unsigned)(rt.ty1 - rt.ty0 + 1) : 0u;
     __syncwarp();
 
     // Entries per Gaussian. The warp's Gaussians have rows_l tile rows each; the
@@ -208,102 +225,116 @@ __device__ __forceinline__ void frontend_block(const FrontendArgs& a, const unsi
             w = (unsigned)(txb - txa + 1);
         if (w) {
             atomicAdd(&s_cnt[warp * 32 + owner], w);
-            if (a.hist_passes)
+            if (ROWS) { // tile row ty (the scatter's digit) and columns txa .. txb (the sort's)
+                atomicAdd(&s_h1[ty], w);
+                count_tile_digits(s_d0, s_h1, 1, (unsigned)txa, w);
+            } else if (a.hist_passes) {
                 count_tile_digits(s_d0, s_h1, a.hist_passes, (unsigned)ty * (unsigned)a.lay.tiles_x + (unsigned)txa, w);
+            }
         }
     }
     __syncwarp();
     const unsigned cnt = s_cnt[tid];
-
-    // block-level prefix sum of the entry counts
-    const unsigned x = warp_inclusive_scan(cnt, lane);
-    if (lane == 31) s_wsum[warp] = x;
-    const int nfront = __syncthreads_count(front);
-    const int nvis = __syncthreads_count(cnt > 0);
-    if (warp == 0) {
-        unsigned ws = lane < FE_WARPS ? s_wsum[lane] : 0u;
-        ws = warp_inclusive_scan(ws, lane);
-        if (lane < FE_WARPS) s_wsum[lane] = ws; // inclusive warp totals
-    }
-    __syncthreads();
-    const unsigned block_total = s_wsum[FE_WARPS - 1];
-
-    // one device-wide allocation per block, ordered by block
-    if (warp == 0) {
-        const unsigned long long base =
-            lookback_exclusive(a.status, vb, (unsigned long long)block_total, a.ctr, a.sticky, ERR_FE_LOOKBACK);
-        if (lane == 0) {
-            s_base = base;
+    if constexpr (ROWS) {
+        const int nfront = __syncthreads_count(front);
+        const int nvis = __syncthreads_count(cnt > 0); // the block's counts are complete after it
+        const unsigned nbl = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
+        if (tid < a.rows) a.row_cnt[(size_t)tid * nbl + vb] = s_h1[tid];
+        if (tid == 0) {
             if (nvis) atomicAdd(&a.ctr->n_visible, (unsigned)nvis);
             if (nfront) atomicAdd(&a.ctr->n_front, (unsigned)nfront);
-            const unsigned nblocks = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
-            if (vb == nblocks - 1) {
-                const unsigned long long total = base + block_total;
-                a.ctr->n_entries_total = total;
-                a.ctr->n_entries = (unsigned)(total < (unsigned long long)a.cap ? total : (unsigned long long)a.cap);
-            }
-            if (base + block_total > (unsigned long long)a.cap) {
-                atomicOr(&a.ctr->overflow, 1u);
-                atomicOr(&a.sticky->overflow, 1u);
-            }
         }
-    }
-    __syncthreads();
-    const unsigned long long base = s_base;
+    } else {
+        // block-level prefix sum of the entry counts
+        const unsigned x = warp_inclusive_scan(cnt, lane);
+        if (lane == 31) s_wsum[warp] = x;
+        const int nfront = __syncthreads_count(front);
+        const int nvis = __syncthreads_count(cnt > 0);
+        if (warp == 0) {
+            unsigned ws = lane < FE_WARPS ? s_wsum[lane] : 0u;
+            ws = warp_inclusive_scan(ws, lane);
+            if (lane < FE_WARPS) s_wsum[lane] = ws; // inclusive warp totals
+        }
+        __syncthreads();
+        const unsigned block_total = s_wsum[FE_WARPS - 1];
 
-    // Emission: the warp's entries are contiguous and in (Gaussian, row, tile)
-    // order, so the warp walks its rows again 32 at a time, scans the row
-    // widths, and writes 32 consecutive entries per store instruction (lane e
-    // finds the row of its entry with a 5-step search over the scan and takes
-    // the row's first tile, depth and Gaussian from that lane).
-    const int b_d = a.lay.b_d;
-    const unsigned tiles_x = (unsigned)a.lay.tiles_x;
-    unsigned long long out = base + (warp ? s_wsum[warp - 1] : 0u); // the warp's first entry
-    for (unsigned r0 = 0; r0 < wrows; r0 += 32) {
-        const unsigned k = r0 + (unsigned)lane;
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-            if (__shfl_sync(0xffffffffu, rincl, owner + step - 1) <= k) owner += step;
-        const unsigned rl = k - __shfl_sync(0xffffffffu, rexcl, owner);
-        unsigned w = 0, tb = 0, q = 0, id = 0;
-        if (k < wrows) {
-            const RowTestS& G = s_rt[warp * 32 + owner];
-            const int ty = G.ty0 + (int)rl;
-            int txa, txb;
-            if (row_range(G, ty, a.cam.tw_log2, a.cam.th, txa, txb)) {
-                w = (unsigned)(txb - txa + 1);
-                tb = (unsigned)ty * tiles_x + (unsigned)txa; // tile of the row's first entry
+        // one device-wide allocation per block, ordered by block
+        if (warp == 0) {
+            const unsigned long long base =
+                lookback_exclusive(a.status, vb, (unsigned long long)block_total, a.ctr, a.sticky, ERR_FE_LOOKBACK);
+            if (lane == 0) {
+                s_base = base;
+                if (nvis) atomicAdd(&a.ctr->n_visible, (unsigned)nvis);
+                if (nfront) atomicAdd(&a.ctr->n_front, (unsigned)nfront);
+                const unsigned nblocks = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
+                if (vb == nblocks - 1) {
+                    const unsigned long long total = base + block_total;
+                    a.ctr->n_entries_total = total;
+                    a.ctr->n_entries = (unsigned)(total < (unsigned long long)a.cap ? total : (unsigned long long)a.cap);
+                }
+                if (base + block_total > (unsigned long long)a.cap) {
+                    atomicOr(&a.ctr->overflow, 1u);
+                    atomicOr(&a.sticky->overflow, 1u);
+                }
             }
-            q = s_q[warp * 32 + owner];
-            id = s_id[warp * 32 + owner];
         }
-        const unsigned incl = warp_inclusive_scan(w, lane);
-        const unsigned chunk = __shfl_sync(0xffffffffu, incl, 31);
-        tb -= incl - w; // entry e of the chunk, if in this row, has tile tb + e (mod 2^32)
-        // entries at or past the capacity are counted but not written
-        const bool fits = out < (unsigned long long)a.cap;
-        const unsigned room = fits ? (unsigned)((unsigned long long)a.cap - out) : 0u;
-        const unsigned long long o = fits ? out : 0ull;
-        unsigned* const kp = a.keys + o;
-        unsigned short* const kp16 = a.keys16 ? a.keys16 + o : nullptr;
-        unsigned* const vp = a.vals + o;
-        for (unsigned e0 = 0; e0 < chunk; e0 += 32) {
-            const unsigned e = e0 + (unsigned)lane;
-            int pos = 0; // row (lane) of entry e
-#pragma unroll
+        __syncthreads();
+        const unsigned long long base = s_base;
+
+        // Emission: the warp's entries are contiguous and in (Gaussian, row, tile)
+        // order, so the warp walks its rows again 32 at a time, scans the row
+        // widths, and writes 32 consecutive entries per store instruction (lane e
+        // finds the row of its entry with a 5-step search over the scan and takes
+        // the row's first tile, depth and Gaussian from that lane).
+        const int b_d = a.lay.b_d;
+        const unsigned tiles_x = (unsigned)a.lay.tiles_x;
+        unsigned long long out = base + (warp ? s_wsum[warp - 1] : 0u); // the warp's first entry
+        for (unsigned r0 = 0; r0 < wrows; r0 += 32) {
+            const unsigned k = r0 + (unsigned)lane;
+            int owner = 0;
+    #pragma unroll
             for (int step = 16; step > 0; step >>= 1)
-                if (__shfl_sync(0xffffffffu, incl, pos + step - 1) <= e) pos += step;
-            const unsigned tile = __shfl_sync(0xffffffffu, tb, pos) + e;
-            const unsigned qe = __shfl_sync(0xffffffffu, q, pos);
-            const unsigned ide = __shfl_sync(0xffffffffu, id, pos);
-            if (e < chunk && e < room) {
-                if (a.keys16) kp16[e] = (unsigned short)tile;
-                else kp[e] = (b_d >= 32) ? qe : ((tile << b_d) | qe);
-                vp[e] = ide;
+                if (__shfl_sync(0xffffffffu, rincl, owner + step - 1) <= k) owner += step;
+            const unsigned rl = k - __shfl_sync(0xffffffffu, rexcl, owner);
+            unsigned w = 0, tb = 0, q = 0, id = 0;
+            if (k < wrows) {
+                const RowTestS& G = s_rt[warp * 32 + owner];
+                const int ty = G.ty0 + (int)rl;
+                int txa, txb;
+                if (row_range(G, ty, a.cam.tw_log2, a.cam.th, txa, txb)) {
+                    w = (unsigned)(txb - txa + 1);
+                    tb = (unsigned)ty * tiles_x + (unsigned)txa; // tile of the row's first entry
+                }
+                q = s_q[warp * 32 + owner];
+                id = s_id[warp * 32 + owner];
             }
+            const unsigned incl = warp_inclusive_scan(w, lane);
+            const unsigned chunk = __shfl_sync(0xffffffffu, incl, 31);
+            tb -= incl - w; // entry e of the chunk, if in this row, has tile tb + e (mod 2^32)
+            // entries at or past the capacity are counted but not written
+            const bool fits = out < (unsigned long long)a.cap;
+            const unsigned room = fits ? (unsigned)((unsigned long long)a.cap - out) : 0u;
+            const unsigned long long o = fits ? out : 0ull;
+            unsigned* const kp = a.keys + o;
+            unsigned short* const kp16 = a.keys16 ? a.keys16 + o : nullptr;
+            unsigned* const vp = a.vals + o;
+            for (unsigned e0 = 0; e0 < chunk; e0 += 32) {
+                const unsigned e = e0 + (unsigned)lane;
+                int pos = 0; // row (lane) of entry e
+    #pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (__shfl_sync(0xffffffffu, incl, pos + step - 1) <= e) pos += step;
+                const unsigned tile = __shfl_sync(0xffffffffu, tb, pos) + e;
+                const unsigned qe = __shfl_sync(0xffffffffu, q, pos);
+                const unsigned ide = __shfl_sync(0xffffffffu, id, pos);
+                if (e < chunk && e < room) {
+                    if (a.keys16) kp16[e] = (unsigned short)tile;
+                    else kp[e] = (b_d >= 32) ? qe : ((tile << b_d) | qe);
+                    vp[e] = ide;
+                }
+            }
+            out += chunk;
         }
-        out += chunk;
     }
 
     // The block's digit counts (complete since the barriers after the count
@@ -332,13 +363,16 @@ __device__ __forceinline__ void frontend_block(const FrontendArgs& a, const unsi
     }
 }
 
+// Full occupancy (64 warps per SM, 32 registers): the kernel is latency-bound on
+// its depth-ordered gathers and shuffles, and 8 blocks of 256 threads per SM
+// measured 0.41 ms at 4K against 0.52 ms at 4 blocks per SM (61 registers)
 __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS) k_frontend_fused(FrontendArgs a)
 {
     __shared__ unsigned s_vb;
     grid_dependency_wait();
     if (threadIdx.x == 0) s_vb = atomicAdd(&a.ctr->fe_block_ctr, 1u);
     __syncthreads();
-    frontend_block(a, s_vb);
+    frontend_block<false>(a, s_vb);
 }
 
 // Every view of a batch in one grid: a block claims the next of all views' blocks
@@ -354,7 +388,7 @@ __global__ void __launch_bounds__(FE_THREADS, 2048 / FE_THREADS)
     const unsigned g = s_g;
     int v = 0;
     while (v + 1 < m.n_views && m.block_prefix[v + 1] <= g) v++;
-    frontend_block(m.views[v], g - m.block_prefix[v]);
+    frontend_block<false>(m.views[v], g - m.block_prefix[v]);
 }
 
 void launch_frontend_views(const FrontendViews& m, cudaStream_t s)
@@ -412,6 +446,233 @@ void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s)
     if (a.n <= 0) return;
     const unsigned blocks = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
     launch_dependent(k_frontend_fused, dim3(blocks), dim3(FE_THREADS), 0, s, a);
+}
+
+// ---------------------------------------------------------------------------
+// Row-bucketed front end (RoofGS, at most 256 x 256 tiles)
+// ---------------------------------------------------------------------------
+// The fused kernel hands each block one contiguous run of entries (the ordered
+// allocation) and leaves two 8-bit passes over the tile id to the sort. Here the entries
+// carry the column-major key tx << 8 | ty and the front end itself places them by tile
+// row: one tile row of one Gaussian is a run of entries that share ty, so ranking a
+// block's entries by tile row takes one count per run, not one per entry.
+//  * k_frontend_count: the fused kernel's per-Gaussian work and entry counts (records,
+//    row tests, entries per tile row per block, the column digits); no emission;
+//  * k_row_scan: per tile row, the exclusive prefix of the block counts over the blocks
+//    and the row's total;
+//  * k_frontend_scatter: the block's runs in (slot, row) order, 256 at a time; a run's
+//    first slot = its tile row's start + the earlier blocks' entries of that row + the
+//    block's earlier runs of that row; the entries go out 32 per store as in the fused
+//    kernel.
+// The entries come out grouped by tile row, in slot (depth) order within a row, so one
+// stable 8-bit pass over the column leaves each tile's entries contiguous and in the order
+// of the 32-bit key of Sec. IV-A.2.
+constexpr unsigned ROW_PREFIX_SAT = 0x7fffffffu; // above any entry capacity (below 2^30)
+
+// resident count kernels per SM: 6 (40 registers, 24 bytes of spill) measured faster than the fused
+// kernel's 8 (32 registers, 88 bytes of spill): 4K front end 0.671 -> 0.630 ms
+#ifndef RG_FEC_MIN_BLOCKS
+#define RG_FEC_MIN_BLOCKS 6
+#endif
+
+__global__ void __launch_bounds__(FE_THREADS, RG_FEC_MIN_BLOCKS) k_frontend_count(FrontendArgs a)
+{
+    grid_dependency_wait();
+    frontend_block<true>(a, blockIdx.x);
+}
+
+// one block of 1024 threads per tile row: the exclusive prefix of the row's block counts
+// over the blocks (in place) and the row's total
+__global__ void __launch_bounds__(1024) k_row_scan(FrontendArgs a)
+{
+    __shared__ unsigned long long s_w[32];
+    grid_dependency_wait();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned nbl = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
+    unsigned* const col = a.row_cnt + (size_t)blockIdx.x * nbl;
+    const unsigned per = (nbl + 1023u) / 1024u;
+    const unsigned b0 = (unsigned)tid * per;
+    unsigned long long sum = 0;
+#pragma unroll 4
+    for (unsigned k = 0; k < per; k++)
+        if (b0 + k < nbl) sum += col[b0 + k];
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long v = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        s_w[lane] = v;
+    }
+    __syncthreads();
+    unsigned long long run = x - sum + (warp ? s_w[warp - 1] : 0ull);
+#pragma unroll 4
+    for (unsigned k = 0; k < per; k++) {
+        const unsigned b = b0 + k;
+        if (b >= nbl) break;
+        const unsigned c = col[b];
+        col[b] = run < ROW_PREFIX_SAT ? (unsigned)run : ROW_PREFIX_SAT;
+        run += c;
+    }
+    if (tid == 1023) a.row_tot[blockIdx.x] = s_w[31];
+}
+
+// inclusive scan of one value per thread over a block of FE_THREADS threads (every thread
+// calls it); s_w holds FE_WARPS words; total = the block's sum
+template <typename T>
+__device__ __forceinline__ T fe_block_inclusive_scan(T v, T* s_w, T& total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    T before = 0, all = 0;
+#pragma unroll
+    for (int q = 0; q < FE_WARPS; q++) {
+        const T t = s_w[q];
+        if (q < warp) before += t;
+        all += t;
+    }
+    total = all;
+    __syncthreads(); // s_w may be written again after the call
+    return x + before;
+}
+
+__global__ void __launch_bounds__(FE_THREADS, 6) k_frontend_scatter(FrontendArgs a)
+{
+    __shared__ RowTestS s_rt[FE_THREADS];         // row test of each slot's Gaussian
+    __shared__ unsigned s_incl[FE_THREADS];       // inclusive prefix of the slots' tile rows
+    __shared__ unsigned s_id[FE_THREADS];         // Gaussian of each slot
+    __shared__ unsigned s_run[RADIX_FE];          // next entry slot of each tile row
+    __shared__ unsigned s_wt[FE_WARPS][RADIX_FE]; // this round: each warp's entries per tile row
+    __shared__ unsigned s_wp[FE_WARPS][RADIX_FE]; // this round: each warp's first slot per tile row
+    __shared__ unsigned s_w[FE_WARPS][32];        // widths of a warp's runs
+    __shared__ unsigned s_sc[FE_WARPS];
+    __shared__ unsigned long long s_sc64[FE_WARPS];
+    grid_dependency_wait();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned vb = blockIdx.x;
+    const unsigned nbl = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
+    const unsigned long long cap = (unsigned long long)a.cap;
+    const long long slot = (long long)vb * FE_THREADS + tid;
+    unsigned nr = 0;
+    if (slot < a.n) {
+        nr = a.row_n[slot];
+        if (nr) {
+            const float4 r0 = a.row_rt[slot], r1 = a.row_rt[a.n + slot], r2 = a.row_rt[2 * a.n + slot];
+            s_rt[tid] = RowTestS{r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, __float_as_int(r2.w)};
+            s_id[tid] = a.order ? a.order[slot] : (unsigned)slot;
+        }
+    }
+    for (int j = tid; j < FE_WARPS * RADIX_FE; j += FE_THREADS) (&s_wt[0][0])[j] = 0u;
+    unsigned R; // the block's tile rows (runs, some possibly empty)
+    s_incl[tid] = fe_block_inclusive_scan(nr, s_sc, R);
+    // first slot of each tile row's entries in this block: the earlier tile rows' entries
+    // (clamped at the capacity: slots past it are not written), then the earlier blocks'
+    // entries of the row; below 2^30 + 2^31 and raised by at most 2^16 per block
+    const unsigned long long tot = tid < a.rows ? a.row_tot[tid] : 0ull;
+    unsigned long long all;
+    const unsigned long long tincl = fe_block_inclusive_scan(tot, s_sc64, all);
+    if (tid < a.rows) {
+        const unsigned long long start = tincl - tot;
+        s_run[tid] = (unsigned)(start < cap ? start : cap) + a.row_cnt[(size_t)tid * nbl + vb];
+    }
+    if (vb == 0 && tid == 0) {
+        a.ctr->n_entries_total = all;
+        a.ctr->n_entries = (unsigned)(all < cap ? all : cap);
+        if (all > cap) {
+            atomicOr(&a.ctr->overflow, 1u);
+            atomicOr(&a.sticky->overflow, 1u);
+        }
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (unsigned r0 = 0; r0 < R; r0 += FE_THREADS) {
+        // run k of the block: slot s (the first with s_incl[s] > k), tile row ty
+        const unsigned k = r0 + (unsigned)tid;
+        unsigned w = 0, d = 0, ta = 0, id = 0;
+        if (k < R) {
+            int s = 0;
+#pragma unroll
+            for (int step = FE_THREADS / 2; step > 0; step >>= 1)
+                if (s_incl[s + step - 1] <= k) s += step;
+            const RowTestS& G = s_rt[s];
+            const int ty = G.ty0 + (int)(k - (s ? s_incl[s - 1] : 0u));
+            int txa, txb;
+            if (row_range(G, ty, a.cam.tw_log2, a.cam.th, txa, txb)) {
+                w = (unsigned)(txb - txa + 1);
+                d = (unsigned)ty;
+                ta = (unsigned)txa;
+                id = s_id[s];
+            }
+        }
+        // entries before the run among the warp's runs of the same tile row (lane order)
+        const unsigned peers = __match_any_sync(0xffffffffu, w ? d : 0x100u + (unsigned)lane);
+        s_w[warp][lane] = w;
+        __syncwarp();
+        unsigned pre = 0;
+        if (w)
+            for (unsigned m = peers & lt; m; m &= m - 1u) pre += s_w[warp][__ffs(m) - 1];
+        if (w && (peers >> lane) == 1u) s_wt[warp][d] = pre + w; // the group's last lane: its total
+        __syncthreads();
+        // per tile row: each warp's first slot this round, in warp order
+        if (tid < a.rows) {
+            unsigned run = s_run[tid];
+#pragma unroll
+            for (int q = 0; q < FE_WARPS; q++) {
+                const unsigned c = s_wt[q][tid];
+                s_wp[q][tid] = run;
+                s_wt[q][tid] = 0u;
+                run += c;
+            }
+            s_run[tid] = run;
+        }
+        __syncthreads();
+        // the warp's entries, 32 per store: entry e of the warp's runs, in run r, goes to
+        // slot dbase(r) + e with key kbase(r) + (e << 8) (low 16 bits)
+        const unsigned incl = warp_inclusive_scan(w, lane);
+        const unsigned chunk = __shfl_sync(0xffffffffu, incl, 31);
+        const unsigned excl = incl - w;
+        const unsigned dbase = (w ? s_wp[warp][d] + pre : 0u) - excl;
+        const unsigned kbase = ((ta - excl) << 8) + d;
+        for (unsigned e0 = 0; e0 < chunk; e0 += 32) {
+            const unsigned e = e0 + (unsigned)lane;
+            int pos = 0; // run (lane) of entry e
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(0xffffffffu, incl, pos + step - 1) <= e) pos += step;
+            const unsigned dst = __shfl_sync(0xffffffffu, dbase, pos) + e;
+            const unsigned key = __shfl_sync(0xffffffffu, kbase, pos) + (e << 8);
+            const unsigned ide = __shfl_sync(0xffffffffu, id, pos);
+            if (e < chunk && dst < cap) {
+                a.keys16[dst] = (unsigned short)key;
+                a.vals[dst] = ide;
+            }
+        }
+    }
+}
+
+void launch_frontend_rows(const FrontendArgs& a, cudaStream_t s)
+{
+    if (a.n <= 0 || a.rows <= 0) return;
+    const unsigned blocks = (unsigned)((a.n + FE_THREADS - 1) / FE_THREADS);
+    launch_dependent(k_frontend_count, dim3(blocks), dim3(FE_THREADS), 0, s, a);
+    launch_dependent(k_row_scan, dim3(a.rows), dim3(1024), 0, s, a);
+    launch_dependent(k_frontend_scatter, dim3(blocks), dim3(FE_THREADS), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------

@@ -235,8 +235,11 @@ __device__ __forceinline__ void raster_tile(const RasterArgs& a, const int tile)
         const int warp = t >> 5;
         if (warp < 2) {
             const unsigned n = a.ctr->n_entries;
-            const unsigned b = a.skeys16 ? warp_lower_bound(a.skeys16, n, 0, (unsigned)(tile + warp))
-                                         : warp_lower_bound(a.skeys, n, a.tile_shift, (unsigned)(tile + warp));
+            // the tile's key: its id, or tx << 8 | ty for column-major keys (ty + 1 <= 256
+            // carries into the next column, whose first entry also ends this tile)
+            const unsigned key = a.key_cols ? (((unsigned)tx << 8) | (unsigned)ty) : (unsigned)tile;
+            const unsigned b = a.skeys16 ? warp_lower_bound(a.skeys16, n, 0, key + (unsigned)warp)
+                                         : warp_lower_bound(a.skeys, n, a.tile_shift, key + (unsigned)warp);
             if ((t & 31) == 0) s_bound[warp] = b;
         }
         __syncthreads();

@@ -114,6 +114,29 @@ rg_status make_layout(const rg_camera* c, FrameLayout& f, int tw, int th)
 // one device word set from the stream (test hook of RG_FLAG_TEST_STALL_SORT)
 __global__ void k_set_word(unsigned* p, unsigned v) { *p = v; }
 
+// the row-bucketed front end's buffer for n slots: rows per slot (4 B, padded to 16 B), the
+// row tests (3 x 16 B per slot), the per-block counts of up to 256 tile rows, the row totals
+size_t row_buffer_bytes(int64_t n)
+{
+    const size_t nb = (size_t)((n + frontend_block_threads() - 1) / frontend_block_threads());
+    return ((size_t)n * 4 + 15) / 16 * 16 + (size_t)n * 48 + (size_t)256 * nb * 4 + 256 * 8;
+}
+
+// points the row-bucketed front end's arrays of a into w.rowbuf (n = a.n slots)
+void row_buffer_views(Workspace& w, FrontendArgs& a)
+{
+    const size_t n = (size_t)a.n;
+    unsigned char* p = w.rowbuf.as<unsigned char>();
+    a.row_n = reinterpret_cast<unsigned*>(p);
+    p += (n * 4 + 15) / 16 * 16;
+    a.row_rt = reinterpret_cast<float4*>(p);
+    p += n * 48;
+    const size_t nb = (n + frontend_block_threads() - 1) / frontend_block_threads();
+    a.row_cnt = reinterpret_cast<unsigned*>(p);
+    p += (size_t)256 * nb * 4;
+    a.row_tot = reinterpret_cast<unsigned long long*>(p);
+}
+
 rg_status ensure_workspace(Workspace& w, int64_t n_gauss, int mode, int tiles, int64_t cap)
 {
     const int64_t n = n_gauss > 0 ? n_gauss : 1;
@@ -145,6 +168,7 @@ rg_status ensure_workspace(Workspace& w, int64_t n_gauss, int mode, int tiles, i
         // memory for any tile count) and tile totals: sized for any frame, so a workspace shared by
         // views of several resolutions never runs short
         RG_TRY(ensure(w.tsort, tilesort_matrix_bytes_max() + (size_t)tilesort_max_tiles() * 4, "tile counting sort"));
+        RG_TRY(ensure(w.rowbuf, row_buffer_bytes(n), "row buckets"));
         for (int k = 0; k < 2; k++) {
             RG_TRY(ensure(w.gkeys[k], (size_t)n * 4, "depth keys"));
             RG_TRY(ensure(w.gvals[k], (size_t)n * 4, "depth order"));
@@ -302,6 +326,7 @@ rg_status roofgs_build(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_t
     }
     f.tile_shift = a.keys16 ? 0 : F.lay.b_d;
     w.last_key16 = a.keys16 != nullptr;
+    w.last_cols = false;
     w.last_tilesort = f.tile_sort;
     w.last_bd = F.lay.b_d;
     w.last_mode = RG_MODE_ROOFGS;
@@ -338,6 +363,7 @@ void roofgs_raster_args(rg_scene* s, Workspace& w, const FrameLayout& F, uint32_
     } else {
         r.skeys = w.keys[fin].as<unsigned>();
     }
+    r.key_cols = w.last_key16 && w.last_cols;
     r.tile_shift = w.last_key16 ? 0 : F.lay.b_d;
     r.ranges_out = w.ranges.as<uint2>();
     r.ctr = w.ctrl.as<Counters>();
@@ -367,6 +393,7 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     const bool search_ranges = mode == RG_MODE_ROOFGS && out != nullptr && !tile_sort;
     w.last_key16 = false;
     w.last_tilesort = false;
+    w.last_cols = false;
     RG_CK(cudaMemsetAsync(w.ctrl.p, 0, CTRL_ALLOC, st));
     if (flags & RG_FLAG_TEST_STALL_SORT) { // tile 0 of the first entry-sort pass is never claimed
         k_set_word<<<1, 1, 0, st>>>(&ctr->sort_tile_ctr[0], 1u);
@@ -439,8 +466,22 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
     } else {
         RoofgsFrame f;
         RG_TRY(roofgs_build(s, w, F, flags, f));
-        RG_CK(cudaMemsetAsync(w.lb_status.p, 0,
-                              (size_t)((n + frontend_block_threads() - 1) / frontend_block_threads() + 1) * 8, st));
+        // the row-bucketed front end: column-major 16-bit keys grouped by tile row, one 8-bit
+        // pass over the column left to the sort (the rasterizer finds the ranges)
+        const bool rows = !(flags & RG_FLAG_ORDERED_FRONT_END) && search_ranges && f.depth_order && f.fa.keys16 &&
+                          !f.tile_sort && F.lay.tiles_x <= 256 && F.lay.tiles_y <= 256 && n > 0;
+        if (rows) {
+            f.fa.rows = F.lay.tiles_y;
+            row_buffer_views(w, f.fa);
+            f.fa.hist_passes = 1; // the column digits
+            f.sa.passes = 1;
+            f.sa.bit0 = 8;
+            f.sa.rank_modes = sort_rank_modes(SORT_RANK_PEERS);
+            w.last_cols = true;
+        } else {
+            RG_CK(cudaMemsetAsync(w.lb_status.p, 0,
+                                  (size_t)((n + frontend_block_threads() - 1) / frontend_block_threads() + 1) * 8, st));
+        }
         if (f.depth_order) {
             NvtxScope r_("rg depth order");
             roofgs_depth_order(f, w, st);
@@ -448,7 +489,8 @@ rg_status render_once(rg_scene* s, Workspace& w, const FrameLayout& F, int mode,
         if (ev) RG_CK(cudaEventRecord(E[1], st));
         {
             NvtxScope r_("rg front end");
-            launch_frontend_fused(f.fa, st);
+            if (rows) launch_frontend_rows(f.fa, st);
+            else launch_frontend_fused(f.fa, st);
         }
         sa = f.sa;
         tile_shift = f.tile_shift;
@@ -925,6 +967,26 @@ rg_status rg_inspect(rg_scene* s, int32_t what, void* host_dst, int64_t cap_byte
         Counters c;
         RG_CK(cudaMemcpy(&c, s->ws.ctrl.p, sizeof(c), cudaMemcpyDeviceToHost));
         const int fin = s->ws.last_passes & 1;
+        // column-major keys: the entries are regrouped tile by tile in tile-id order (each tile's
+        // range, in its order), which is the order of the entries sorted by tile id
+        std::vector<uint32_t> cval;
+        std::vector<uint2> cr;
+        if (s->ws.last_key16 && s->ws.last_cols) {
+            const size_t ne = c.n_entries;
+            std::vector<uint32_t> v(ne);
+            cr.resize((size_t)s->ws.last_tiles);
+            RG_CK(cudaMemcpy(cr.data(), s->ws.ranges.p, cr.size() * 8, cudaMemcpyDeviceToHost));
+            if (ne) RG_CK(cudaMemcpy(v.data(), s->ws.vals[fin].p, ne * 4, cudaMemcpyDeviceToHost));
+            cval.reserve(ne);
+            uint32_t at = 0;
+            for (size_t t = 0; t < cr.size(); t++) {
+                const uint32_t b = cr[t].x, e = std::min<uint32_t>(cr[t].y, (uint32_t)ne);
+                const uint32_t len = e > b ? e - b : 0u;
+                for (uint32_t j = b; j < b + len; j++) cval.push_back(v[j]);
+                cr[t] = len ? make_uint2(at, at + len) : make_uint2(0u, 0u);
+                at += len;
+            }
+        }
         if (what == RG_INSPECT_KEYS && s->ws.last_key16) {
             // the entries carried 16-bit tile ids: each 32-bit key (tile << b_d | q_d) is rebuilt
             // from the tile and the depth code of its Gaussian (the per-Gaussian depth sort's result);
@@ -933,7 +995,11 @@ rg_status rg_inspect(rg_scene* s, int32_t what, void* host_dst, int64_t cap_byte
             std::vector<uint16_t> t16(ne);
             std::vector<uint32_t> val(ne), gq(ng), gi(ng), q(ng, 0u);
             if (ne) {
-                if (s->ws.last_tilesort) {
+                if (s->ws.last_cols) {
+                    for (size_t t = 0; t < cr.size(); t++)
+                        for (uint32_t j = cr[t].x; j < cr[t].y; j++) t16[j] = (uint16_t)t;
+                    for (size_t j = 0; j < ne; j++) val[j] = j < cval.size() ? cval[j] : 0u;
+                } else if (s->ws.last_tilesort) {
                     std::vector<uint2> rr((size_t)s->ws.last_tiles);
                     RG_CK(cudaMemcpy(rr.data(), s->ws.ranges.p, rr.size() * 8, cudaMemcpyDeviceToHost));
                     for (size_t t = 0; t < rr.size(); t++)
@@ -941,7 +1007,7 @@ rg_status rg_inspect(rg_scene* s, int32_t what, void* host_dst, int64_t cap_byte
                 } else {
                     RG_CK(cudaMemcpy(t16.data(), s->ws.keys[fin].p, ne * 2, cudaMemcpyDeviceToHost));
                 }
-                RG_CK(cudaMemcpy(val.data(), s->ws.vals[fin].p, ne * 4, cudaMemcpyDeviceToHost));
+                if (!s->ws.last_cols) RG_CK(cudaMemcpy(val.data(), s->ws.vals[fin].p, ne * 4, cudaMemcpyDeviceToHost));
             }
             if (ng) {
                 RG_CK(cudaMemcpy(gq.data(), s->ws.gkeys[s->ws.last_gfin].p, ng * 4, cudaMemcpyDeviceToHost));
@@ -962,9 +1028,22 @@ rg_status rg_inspect(rg_scene* s, int32_t what, void* host_dst, int64_t cap_byte
         } else if (what == RG_INSPECT_KEYS) {
             src = s->ws.keys[fin].p;
             bytes = (int64_t)c.n_entries * (s->ws.last_mode == RG_MODE_EXACT ? 8 : 4);
+        } else if (what == RG_INSPECT_VALUES && s->ws.last_key16 && s->ws.last_cols) {
+            cval.resize(c.n_entries, 0u);
+            tmp.resize(cval.size() * 4);
+            if (!cval.empty()) memcpy(tmp.data(), cval.data(), tmp.size());
+            src = tmp.data();
+            device_src = false;
+            bytes = (int64_t)tmp.size();
         } else if (what == RG_INSPECT_VALUES) {
             src = s->ws.vals[fin].p;
             bytes = (int64_t)c.n_entries * 4;
+        } else if (s->ws.last_key16 && s->ws.last_cols) {
+            tmp.resize(cr.size() * 8);
+            if (!cr.empty()) memcpy(tmp.data(), cr.data(), tmp.size());
+            src = tmp.data();
+            device_src = false;
+            bytes = (int64_t)tmp.size();
         } else {
             src = s->ws.ranges.p;
             bytes = (int64_t)s->ws.last_tiles * 8;

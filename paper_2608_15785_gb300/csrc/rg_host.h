@@ -66,12 +66,14 @@ struct Workspace {
     DevBuf gkeys[2], gvals[2], gstatus[2];                // RoofGS per-Gaussian depth sort
     DevBuf gbuf;                                          // backward: image-space gradients [n][9]
     DevBuf tsort;                                         // RoofGS per-tile counting sort: matrix + tile totals
+    DevBuf rowbuf; // RoofGS row-bucketed front end: rows and row tests per slot, counts per tile row
     // last frame
     int last_mode = -1;
     int last_passes = 0;
     int last_tiles = 0;
     bool last_key16 = false; // entries carried 16-bit tile ids (the 32-bit keys are rebuilt on inspection)
     bool last_tilesort = false; // the entries were grouped by the per-tile counting sort (keys rebuilt from ranges)
+    bool last_cols = false;  // the 16-bit keys were column-major (tx << 8 | ty): entries regrouped from the ranges
     int last_bd = 0;         // b_d of the last RoofGS frame
     int last_gfin = 0;       // buffer of the per-Gaussian depth sort's result
     // stage events
@@ -84,7 +86,7 @@ struct Workspace {
     {
         DevBuf* bufs[] = {&keys[0], &keys[1], &vals[0], &vals[1], &ranges, &ctrl, &lb_status, &sort_status[0],
                           &sort_status[1], &mean2, &depth, &quad, &rgb, &rect, &touched, &offsets, &rec, &gkeys[0],
-                          &gkeys[1], &gvals[0], &gvals[1], &gstatus[0], &gstatus[1], &gbuf, &tsort};
+                          &gkeys[1], &gvals[0], &gvals[1], &gstatus[0], &gstatus[1], &gbuf, &tsort, &rowbuf};
         for (DevBuf* b : bufs) b->release();
         if (ev_init)
             for (int f = 0; f < EV_RING; f++)

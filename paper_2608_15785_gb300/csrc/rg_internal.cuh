@@ -505,8 +505,19 @@ struct FrontendArgs {
     Sticky* sticky;
     unsigned* hist;             // [FE_HIST_COPIES][2][256] digit counts of the tile field, or null
     int hist_passes;            // 0, 1 or 2: 8-bit digits of the tile id counted (b_t <= 16)
+    // Row-bucketed front end (launch_frontend_rows): rows > 0 tile rows (at most 256, as are
+    // the tile columns); the entries carry the column-major 16-bit key tx << 8 | ty and come
+    // out grouped by tile row, which leaves one 8-bit sort pass (the column) to the sort
+    int rows;
+    unsigned* row_n;             // [N] tile rows of the Gaussian of each slot (0: none)
+    float4* row_rt;              // [3][N] its row test (RowTestS as three float4 planes)
+    unsigned* row_cnt;           // [rows][blocks] entries of each tile row per block, then their
+                                 // exclusive prefix over the blocks (saturated at 2^31 - 1)
+    unsigned long long* row_tot; // [rows] entries of each tile row
 };
 void launch_frontend_fused(const FrontendArgs& a, cudaStream_t s);
+// count kernel -> per-row scan of the block counts -> scatter kernel (a.rows > 0)
+void launch_frontend_rows(const FrontendArgs& a, cudaStream_t s);
 
 // Views of a batch rendered by one launch of a stage (the batch's fused path).
 constexpr int MAX_BATCH_VIEWS = 32;
@@ -614,6 +625,7 @@ struct RasterArgs {
     // ranges_out; `ranges` is then unused
     const unsigned* skeys;
     const unsigned short* skeys16; // instead of skeys: 16-bit tile ids (tile_shift 0)
+    int key_cols;                  // skeys16 hold the column-major key tx << 8 | ty
     int tile_shift;
     uint2* ranges_out;
     const Counters* ctr;  // frame counters (n_entries) for the search

@@ -229,8 +229,9 @@ rg_status rg_server_create(rg_scene* const* scenes, int32_t n_scenes, const rg_s
     const int64_t cap = std::min<int64_t>(MAX_CAP, std::max<int64_t>(1 << 20, entries + entries / 2 + 1024));
     const int64_t ngauss = scenes[big]->n;
     const int64_t tiles = (int64_t)((sv->max_w + TILE - 1) / TILE) * ((sv->max_h + TILE - 1) / TILE);
-    // bytes of one slot: 2 x (keys 8 B + values 4 B) per entry, sort status, per-Gaussian arrays, ranges, image
-    sv->slot_bytes = cap * 24 + (cap / 4096 + 1) * 2048 + ngauss * (sv->mode == RG_MODE_EXACT ? 72 : 56) +
+    // bytes of one slot: 2 x (keys 8 B + values 4 B) per entry, sort status, per-Gaussian arrays (RoofGS:
+    // records, depth order, row tests and row counts), ranges, image
+    sv->slot_bytes = cap * 24 + (cap / 4096 + 1) * 2048 + ngauss * (sv->mode == RG_MODE_EXACT ? 72 : 112) +
                      tiles * 8 + (int64_t)out_bytes;
     int nslots = cfg->max_slots > 0 ? cfg->max_slots : 8;
     nslots = (int)std::max<int64_t>(1, std::min<int64_t>(nslots, sv->budget / std::max<int64_t>(sv->slot_bytes, 1)));

@@ -122,3 +122,19 @@ def test_noalloc_sort_rejects_misaligned_arrays_before_any_launch(L):
         assert b"16-byte" in L.rg_last_error()
     assert L.rg_sort_pairs_noalloc(C.c_void_p(0x10000), C.c_void_p(0x20000), -1, 32, None, None) == 1
     assert L.rg_sort_pairs_noalloc(C.c_void_p(0x10000), C.c_void_p(0x20000), 10, 12, None, None) == 1
+
+
+def test_binding_constants_match_the_header():
+    """Every RG_* integer constant of include/rg.h has the same value in the binding."""
+    src = open(os.path.join(ROOT, "include", "rg.h")).read()
+    consts = {}
+    for name, expr in re.findall(r"#define (RG_[A-Z0-9_]+)\s+(\(1u << \d+\)|\d+u?)(?=\s|$)", src):
+        m = re.match(r"\(1u << (\d+)\)", expr)
+        consts[name] = (1 << int(m.group(1))) if m else int(expr.rstrip("u"))
+    assert "RG_FLAG_ORDERED_FRONT_END" in consts and "RG_INSPECT_KEYS" in consts
+    for name, v in consts.items():
+        if hasattr(binding, name):
+            assert getattr(binding, name) == v, name
+    flags = [n for n in consts if n.startswith("RG_FLAG_")]
+    assert all(hasattr(binding, n) for n in flags), [n for n in flags if not hasattr(binding, n)]
+    assert len({consts[n] for n in flags}) == len(flags)  # no two flags share a bit

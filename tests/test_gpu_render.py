@@ -308,9 +308,9 @@ def test_capacity_overflow_regrows_and_is_reported():
     small = gpu_scene(sc)
     small.reserve(1000)  # far below the ~27k entries of this frame
     # asynchronous render: image incomplete, overflow recorded
-    small.render(cam)
+    small.render(cam, flags=binding.RG_FLAG_ORDERED_FRONT_END)
     torch.cuda.synchronize()
-    # the sort covers the entries that fit, i.e. the first ones the front end emitted
+    # the sort covers the entries that fit, i.e. the first ones the fused front end emitted
     # (Gaussians in (depth code, index) order, each one's tiles ascending): its digit
     # counts are taken from the stored keys, not from the front end's count of all
     gk = small.inspect(binding.RG_INSPECT_KEYS).view(np.uint32).astype(np.uint64)
@@ -570,3 +570,95 @@ def test_render_into_pinned_host_memory(mode):
     torch.cuda.synchronize()
     assert torch.equal(dev.cpu(), host)
     gs.check()
+
+
+# ---------------------------------------------------------------------------
+# the row-bucketed front end (default) against the fused front end with the ordered
+# allocation (RG_FLAG_ORDERED_FRONT_END): the same entries per tile in the same order
+# ---------------------------------------------------------------------------
+
+def _entries(gs):
+    return tuple(gs.inspect(w) for w in (binding.RG_INSPECT_KEYS, binding.RG_INSPECT_VALUES,
+                                         binding.RG_INSPECT_RANGES))
+
+
+def _both_front_ends(gs, cam, flags=0, tile=(16, 16)):
+    ia, sa = render(gs, cam, "roofgs", flags=flags, stats=True, tile=tile)
+    ea = _entries(gs)
+    ib, sb = render(gs, cam, "roofgs", flags=flags | binding.RG_FLAG_ORDERED_FRONT_END, stats=True, tile=tile)
+    eb = _entries(gs)
+    for f in ("n_entries", "n_visible", "n_front", "n_pairs", "n_blends"):
+        assert sa[f] == sb[f], (f, sa[f], sb[f])
+    for x, y in zip(ea, eb):
+        assert np.array_equal(x, y)
+    assert np.array_equal(ia, ib)
+    return sa, sb
+
+
+@pytest.mark.parametrize("name", ["tiny_256", "clustered_1080p", "clustered_4k"])
+def test_row_buckets_equal_the_ordered_front_end(name):
+    """Keys, values and ranges (rebuilt in tile-id order), counters and images (2 and 4 pixels
+    per thread) bit-identical between the two front ends; the row-bucketed frame leaves one
+    8-bit pass (the tile column) to the sort."""
+    sc, cams = synth.workload(name)
+    gs = gpu_scene(sc, per_gauss=True)
+    cam = cams[0] if name != "clustered_4k" else cams[11]
+    for flags in (0, binding.RG_FLAG_QUAD_PIXEL):
+        sa, sb = _both_front_ends(gs, cam, flags)
+        assert sa["sort_passes"] == 1
+        assert sb["sort_passes"] == (sa["b_t"] + 7) // 8
+    gs.check()
+
+
+@pytest.mark.parametrize("wh,hfov,tile", [((4096, 48), 40.0, (16, 16)), ((48, 4096), 0.5, (16, 16)),
+                                          ((1000, 700), 60.0, (8, 32)), ((100, 37), 60.0, (16, 16)),
+                                          ((1, 1), 60.0, (16, 16))])
+def test_row_buckets_extreme_grids_against_the_oracle(wh, hfov, tile):
+    """256 tile columns (the key's high byte full), 256 tile rows (the search for the last row's
+    end carries into the next column), an 8 x 32 tile grid and ragged images: keys, values and
+    ranges bit-exact against the oracle, and equal to the ordered front end's."""
+    sc = small_random_scene(4000, seed=5, spread=1.0)
+    cam = synth.look_at_camera((0.0, 0.0, -3.0), wh[0], wh[1], hfov, 0.2, 6.0, bg=(0.1, 0.2, 0.3))
+    gs = gpu_scene(sc)
+    comp = oracle.compact(sc)
+    sa, _ = _both_front_ends(gs, cam, tile=tile)
+    render(gs, cam, "roofgs", stats=True, tile=tile)
+    assert sa["n_entries"] == _keys_equal(gs, sc, cam, oracle.ROOFGS, comp, tile=tile)
+    if wh[0] * wh[1] > 1:
+        assert sa["n_entries"] > 0
+    if wh == (48, 4096):  # entries in the last tile row
+        r = gs.inspect(binding.RG_INSPECT_RANGES).reshape(-1, 2)
+        assert (r[-3:, 1] > r[-3:, 0]).any()
+    gs.check()
+
+
+def test_row_buckets_capacity_overflow_regrows():
+    """A workspace too small for the frame: the row-bucketed front end keeps the entries whose
+    slot in its (tile row, depth code, index, tile column) order lies below the capacity, the
+    sort covers exactly those (digits recounted from the stored keys), the overflow is
+    reported, and the re-rendered frame equals a full one."""
+    sc, cams = synth.workload("tiny_256")
+    cam = cams[0]
+    ref = render(gpu_scene(sc), cam, "roofgs")
+    small = gpu_scene(sc)
+    small.reserve(1000)
+    small.render(cam)
+    torch.cuda.synchronize()
+    gk = small.inspect(binding.RG_INSPECT_KEYS).view(np.uint32).astype(np.uint64)
+    gv = small.inspect(binding.RG_INSPECT_VALUES)
+    k, v, _, _ = oracle.keys(sc, cam, oracle.ROOFGS, comp=oracle.compact(sc))
+    lay = oracle.layout(cam)
+    b_d = np.uint64(lay["b_d"])
+    tile = k >> b_d
+    tx, ty = tile % np.uint64(lay["tiles_x"]), tile // np.uint64(lay["tiles_x"])
+    assert 0 < gk.size < k.size
+    kept = np.lexsort((tx, v, k & ((np.uint64(1) << b_d) - np.uint64(1)), ty))[: gk.size]
+    expect = kept[np.lexsort((v[kept], k[kept]))]
+    assert np.array_equal(gk, k[expect]) and np.array_equal(gv, v[expect])
+    with pytest.raises(binding.RgError) as e:
+        small.check()
+    assert e.value.status == 4
+    img, st = render(small, cam, "roofgs", stats=True)
+    assert st["regrown"] == 1 and st["capacity"] >= st["n_entries"]
+    assert np.array_equal(img, ref)
+    small.check()
