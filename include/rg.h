@@ -208,11 +208,14 @@ rg_status rg_scene_reserve(rg_scene* scene, int64_t n_entries);
  * precision and the quadratic form completed in dx, so the image stays within
  * 2e-4 per channel of an FP64 evaluation except where a pair's alpha or T lies
  * within rounding of the 1/255 or 1e-4 thresholds.
- * Pipeline (RoofGS): Gaussians ordered by quantized depth -> fused front end ->
- * stable radix sort of the tile bits of the 32-bit keys (the order of the full
- * key; RG_FLAG_SORT_FULL_KEY sorts all 32 bits in 4 passes instead) -> fast-exp
- * rasterizer with 2 (dual-pixel), 1 or 4 pixels per thread, each tile block
- * finding its own range of the sorted entries (Sec. IV).
+ * Pipeline (RoofGS): Gaussians ordered by quantized depth -> front end (by
+ * default row-bucketed: the entries leave it grouped by tile row, in depth order)
+ * -> stable radix sort of the remaining tile bits (one pass over the tile column;
+ * two tile-bit passes after the fused front end of RG_FLAG_ORDERED_FRONT_END;
+ * either way the order of the full 32-bit key; RG_FLAG_SORT_FULL_KEY sorts all
+ * 32 bits in 4 passes instead) -> fast-exp rasterizer with 2 (dual-pixel), 1 or
+ * 4 pixels per thread, each tile block finding its own range of the sorted
+ * entries (Sec. IV).
  * The number of entries stays on the device: with stats == NULL the call does
  * not synchronise; if the entries exceed the workspace the image is
  * incomplete and the overflow is recorded (see rg_scene_check). With stats
@@ -244,11 +247,14 @@ rg_status rg_stage_times(rg_scene* scene, float* ms7, int32_t* frames);
 
 /* rg_inspect selectors: copy internal buffers of the last frame to host memory */
 #define RG_INSPECT_KEYS 1        /* sorted keys: uint32 (RoofGS) or uint64 (exact), n_entries of them;
-                                    RoofGS frames with at most 16 tile bits sort 16-bit tile ids and
+                                    RoofGS frames with at most 16 tile bits sort 16-bit tile keys and
                                     the 32-bit keys (tile << b_d | q_d) are rebuilt on the host from
-                                    the values and the per-Gaussian depth codes */
-#define RG_INSPECT_VALUES 2      /* sorted values: uint32 Gaussian indices */
-#define RG_INSPECT_RANGES 3      /* uint32 [tiles][2] = [start, end) per tile */
+                                    the values and the per-Gaussian depth codes; the entries of a
+                                    row-bucketed frame (column-major tile keys) are first regrouped in
+                                    tile-id order from the tile ranges, so every frame reports the
+                                    order of the 32-bit key */
+#define RG_INSPECT_VALUES 2      /* sorted values: uint32 Gaussian indices (in the same order) */
+#define RG_INSPECT_RANGES 3      /* uint32 [tiles][2] = [start, end) per tile (of the same order) */
 #define RG_INSPECT_SH_CODES 4    /* int8 [n][16][3] compact SH codes */
 #define RG_INSPECT_SH_SCALES 5   /* float [4][3] band scales s_{d,c} */
 #define RG_INSPECT_GAUSS_SCALE 6 /* uint16 [n] FP16 per-Gaussian SH factors */
