@@ -46,3 +46,22 @@ def test_roofgs_more_than_16_tile_bits_and_exact_mode():
     assert w["ranges"] == 8 * nd + 8 * 240 * 135
     w = bench.stage_work("exact", _stats(7, tiles_x=480, tiles_y=270), 7680, 4320)
     assert w["hist"] == 8 * nd  # 3 tile digits: the keys are read for the digits
+
+
+def test_roofgs_row_bucketed_front_end():
+    """The row-bucketed front end (the default where the tile grid fits 256 x 256 and the tile bits
+    16): the fused kernel's bytes plus the row data it stores and reads back, and one column pass."""
+    st = dict(_stats(1), b_t=15)
+    assert bench.row_buckets(st, ordered=False)
+    assert not bench.row_buckets(st, ordered=True)
+    assert not bench.row_buckets(dict(st, tiles_x=480, tiles_y=270, b_t=17), ordered=False)
+    assert not bench.row_buckets(dict(st, tiles_x=120, tiles_y=270), ordered=False)  # 32 x 8 tiles at 4K
+    w = bench.stage_work("roofgs", st, 3840, 2160, rows=True)
+    N, nf, nv, nd = 3_000_000, 2_500_000, 2_000_000, 60_000_000
+    nb = (N + 255) // 256
+    # + 4 B of tile rows per slot written and read, 48 B row test + 4 B order per visible Gaussian
+    # (written / read back), 4 B per (tile row, block) counted, scanned both ways and read
+    assert w["front"] == 20 * N + 16 * nf + 80 * nv + 6 * nd + 8 * N + 100 * nv + 16 * 135 * nb
+    assert w["sort_pass"] == 12 * nd and w["passes"] == 1
+    # one pass's digit counts summed from the front end's 16 copies
+    assert w["hist"] == 1024 * ((nd + 6143) // 6144) + 17 * 256 * 4
